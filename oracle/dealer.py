@@ -1,0 +1,164 @@
+"""Trusted dealer and party simulation for tests -- TEST INFRASTRUCTURE.
+
+The offline phase (§3.5) and F_MAC (App. A.2) are replaced by a trusted dealer,
+as in the simulator of the security proof (App. B): it knows the global key and
+the triples and hands each party consistent authenticated shares.
+
+  * alpha_i uniform in [0, 2^s) per party; alpha = sum_i alpha_i mod 2^{k+s}.
+  * A~, B~ uniform; C~ = A~ . B~ mod 2^{k+s}; R~ uniform (Fig. Pi_MatMul and
+    Fig. Pi_OptMAC preprocessing).
+  * every secret V in {A, B, C, R} is additively shared: parties 0..n-2 draw
+    uniform shares, the last party's share makes the sum V~; its tag
+    m(V) = alpha . V~ (§2.4) is shared the same way.
+  * X~, Y~ uniform; the opened E = X~ - A~ and F = Y~ - B~ (Fig. Pi_MatMul
+    step 1) are public.  chi (N) and chi^ (M) are public coins in [0, 2^s)
+    (F_Rand, App. A.1).
+
+Randomness comes from `synth` (uniform words); all ring arithmetic goes
+through `oracle`.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+import oracle as O
+import synth
+
+
+def _store(bits: int, a: np.ndarray) -> np.ndarray:
+    """Values below 2^64 re-stored in the storage of Z_{2^bits} (hi word 0)."""
+    if O.words(bits) == 1:
+        return np.ascontiguousarray(a.astype(np.uint64))
+    out = np.zeros(a.shape + (2,), dtype=np.uint64)
+    out[..., 0] = a
+    return out
+
+
+def key_range(ring: synth.Ring, seed: int, tid: int, party: int, shape) -> np.ndarray:
+    """Uniform elements of [0, 2^s) (s <= 64) stored in ring width k + s."""
+    if ring.s > 64:
+        raise ValueError("key ring wider than 64 bits is not used")
+    return _store(ring.bits, synth.uniform(seed, tid, party, shape, ring.s))
+
+
+@dataclass
+class Party:
+    """One party's authenticated shares for one layer."""
+    index: int
+    alpha: np.ndarray
+    A: np.ndarray
+    B: np.ndarray
+    C: np.ndarray
+    R: np.ndarray
+    mA: np.ndarray
+    mB: np.ndarray
+    mC: np.ndarray
+    mR: np.ndarray
+
+
+@dataclass
+class Deal:
+    ring: synth.Ring
+    M: int
+    K: int
+    N: int
+    alpha: np.ndarray            # global key (one element)
+    X: np.ndarray                # secret inputs (for invariants only)
+    Y: np.ndarray
+    A: np.ndarray                # reconstructed triple (for invariants only)
+    B: np.ndarray
+    C: np.ndarray
+    R: np.ndarray
+    E: np.ndarray                # public opened matrices
+    F: np.ndarray
+    chi: np.ndarray
+    chi_hat: np.ndarray
+    parties: list = field(default_factory=list)
+
+
+def _share(bits, seed, tid, target, n, shape):
+    """Additive shares of `target`: uniform for parties 0..n-2, last fixes the sum."""
+    shares = [synth.uniform(seed, tid, i + 1, shape, bits) for i in range(n - 1)]
+    last = target.copy()
+    for s_ in shares:
+        last = O.sub(bits, last, s_)
+    return shares + [last]
+
+
+def deal(ring: synth.Ring, M: int, K: int, N: int, n: int = 2, seed: int = 1,
+         alpha_full_width: bool = False) -> Deal:
+    bits = ring.bits
+    T = synth.TID
+    if alpha_full_width:
+        alphas = [synth.uniform(seed, T["alpha"], i, (1,), bits) for i in range(n)]
+    else:
+        alphas = [key_range(ring, seed, T["alpha"], i, (1,)) for i in range(n)]
+    alpha = alphas[0].copy()
+    for a in alphas[1:]:
+        alpha = O.add(bits, alpha, a)
+    X = synth.uniform(seed, T["X"], 0, (M, K), bits)
+    Y = synth.uniform(seed, T["Y"], 0, (K, N), bits)
+    A = synth.uniform(seed, T["A"], 0, (M, K), bits)
+    B = synth.uniform(seed, T["B"], 0, (K, N), bits)
+    C = O.ring_gemm(bits, A, B)
+    R = synth.uniform(seed, T["R"], 0, (M, N), bits)
+    E = O.sub(bits, X, A)
+    F = O.sub(bits, Y, B)
+    chi = key_range(ring, seed, T["chi"], 0, (N,))
+    chi_hat = key_range(ring, seed, T["chi_hat"], 0, (M,))
+    sh = {}
+    for name, V, shape in (("A", A, (M, K)), ("B", B, (K, N)), ("C", C, (M, N)), ("R", R, (M, N))):
+        sh[name] = _share(bits, seed, T[name], V, n, shape)
+        sh["m" + name] = _share(bits, seed, T["m" + name], O.smul(bits, alpha, V), n, shape)
+    parties = [Party(i, alphas[i], sh["A"][i], sh["B"][i], sh["C"][i], sh["R"][i],
+                     sh["mA"][i], sh["mB"][i], sh["mC"][i], sh["mR"][i]) for i in range(n)]
+    return Deal(ring, M, K, N, alpha, X, Y, A, B, C, R, E, F, chi, chi_hat, parties)
+
+
+def total(bits: int, arrays) -> np.ndarray:
+    """Opening: sum of the parties' shares mod 2^{k+s}."""
+    arrays = list(arrays)
+    acc = arrays[0].copy()
+    for a in arrays[1:]:
+        acc = O.add(bits, acc, a)
+    return acc
+
+
+def run_layer(d: Deal, tamper=None):
+    """Run the whole per-layer protocol for every party through the oracle.
+
+    Returns a dict of per-party lists and public values.  `tamper` is an
+    optional dict of host-side fault injections:
+      "Z": (party, flat_index, e)   add e to one party's [Z]_i before opening D
+      "Dt": (flat_index, e)         add e to the broadcast D~ seen by everyone
+      "alpha": (party, e)           use alpha_i + e in that party's tag
+    """
+    tamper = tamper or {}
+    bits = d.ring.bits
+    Z = [O.linear_share(bits, p.index, d.E, d.F, p.A, p.B, p.C) for p in d.parties]
+    if "Z" in tamper:
+        i, j, e = tamper["Z"]
+        flat = Z[i].reshape(-1, O.words(bits))
+        flat[j] = O.from_int(O.to_int(flat[j], bits) + e, bits)
+    mZ_full = [O.linear_tag_full(bits, p.alpha, d.E, d.F, p.mA, p.mB, p.mC) for p in d.parties]
+    D = [O.sub(bits, p.R, z) for p, z in zip(d.parties, Z)]
+    Dt = total(bits, D)
+    if "Dt" in tamper:
+        j, e = tamper["Dt"]
+        flat = Dt.reshape(-1, O.words(bits))
+        flat[j] = O.from_int(O.to_int(flat[j], bits) + e, bits)
+    alphas = [p.alpha for p in d.parties]
+    if "alpha" in tamper:
+        i, e = tamper["alpha"]
+        alphas[i] = O.from_int(O.to_int(alphas[i], bits).reshape(-1)[0] + e, bits).reshape(alphas[i].shape)
+    mZ_opt = [O.optmac(bits, a, p.mR, Dt) for a, p in zip(alphas, d.parties)]
+    comp = [O.compact_tag(bits, a, d.E, d.F, p.mA, p.mB, p.mC, p.mR, Dt, d.chi)
+            for a, p in zip(alphas, d.parties)]
+    mDc = [c[0] for c in comp]
+    Dc = comp[0][1]
+    mZc = [c[2] for c in comp]
+    cs = [O.check_compact(bits, a, d.chi_hat, Dc, m) for a, m in zip(alphas, mDc)]
+    return dict(Z=Z, mZ_full=mZ_full, D=D, Dt=Dt, mZ_opt=mZ_opt, mDc=mDc, Dc=Dc,
+                mZc=mZc, cs=cs, cs_total=total(bits, cs))
