@@ -1,0 +1,553 @@
+#!/usr/bin/env python3
+"""Benchmark of one party's online SPDZ2k linear layers with CompactTag on GB300.
+
+Workload (default): the two CNN-style linear layers as im2col ring GEMMs in
+Z_2^64 (k = s = 32) -- a 3x3 conv on 32x32x64 -> 64 (M, K, N = 1024, 576, 64)
+and a 4096 x 4096 dense layer at batch 128 (128, 4096, 4096) -- for two
+simulated parties on one GPU.  One step runs, for each layer and each party:
+the share (a1), the full SPDZ2k tag (a2, the baseline), the CompactTag tag
+(a3-a5) and its check share (a6).  Inputs are uniform ring words (exactly the
+distribution of real shares), resident in HBM before the timed region.
+
+Metric: ring-GMAC/s over the step.  Ring multiply-accumulates per layer and
+party: 2MKN for the share, 2MKN for the full tag (E.mB + (mA + alpha E).F; the
+paper's count is 3MKN + MN), 4MN + 2KN + 3MK + M for the CompactTag tag
+(§3.4.3) and M for the check.  Also reported: the tag-overhead ratio
+t(CompactTag) / t(full tag) per layer and summed, p50/p99 step latency, the
+roofline fraction of the dominant kernel and the oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+from paper_2311_04406_gb300 import costmodel  # noqa: E402
+
+METRIC = "ring-GMAC/s and tag-overhead ratio (CompactTag vs full tag), bit-exact; p99"
+PARTIES = 2
+RING = synth.Z64
+SEED = 0xC0FFEE01
+L2_BYTES = 129 * 2**20
+
+
+def layer_units(L) -> dict:
+    M, K, N = L.M, L.K, L.N
+    return dict(share=2 * M * K * N, full=2 * M * K * N,
+                compact=costmodel.compact_tag_mults(M, K, N), check=M)
+
+
+def step_units(layers) -> int:
+    return PARTIES * sum(sum(layer_units(L).values()) for L in layers)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get(
+            "bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: every rank runs the same workload)
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("MPC_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+
+def _uniform(seed, name, party, shape, bits):
+    return synth.uniform(seed, synth.TID[name], party, shape, bits)
+
+
+def host_inputs(layers, seed=SEED):
+    """Uniform inputs per layer: public E, F, D~, chi, chi^ and per-party shares."""
+    out = []
+    b = RING.bits
+    for li, L in enumerate(layers):
+        M, K, N = L.M, L.K, L.N
+        sd = seed + 1000 * li
+        pub = dict(E=_uniform(sd, "E", 0, (M, K), b), F=_uniform(sd, "F", 0, (K, N), b),
+                   Dt=_uniform(sd, "Dt", 0, (M, N), b), chi=_uniform(sd, "chi", 0, (N,), RING.s),
+                   chi_hat=_uniform(sd, "chi_hat", 0, (M,), RING.s))
+        parties = []
+        for p in range(PARTIES):
+            parties.append(dict(
+                alpha=_uniform(sd, "alpha", p, (1,), RING.s),
+                A=_uniform(sd, "A", p + 1, (M, K), b), B=_uniform(sd, "B", p + 1, (K, N), b),
+                C=_uniform(sd, "C", p + 1, (M, N), b), mA=_uniform(sd, "mA", p + 1, (M, K), b),
+                mB=_uniform(sd, "mB", p + 1, (K, N), b), mC=_uniform(sd, "mC", p + 1, (M, N), b),
+                mR=_uniform(sd, "mR", p + 1, (M, N), b)))
+        out.append((L, pub, parties))
+    return out
+
+
+class GpuRun:
+    def __init__(self, layers, torch, abi, pinned_host=False):
+        self.torch, self.abi = torch, abi
+        self.layers = layers
+        self.stream = torch.cuda.current_stream()
+        hi = host_inputs(layers)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64))
+        self.items = []
+        self.h2d_pairs = []   # (host pinned, device) for the e2e copy
+        for L, pub, parties in hi:
+            M, K, N = L.M, L.K, L.N
+            dpub = {k: t(v).cuda() for k, v in pub.items()}
+            dpar = []
+            for p, sh in enumerate(parties):
+                lay = abi.make_layer(M, K, N, RING.k, RING.s, p, PARTIES)
+                d = {k: t(v).cuda() for k, v in sh.items()}
+                d["Z"] = torch.empty(M, N, dtype=torch.int64, device="cuda")
+                d["mZf"] = torch.empty(M, N, dtype=torch.int64, device="cuda")
+                d["mZ"] = torch.empty(M, N, dtype=torch.int64, device="cuda")
+                d["mDc"] = torch.empty(M, dtype=torch.int64, device="cuda")
+                d["Dc"] = torch.empty(M, dtype=torch.int64, device="cuda")
+                d["cs"] = torch.empty(1, dtype=torch.int64, device="cuda")
+                d["layer"] = lay
+                nws = max(abi.mpc_workspace_size(lay, w) for w in range(5))
+                d["ws"] = torch.empty(max(nws, 256), dtype=torch.uint8, device="cuda")
+                dpar.append(d)
+                if pinned_host:
+                    for k, v in sh.items():
+                        self.h2d_pairs.append((t(v).pin_memory(), d[k]))
+            if pinned_host:
+                for k, v in pub.items():
+                    self.h2d_pairs.append((t(v).pin_memory(), dpub[k]))
+            self.items.append((L, dpub, dpar))
+        self.outputs = [d[k] for _, _, dpar in self.items for d in dpar
+                        for k in ("Z", "mZf", "mZ", "mDc", "Dc", "cs")]
+        self.h_outputs = [o.cpu().pin_memory() for o in self.outputs] if pinned_host else []
+
+    # one call of each kind
+    def share(self, i, p):
+        L, pub, par = self.items[i]
+        d = par[p]
+        self.abi.mpc_linear_share(d["layer"], pub["E"], pub["F"], d["A"], d["B"], d["C"], d["Z"],
+                                  ws=d["ws"], stream=self.stream)
+
+    def full(self, i, p):
+        L, pub, par = self.items[i]
+        d = par[p]
+        self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_FULL, d["alpha"], pub["E"], pub["F"],
+                                d["mA"], d["mB"], d["mC"], d["mZf"], ws=d["ws"], stream=self.stream)
+
+    def compact(self, i, p):
+        L, pub, par = self.items[i]
+        d = par[p]
+        self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_COMPACT, d["alpha"], pub["E"], pub["F"],
+                                d["mA"], d["mB"], d["mC"], d["mZ"], mR_i=d["mR"], Dtilde=pub["Dt"],
+                                chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"], ws=d["ws"],
+                                stream=self.stream)
+        self.abi.mpc_tag_check(d["layer"], self.abi.MPC_CHECK_COMPACT, d["alpha"], pub["chi_hat"],
+                               d["Dc"], d["mDc"], d["cs"], ws=d["ws"], stream=self.stream)
+
+    def step(self):
+        for i in range(len(self.items)):
+            for p in range(PARTIES):
+                self.share(i, p)
+                self.full(i, p)
+                self.compact(i, p)
+
+    def launches_per_step(self):
+        n = 0
+        for L, _, _ in self.items:
+            gemm = 1
+            compact = 2 + (1 if L.K > 0 else 0)
+            n += PARTIES * (2 * gemm + compact + 1)
+        return n
+
+    def h2d(self):
+        for h, d in self.h2d_pairs:
+            d.copy_(h, non_blocking=True)
+
+    def d2h(self):
+        for h, d in zip(self.h_outputs, self.outputs):
+            h.copy_(d, non_blocking=True)
+
+    def h2d_bytes(self):
+        return sum(h.numel() * 8 for h, _ in self.h2d_pairs)
+
+    def d2h_bytes(self):
+        return sum(h.numel() * 8 for h in self.h_outputs)
+
+
+def time_calls(torch, fn, reps):
+    """Per-call durations (ms) with CUDA events on the launching stream."""
+    st = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    for a, b in evs:
+        a.record(st)
+        fn()
+        b.record(st)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[i]
+
+
+def profile_traffic(kernel_tag: str):
+    """Per-launch DRAM bytes of `kernel_tag` from the committed ncu summary,
+    when it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel_tag)
+        if not rec:
+            return None
+        import hashlib
+        src = os.path.join(ROOT, "paper_2311_04406_gb300", "csrc", rec["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
+            return None
+        return rec["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    from paper_2311_04406_gb300 import abi, build
+    rank, ws = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    abi.load()
+    layers = synth.cnn_pair()
+    run = GpuRun(layers, torch, abi, pinned_host=not args.no_e2e)
+    units = step_units(layers)
+
+    # warm-up
+    for _ in range(args.warmup):
+        run.step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, per-step events, barrier + sync on both sides
+    barrier(ws)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with Clocks(local) as ck:
+        ev[0].record(st)
+        for k in range(args.steps):
+            run.step()
+            ev[k + 1].record(st)
+        torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = max_over_ranks(total_ms, ws)
+    ms_per_step = total_ms / args.steps
+    value = ws * units * args.steps / (total_ms / 1e3) / 1e9
+
+    # per-call timings: share / full tag / compact tag (+check), per layer
+    reps = max(10, min(50, args.steps * 2))
+    per_layer = []
+    gemm_ms, gemm_flop = [], 0.0
+    for i, L in enumerate(layers):
+        sh = time_calls(torch, lambda: run.share(i, 1), reps)
+        fu = time_calls(torch, lambda: run.full(i, 1), reps)
+        co = time_calls(torch, lambda: run.compact(i, 1), reps)
+        per_layer.append(dict(layer=L.name, M=L.M, K=L.K, N=L.N,
+                              share_ms_p50=pct(sh, 50), full_tag_ms_p50=pct(fu, 50),
+                              compact_tag_ms_p50=pct(co, 50), compact_tag_ms_p99=pct(co, 99),
+                              full_tag_ms_p99=pct(fu, 99),
+                              tag_overhead_ratio=pct(co, 50) / pct(fu, 50),
+                              share_ring_gmacs=2 * L.M * L.K * L.N / (pct(sh, 50) / 1e3) / 1e9,
+                              cost_model_tag_ratio=costmodel.tag_mult_ratio(L.M, L.K, L.N)))
+        gemm_ms += sh + fu
+        gemm_flop += reps * 2 * (2 * L.M * L.K * L.N)
+    sum_co = sum(x["compact_tag_ms_p50"] for x in per_layer)
+    sum_fu = sum(x["full_tag_ms_p50"] for x in per_layer)
+    hbm, bf16, bf16s, src = peaks()
+    tc = any(abi_path_is_tc(abi, L) for L in layers)
+    ring_macs_per_s = gemm_flop / (sum(gemm_ms) / 1e3)
+    if tc:
+        digit = costmodel.digit_products(RING.bits)
+        achieved = ring_macs_per_s * digit * 2 / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
+                "frac": achieved / bf16, "kernel": "ring_gemm_tc",
+                "per_unit": f"{digit} fp16 digit products (2 flop each) per ring MAC",
+                "peak_source": f"{src} bf16 dense burst x 1.0 (fp16 nominal rate equals bf16)",
+                "traffic": profile_traffic("ring_gemm_tc")}
+    else:
+        # 64-bit wrapping multiply-add = 3 IMAD-class ops; 152 SMs x 64 IMAD/clk x 2.07 GHz
+        peak_gops = 152 * 64 * 2.07
+        achieved = ring_macs_per_s * 3 / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                "frac": achieved / peak_gops, "kernel": "ring_gemm_simt",
+                "per_unit": "3 IMAD-class ops per 64-bit ring MAC",
+                "peak_source": "derived: 152 SMs x 64 int32 multiply-add/clk x 2070 MHz",
+                "traffic": profile_traffic("ring_gemm_simt")}
+
+    # end-to-end: the same step through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = max(3, args.steps // 2)
+        run.h2d(); run.step(); run.d2h()
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(e2e_steps):
+            run.h2d()
+            run.step()
+            run.d2h()
+        b.record(st)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e2e_ms = max_over_ranks(max(a.elapsed_time(b), wall * 1e3), ws) / e2e_steps
+        e2e = {"value": ws * units / (e2e_ms / 1e3) / 1e9, "unit": "ring-GMAC/s",
+               "ms_per_step": e2e_ms, "h2d_bytes_per_step": run.h2d_bytes(),
+               "d2h_bytes_per_step": run.d2h_bytes(), "host_buffers": "pinned"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(layers, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "ring-GMAC/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "p50_ms_per_step": pct(step_ms, 50), "p99_ms_per_step": pct(step_ms, 99),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (uniform ring words from seeded SplitMix64; shapes of the CNN layers)",
+            "config": {"workload": "cnn_im2col_conv3x3_32x32x64_and_dense4096_b128",
+                       "layers": [[L.M, L.K, L.N] for L in layers], "ring": "Z_2^64 (k=32, s=32)",
+                       "parties": PARTIES, "parallelism": f"replicas x{ws}",
+                       "l2": f"inputs larger than L2 ({run_bytes(layers) / 2**20:.0f} MiB per step > 129 MiB)"},
+            "tag_overhead_ratio": sum_co / sum_fu,
+            "per_layer": per_layer,
+            "roofline": roof,
+            "gpu_launches": run.launches_per_step() * args.steps,
+            "clocks": ck.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def abi_path_is_tc(abi, L) -> bool:
+    """Whether the library routes this layer's GEMM to the tensor-core kernel."""
+    lay = abi.make_layer(L.M, L.K, L.N, RING.k, RING.s)
+    return abi.mpc_gemm_path(lay) == 1
+
+
+def run_bytes(layers) -> int:
+    tot = 0
+    for L in layers:
+        M, K, N = L.M, L.K, L.N
+        per_party = 8 * (2 * M * K + 2 * K * N + 3 * M * N + 3 * M * N)
+        tot += PARTIES * per_party + 8 * (M * K + K * N + M * N)
+    return tot
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the --impl reference arm)
+
+def cpu_sample(layers, frac_rows):
+    """A bounded sample of the step: share and full tag at the output rows
+    [0, ceil(frac * M)) of each layer and party, and the whole CompactTag path
+    (tag + check) of each layer and party.  Returns (callable, units)."""
+    import oracle as O
+    hi = host_inputs(layers)
+    jobs, units = [], 0
+    for L, pub, parties in hi:
+        M, K, N = L.M, L.K, L.N
+        m = max(1, int(np.ceil(frac_rows * M)))
+        rows = np.repeat(np.arange(m, dtype=np.int64), N)
+        cols = np.tile(np.arange(N, dtype=np.int64), m)
+        for p, sh in enumerate(parties):
+            jobs.append(lambda sh=sh, p=p, pub=pub, rows=rows, cols=cols: (
+                O.linear_share_at(64, p, pub["E"], pub["F"], sh["A"], sh["B"], sh["C"], rows, cols),
+                O.linear_tag_full_at(64, sh["alpha"], pub["E"], pub["F"], sh["mA"], sh["mB"],
+                                     sh["mC"], rows, cols)))
+            units += 2 * (2 * m * K * N)
+            jobs.append(lambda sh=sh, pub=pub: O.check_compact(
+                64, sh["alpha"], pub["chi_hat"],
+                *O.compact_tag(64, sh["alpha"], pub["E"], pub["F"], sh["mA"], sh["mB"], sh["mC"],
+                               sh["mR"], pub["Dt"], pub["chi"])[1::-1]))
+            units += costmodel.compact_tag_mults(M, K, N) + M
+
+    def run():
+        for j in jobs:
+            j()
+    return run, units
+
+
+def cpu_cores() -> int:
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def cpu_baseline(layers, budget_s=15.0):
+    # calibrate on a small sample, then time a sample sized for ~budget_s
+    run, units = cpu_sample(layers, 1.0 / 128)
+    t0 = time.perf_counter(); run(); t1 = time.perf_counter()
+    rate = units / max(t1 - t0, 1e-6)
+    full_units = step_units(layers)
+    frac = min(1.0, max(1.0 / 128, (budget_s * rate) / full_units))
+    run, units = cpu_sample(layers, frac)
+    t0 = time.perf_counter(); run(); t1 = time.perf_counter()
+    return {"value": units / (t1 - t0) / 1e9, "unit": "ring-GMAC/s", "cores": cpu_cores(),
+            "kind": "oracle", "seconds": t1 - t0,
+            "sample": (f"share + full tag at the first {frac:.4f} of output rows of both layers and "
+                       f"both parties, plus the whole CompactTag tag and check of both layers and "
+                       f"parties ({units:.3e} ring MACs)")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    layers = synth.cnn_pair()
+    run, units = cpu_sample(layers, 1.0 / 64)
+    for _ in range(args.warmup):
+        run()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter(); run(); times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = units * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ring-GMAC/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot / args.steps * 1e3, "p99_ms_per_step": pct([t * 1e3 for t in times], 99),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (uniform ring words from seeded SplitMix64)",
+        "config": {"workload": "cnn_im2col_conv3x3_32x32x64_and_dense4096_b128",
+                   "layers": [[L.M, L.K, L.N] for L in layers], "ring": "Z_2^64 (k=32, s=32)",
+                   "parties": PARTIES, "parallelism": "host cores (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "ring-GMAC/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "per step: share + full tag at the first 1/64 of output rows and "
+                                   "the whole CompactTag tag and check, both layers and parties"},
+        "e2e": {"value": value, "unit": "ring-GMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * mpclinear.h -- C ABI of the GB300 library for one party's online
+ * computation of an actively secure SPDZ2k linear layer Z = X . W with
+ * CompactTag (arXiv 2311.04406).
+ *
+ * Notation (§2.2, §2.5): the layer multiplies X (M x K) by W (K x N).  Party i
+ * holds authenticated shares of a Beaver matrix triple (A, B, C = A.B), of a
+ * random mask R (M x N), their tag shares m(A), m(B), m(C), m(R), and a key
+ * share alpha_i.  The public opened matrices are E = X - A (M x K) and
+ * F = W - B (K x N) (the paper calls F "U"), and, for CompactTag, the opened
+ * D~ = sum_i ([R]_i - [Z]_i) (M x N) and the public combiners chi (N) and
+ * chi^ (M).  Party index 0 is the paper's P1.
+ *
+ * Memory: every matrix/vector pointer is DEVICE memory owned by the caller,
+ * row-major, contiguous, 16-byte aligned, `ring.words` little-endian uint64
+ * words per element (Z_2^64: one word; Z_2^128: (lo, hi)).  The library never
+ * allocates or frees: scratch comes from the caller's workspace, sized by
+ * mpc_workspace_size().  All calls are asynchronous on `stream` (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream) and return
+ * after enqueueing.  Arguments are validated on the host before any launch;
+ * invalid arguments return a negative status and launch nothing.  The library
+ * holds no state between calls.
+ *
+ * All arithmetic is exact wrapping integer arithmetic mod 2^(k+s); results are
+ * bit-identical for every launch configuration.
+ */
+#ifndef MPCLINEAR_H
+#define MPCLINEAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Ring parameters (§4.1): (k, s, words) = (32, 32, 1) for Z_2^64 or
+ * (64, 64, 2) for Z_2^128.  k + s must equal 64 * words. */
+typedef struct {
+    int32_t k;
+    int32_t s;
+    int32_t words;
+} mpc_ring;
+
+/* One linear layer for one party.  M, K, N >= 0 (zero-sized layers are valid
+ * no-ops; K = 0 gives Z = C).  party in [0, nparties). */
+typedef struct {
+    int64_t M;
+    int64_t K;
+    int64_t N;
+    mpc_ring ring;
+    int32_t party;
+    int32_t nparties;
+} mpc_layer;
+
+typedef enum { MPC_TAG_FULL = 0, MPC_TAG_COMPACT = 1 } mpc_tag_mode;
+typedef enum { MPC_CHECK_COMPACT = 0, MPC_CHECK_BATCHREC = 1 } mpc_check_mode;
+
+/* `which` argument of mpc_workspace_size */
+enum {
+    MPC_WS_SHARE = 0,
+    MPC_WS_TAG_FULL = 1,
+    MPC_WS_TAG_COMPACT = 2,
+    MPC_WS_CHECK_COMPACT = 3,
+    MPC_WS_CHECK_BATCHREC = 4
+};
+
+/* Status codes */
+#define MPC_OK 0
+#define MPC_E_NULL (-1)        /* a required pointer is NULL */
+#define MPC_E_SHAPE (-2)       /* negative or too large M, K, N */
+#define MPC_E_RING (-3)        /* unsupported (k, s, words) */
+#define MPC_E_ALIGN (-4)       /* a pointer is not 16-byte aligned */
+#define MPC_E_WORKSPACE (-5)   /* workspace NULL or smaller than required */
+#define MPC_E_CUDA (-6)        /* a CUDA launch or runtime error */
+#define MPC_E_MODE (-7)        /* unknown tag/check mode */
+#define MPC_E_PARTY (-8)       /* party index outside [0, nparties) */
+#define MPC_E_TIMEOUT (-9)     /* a device-side wait gave up (status read back) */
+
+/*
+ * a1. Share of Z = X . W from the triple, Eq. (compute-z) and Fig. Pi_MatMul
+ * steps 2-3 (§2.5):
+ *     Z_i = C_i + E . B_i + A_i . F   (+ E . F when layer->party == 0)
+ * E: M x K, F: K x N, A_i: M x K, B_i: K x N, C_i: M x N, Z_i: M x N (output,
+ * may not alias an input).
+ */
+int mpc_linear_share(const mpc_layer *layer,
+                     const uint64_t *E, const uint64_t *F,
+                     const uint64_t *A_i, const uint64_t *B_i, const uint64_t *C_i,
+                     uint64_t *Z_i,
+                     void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Tag share of Z for party i.
+ *
+ * MPC_TAG_FULL -- a2, the SPDZ2k recurrence, Eq. (compute-ztag) (§2.5), with
+ * the alpha term added by every party:
+ *     mZ_i = mC_i + E . mB_i + mA_i . F + alpha_i * (E . F)
+ *   reads E, F, mA_i (M x K), mB_i (K x N), mC_i (M x N); writes mZ_i (M x N).
+ *   mR_i, Dtilde, chi, mDc_i, Dc are ignored (may be NULL).
+ *
+ * MPC_TAG_COMPACT -- CompactTag, §3.2-§3.3 and Fig. Pi_CompactMatMul
+ * steps 6-7 (untruncated layer):
+ *   a3 optimistic tag (Fig. Pi_OptMAC):  mZ_i = mR_i - alpha_i * Dtilde
+ *   a4 compressions (Fig. Pi_Compress): mR_i.chi, Dtilde.chi, mC_i.chi (M),
+ *                                        mB_i.chi, F.chi (K)
+ *   a5 compact tag, Eq. (compute-zcomptag):
+ *       mZc_i = mC_i.chi + E.(mB_i.chi) + mA_i.(F.chi) + alpha_i * E.(F.chi)
+ *       mDc_i = mR_i.chi - mZc_i               (output, M)
+ *       Dc    = Dtilde.chi                     (output, M; the compressed D)
+ *   reads E, F, mA_i, mB_i, mC_i, mR_i (M x N), Dtilde (M x N), chi (N).
+ *
+ * alpha_i: device pointer to one ring element (the key share, §2.4).
+ */
+int mpc_linear_tag(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
+                   const uint64_t *E, const uint64_t *F,
+                   const uint64_t *mA_i, const uint64_t *mB_i, const uint64_t *mC_i,
+                   const uint64_t *mR_i, const uint64_t *Dtilde, const uint64_t *chi,
+                   uint64_t *mZ_i, uint64_t *mDc_i, uint64_t *Dc,
+                   void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * a6. Check share of party i, written to cs_i (device, one ring element).
+ *
+ * MPC_CHECK_COMPACT -- Fig. Pi_CompactMatMul verification steps 3-5, reduced
+ * mod 2^(k+s):  cs_i = sum_r chi_hat_r * (alpha_i * Dc_r - mDc_i_r)
+ *   chi_hat: M, opened = Dc: M, tag_i = mDc_i: M.  Parties accept iff the sum
+ *   of all cs_i is 0 mod 2^(k+s).
+ * MPC_CHECK_BATCHREC -- tag check of Fig. Pi_BatchRec (§2.5) steps 2-3:
+ *   cs_i = sum_{p,q} chi_pq * (mW_i_pq - alpha_i * W_pq)
+ *   chi_hat = chi: M x N, opened = W: M x N, tag_i = mW_i: M x N.
+ */
+int mpc_tag_check(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
+                  const uint64_t *chi_hat, const uint64_t *opened,
+                  const uint64_t *tag_i, uint64_t *cs_i,
+                  void *workspace, size_t ws_bytes, void *stream);
+
+/* Bytes of workspace the call `which` (MPC_WS_*) needs for this layer; 0 for
+ * an invalid layer.  A larger workspace is always accepted. */
+size_t mpc_workspace_size(const mpc_layer *layer, int which);
+
+/* Which ring-GEMM kernel mpc_linear_share / MPC_TAG_FULL use for this layer:
+ * 1 = the tensor-core kernel, 0 = the integer-pipe kernel, negative = invalid
+ * layer (status code).  Pure host query; launches nothing. */
+int mpc_gemm_path(const mpc_layer *layer);
+
+/* Static string for a status code. */
+const char *mpc_status_str(int status);
+
+/* Library ABI version (major * 100 + minor). */
+int mpc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPCLINEAR_H */

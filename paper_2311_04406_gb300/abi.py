@@ -1,0 +1,167 @@
+"""Thin ctypes binding of the C ABI in include/mpclinear.h.
+
+Argument marshalling only: torch tensors supply device pointers and the
+current CUDA stream; every step of the computation runs in the library's
+kernels.  Each function has the C name and raises `MpcError` on a non-zero
+status.  If the shared library is missing, loading raises immediately: there
+is no fallback path.
+
+Tensors hold ring elements as 64-bit words (torch.int64 bit patterns):
+shape (rows, cols) for Z_2^64 and (rows, cols, 2) for Z_2^128 (lo, hi).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+MPC_TAG_FULL, MPC_TAG_COMPACT = 0, 1
+MPC_CHECK_COMPACT, MPC_CHECK_BATCHREC = 0, 1
+MPC_WS_SHARE, MPC_WS_TAG_FULL, MPC_WS_TAG_COMPACT, MPC_WS_CHECK_COMPACT, MPC_WS_CHECK_BATCHREC = range(5)
+
+# the functions include/mpclinear.h declares
+ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_workspace_size",
+                 "mpc_gemm_path", "mpc_status_str", "mpc_version")
+
+
+class mpc_ring(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("s", ctypes.c_int32), ("words", ctypes.c_int32)]
+
+
+class mpc_layer(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("K", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("ring", mpc_ring), ("party", ctypes.c_int32), ("nparties", ctypes.c_int32)]
+
+
+class MpcError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn}: status {status}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmpclinear.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise RuntimeError(f"libmpclinear.so is not built ({path}); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        L = ctypes.POINTER(mpc_layer)
+        lib.mpc_linear_share.argtypes = [L] + [P] * 6 + [P, ctypes.c_size_t, P]
+        lib.mpc_linear_share.restype = ctypes.c_int
+        lib.mpc_linear_tag.argtypes = [L, ctypes.c_int] + [P] * 12 + [P, ctypes.c_size_t, P]
+        lib.mpc_linear_tag.restype = ctypes.c_int
+        lib.mpc_tag_check.argtypes = [L, ctypes.c_int] + [P] * 5 + [P, ctypes.c_size_t, P]
+        lib.mpc_tag_check.restype = ctypes.c_int
+        lib.mpc_workspace_size.argtypes = [L, ctypes.c_int]
+        lib.mpc_workspace_size.restype = ctypes.c_size_t
+        lib.mpc_status_str.argtypes = [ctypes.c_int]
+        lib.mpc_status_str.restype = ctypes.c_char_p
+        lib.mpc_gemm_path.argtypes = [L]
+        lib.mpc_gemm_path.restype = ctypes.c_int
+        lib.mpc_version.argtypes = []
+        lib.mpc_version.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def make_layer(M: int, K: int, N: int, k: int = 32, s: int = 32, party: int = 0,
+               nparties: int = 2) -> mpc_layer:
+    words = (k + s + 63) // 64
+    return mpc_layer(int(M), int(K), int(N), mpc_ring(int(k), int(s), int(words)), int(party),
+                     int(nparties))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        raise MpcError(fn, status, load().mpc_status_str(status).decode())
+
+
+def mpc_status_str(status: int) -> str:
+    return load().mpc_status_str(int(status)).decode()
+
+
+def mpc_version() -> int:
+    return load().mpc_version()
+
+
+def mpc_gemm_path(layer: mpc_layer) -> int:
+    return int(load().mpc_gemm_path(ctypes.byref(layer)))
+
+
+def mpc_workspace_size(layer: mpc_layer, which: int) -> int:
+    return int(load().mpc_workspace_size(ctypes.byref(layer), int(which)))
+
+
+def _ws(layer, which, ws):
+    if ws is not None:
+        return _ptr(ws), ws.numel() * ws.element_size()
+    need = mpc_workspace_size(layer, which)
+    if need == 0:
+        return None, 0
+    import torch
+    buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+    _ws.keep = buf  # lives until the next call that allocates; the stream orders reuse
+    return buf.data_ptr(), need
+
+
+def mpc_linear_share(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None):
+    wp, wb = _ws(layer, MPC_WS_SHARE, ws)
+    _check("mpc_linear_share", load().mpc_linear_share(
+        ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(A_i), _ptr(B_i), _ptr(C_i), _ptr(Z_i),
+        wp, wb, _stream(stream)))
+    return Z_i
+
+
+def mpc_linear_tag(layer, mode, alpha_i, E, F, mA_i, mB_i, mC_i, mZ_i, mR_i=None, Dtilde=None,
+                   chi=None, mDc_i=None, Dc=None, ws=None, stream=None):
+    which = MPC_WS_TAG_FULL if mode == MPC_TAG_FULL else MPC_WS_TAG_COMPACT
+    wp, wb = _ws(layer, which, ws)
+    _check("mpc_linear_tag", load().mpc_linear_tag(
+        ctypes.byref(layer), int(mode), _ptr(alpha_i), _ptr(E), _ptr(F), _ptr(mA_i), _ptr(mB_i),
+        _ptr(mC_i), _ptr(mR_i), _ptr(Dtilde), _ptr(chi), _ptr(mZ_i), _ptr(mDc_i), _ptr(Dc),
+        wp, wb, _stream(stream)))
+    return mZ_i
+
+
+def mpc_tag_check(layer, mode, alpha_i, chi_hat, opened, tag_i, cs_i, ws=None, stream=None):
+    which = MPC_WS_CHECK_COMPACT if mode == MPC_CHECK_COMPACT else MPC_WS_CHECK_BATCHREC
+    wp, wb = _ws(layer, which, ws)
+    _check("mpc_tag_check", load().mpc_tag_check(
+        ctypes.byref(layer), int(mode), _ptr(alpha_i), _ptr(chi_hat), _ptr(opened), _ptr(tag_i),
+        _ptr(cs_i), wp, wb, _stream(stream)))
+    return cs_i

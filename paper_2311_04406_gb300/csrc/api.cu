@@ -1,0 +1,197 @@
+// api.cu -- the C ABI declared in include/mpclinear.h.
+//
+// Every entry point validates its arguments on the host (shapes, ring,
+// pointers, alignment, workspace) and returns a negative status without
+// launching anything when they are invalid, so no kernel ever runs on bad
+// input.  Valid calls enqueue kernels on the caller's stream and return.
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/mpclinear.h"
+#include "kernels.h"
+
+using mpcl::u64;
+
+namespace {
+
+constexpr int64_t kMaxDim = int64_t(1) << 31;     // per dimension
+constexpr int64_t kMaxElems = int64_t(1) << 36;   // per matrix
+
+bool ring_ok(const mpc_ring& r) {
+    return (r.words == 1 || r.words == 2) && r.k >= 1 && r.s >= 1 && r.k + r.s == 64 * r.words;
+}
+
+int check_layer(const mpc_layer* L) {
+    if (!L) return MPC_E_NULL;
+    if (!ring_ok(L->ring)) return MPC_E_RING;
+    if (L->M < 0 || L->K < 0 || L->N < 0) return MPC_E_SHAPE;
+    if (L->M > kMaxDim || L->K > kMaxDim || L->N > kMaxDim) return MPC_E_SHAPE;
+    if (L->M * L->K > kMaxElems || L->K * L->N > kMaxElems || L->M * L->N > kMaxElems)
+        return MPC_E_SHAPE;
+    if (L->nparties < 1 || L->party < 0 || L->party >= L->nparties) return MPC_E_PARTY;
+    return MPC_OK;
+}
+
+// a pointer to `elems` ring elements: NULL allowed only when elems == 0
+int check_ptr(const void* p, int64_t elems) {
+    if (elems == 0) return MPC_OK;
+    if (!p) return MPC_E_NULL;
+    if (reinterpret_cast<uintptr_t>(p) % 16 != 0) return MPC_E_ALIGN;
+    return MPC_OK;
+}
+
+#define CHK(x)                         \
+    do {                               \
+        int _s = (x);                  \
+        if (_s != MPC_OK) return _s;   \
+    } while (0)
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MPC_OK;
+    return MPC_E_CUDA;
+}
+
+size_t gemm_ws(const mpc_layer* L) {
+    if (mpcl::gemm_tc_eligible(L->M, L->K, L->N, L->ring.words))
+        return mpcl::gemm_tc_workspace(L->M, L->K, L->N, L->ring.words);
+    return 0;
+}
+
+int run_gemm(const mpcl::GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (g.M == 0 || g.N == 0) return MPC_OK;
+    if (mpcl::gemm_tc_eligible(g.M, g.K, g.N, g.words)) {
+        if (ws_bytes < mpcl::gemm_tc_workspace(g.M, g.K, g.N, g.words)) return MPC_E_WORKSPACE;
+        return cuda_status(mpcl::launch_gemm_tc(g, ws, ws_bytes, st));
+    }
+    return cuda_status(mpcl::launch_gemm_simt(g, st));
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpc_version(void) { return 100; }
+
+int mpc_gemm_path(const mpc_layer* L) {
+    int st = check_layer(L);
+    if (st != MPC_OK) return st;
+    return mpcl::gemm_tc_eligible(L->M, L->K, L->N, L->ring.words) ? 1 : 0;
+}
+
+const char* mpc_status_str(int s) {
+    switch (s) {
+        case MPC_OK: return "ok";
+        case MPC_E_NULL: return "a required pointer is NULL";
+        case MPC_E_SHAPE: return "invalid shape (negative or too large M, K, N)";
+        case MPC_E_RING: return "unsupported ring: need (k, s, words) with k + s = 64 * words, words 1 or 2";
+        case MPC_E_ALIGN: return "a pointer is not 16-byte aligned";
+        case MPC_E_WORKSPACE: return "workspace missing or smaller than mpc_workspace_size()";
+        case MPC_E_CUDA: return "CUDA launch or runtime error";
+        case MPC_E_MODE: return "unknown tag or check mode";
+        case MPC_E_PARTY: return "party index outside [0, nparties)";
+        case MPC_E_TIMEOUT: return "a device-side wait gave up";
+        default: return "unknown status";
+    }
+}
+
+size_t mpc_workspace_size(const mpc_layer* L, int which) {
+    if (check_layer(L) != MPC_OK) return 0;
+    const int w = L->ring.words;
+    switch (which) {
+        case MPC_WS_SHARE:
+        case MPC_WS_TAG_FULL: return gemm_ws(L);
+        case MPC_WS_TAG_COMPACT: return mpcl::compact_workspace(L->M, L->K, L->N, w);
+        case MPC_WS_CHECK_COMPACT: return 0;
+        case MPC_WS_CHECK_BATCHREC: return mpcl::check_batchrec_workspace(L->M, L->N, w);
+        default: return 0;
+    }
+}
+
+int mpc_linear_share(const mpc_layer* L, const uint64_t* E, const uint64_t* F,
+                     const uint64_t* A_i, const uint64_t* B_i, const uint64_t* C_i,
+                     uint64_t* Z_i, void* ws, size_t ws_bytes, void* stream) {
+    CHK(check_layer(L));
+    const int64_t M = L->M, K = L->K, N = L->N;
+    CHK(check_ptr(E, M * K));
+    CHK(check_ptr(A_i, M * K));
+    CHK(check_ptr(F, K * N));
+    CHK(check_ptr(B_i, K * N));
+    CHK(check_ptr(C_i, M * N));
+    CHK(check_ptr(Z_i, M * N));
+    mpcl::GemmArgs g{M, K, N, L->ring.words,
+                     (const u64*)E, (const u64*)F, (const u64*)A_i, (const u64*)B_i,
+                     (const u64*)C_i, (u64*)Z_i,
+                     L->party == 0 ? mpcl::COEF_ONE : mpcl::COEF_ZERO, nullptr};
+    return run_gemm(g, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mpc_linear_tag(const mpc_layer* L, int mode, const uint64_t* alpha_i,
+                   const uint64_t* E, const uint64_t* F,
+                   const uint64_t* mA_i, const uint64_t* mB_i, const uint64_t* mC_i,
+                   const uint64_t* mR_i, const uint64_t* Dtilde, const uint64_t* chi,
+                   uint64_t* mZ_i, uint64_t* mDc_i, uint64_t* Dc,
+                   void* ws, size_t ws_bytes, void* stream) {
+    CHK(check_layer(L));
+    if (mode != MPC_TAG_FULL && mode != MPC_TAG_COMPACT) return MPC_E_MODE;
+    const int64_t M = L->M, K = L->K, N = L->N;
+    const int w = L->ring.words;
+    CHK(check_ptr(alpha_i, 1));
+    CHK(check_ptr(E, M * K));
+    CHK(check_ptr(mA_i, M * K));
+    CHK(check_ptr(F, K * N));
+    CHK(check_ptr(mB_i, K * N));
+    CHK(check_ptr(mC_i, M * N));
+    CHK(check_ptr(mZ_i, M * N));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == MPC_TAG_FULL) {
+        mpcl::GemmArgs g{M, K, N, w, (const u64*)E, (const u64*)F, (const u64*)mA_i,
+                         (const u64*)mB_i, (const u64*)mC_i, (u64*)mZ_i, mpcl::COEF_ALPHA,
+                         (const u64*)alpha_i};
+        return run_gemm(g, ws, ws_bytes, st);
+    }
+    CHK(check_ptr(mR_i, M * N));
+    CHK(check_ptr(Dtilde, M * N));
+    CHK(check_ptr(chi, N));
+    CHK(check_ptr(mDc_i, M));
+    CHK(check_ptr(Dc, M));
+    const size_t need = mpcl::compact_workspace(M, K, N, w);
+    if (M > 0 && need > 0) {
+        if (!ws || ws_bytes < need) return MPC_E_WORKSPACE;
+        if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
+    }
+    mpcl::CompactArgs c{M, K, N, w, (const u64*)alpha_i, (const u64*)E, (const u64*)F,
+                        (const u64*)mA_i, (const u64*)mB_i, (const u64*)mC_i, (const u64*)mR_i,
+                        (const u64*)Dtilde, (const u64*)chi, (u64*)mZ_i, (u64*)mDc_i, (u64*)Dc};
+    return cuda_status(mpcl::launch_compact(c, ws, ws_bytes, st));
+}
+
+int mpc_tag_check(const mpc_layer* L, int mode, const uint64_t* alpha_i,
+                  const uint64_t* chi_hat, const uint64_t* opened, const uint64_t* tag_i,
+                  uint64_t* cs_i, void* ws, size_t ws_bytes, void* stream) {
+    CHK(check_layer(L));
+    const int64_t M = L->M, N = L->N;
+    const int w = L->ring.words;
+    cudaStream_t st = (cudaStream_t)stream;
+    CHK(check_ptr(alpha_i, 1));
+    CHK(check_ptr(cs_i, 1));
+    if (mode == MPC_CHECK_COMPACT) {
+        CHK(check_ptr(chi_hat, M));
+        CHK(check_ptr(opened, M));
+        CHK(check_ptr(tag_i, M));
+        return cuda_status(mpcl::launch_check_compact(M, w, (const u64*)alpha_i,
+                                                      (const u64*)chi_hat, (const u64*)opened,
+                                                      (const u64*)tag_i, (u64*)cs_i, st));
+    }
+    if (mode != MPC_CHECK_BATCHREC) return MPC_E_MODE;
+    CHK(check_ptr(chi_hat, M * N));
+    CHK(check_ptr(opened, M * N));
+    CHK(check_ptr(tag_i, M * N));
+    const size_t need = mpcl::check_batchrec_workspace(M, N, w);
+    if (!ws || ws_bytes < need) return MPC_E_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(ws) % 16 != 0) return MPC_E_ALIGN;
+    return cuda_status(mpcl::launch_check_batchrec(M, N, w, (const u64*)alpha_i,
+                                                   (const u64*)chi_hat, (const u64*)opened,
+                                                   (const u64*)tag_i, (u64*)cs_i, ws, ws_bytes, st));
+}
+
+}  // extern "C"

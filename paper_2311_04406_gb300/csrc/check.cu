@@ -1,0 +1,117 @@
+// check.cu -- check shares (a6).
+//
+// Compact check, Fig. Pi_CompactMatMul verification steps 3-5 reduced mod
+// 2^(k+s):  cs = sum_r chi^_r (alpha Dc_r - mDc_r).  M values: one block.
+//
+// BatchRec tag check, Fig. Pi_BatchRec (§2.5) steps 2-3:
+//   cs = sum_{p,q} chi_pq (mW_pq - alpha W_pq).  M x N values: a grid of
+// blocks leaves per-block partial sums in the workspace, one block adds them.
+// Wrapping sums mod 2^(64 W) are order independent, so the result is the same
+// for any grid.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpcl {
+
+namespace {
+
+constexpr int NT = 512;
+
+template <int W>
+__device__ typename Elem<W>::T block_sum(typename Elem<W>::T v) {
+    using T = typename Elem<W>::T;
+    __shared__ T sh[NT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if constexpr (W == 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        } else {
+            u64 lo = __shfl_xor_sync(0xffffffffu, (u64)v, o);
+            u64 hi = __shfl_xor_sync(0xffffffffu, (u64)(v >> 64), o);
+            v += (u128)lo | ((u128)hi << 64);
+        }
+    }
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T tot = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NT / 32; ++i) tot += sh[i];
+    return tot;  // valid in thread 0
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) check_compact_kernel(int64_t M, const u64* alpha,
+                                                           const u64* chi_hat, const u64* Dc,
+                                                           const u64* mDc, u64* cs) {
+    using T = typename Elem<W>::T;
+    const T a = ld_elem<W>(alpha, 0);
+    T acc = 0;
+    for (int64_t r = threadIdx.x; r < M; r += NT)
+        acc += ldg_elem<W>(chi_hat, r) * (a * ldg_elem<W>(Dc, r) - ldg_elem<W>(mDc, r));
+    T tot = block_sum<W>(acc);
+    if (threadIdx.x == 0) st_elem<W>(cs, 0, tot);
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) batchrec_partial_kernel(int64_t n, const u64* alpha,
+                                                              const u64* chi, const u64* Wm,
+                                                              const u64* mW, u64* part) {
+    using T = typename Elem<W>::T;
+    const T a = ld_elem<W>(alpha, 0);
+    T acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+        T x = ldg_elem<W>(chi, i);
+        acc += ldg_elem<W>(mW, i) * x - a * (ldg_elem<W>(Wm, i) * x);
+    }
+    T tot = block_sum<W>(acc);
+    if (threadIdx.x == 0) st_elem<W>(part, blockIdx.x, tot);
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) sum_kernel(int64_t n, const u64* part, u64* out) {
+    using T = typename Elem<W>::T;
+    T acc = 0;
+    for (int64_t i = threadIdx.x; i < n; i += NT) acc += ld_elem<W>(part, i);
+    T tot = block_sum<W>(acc);
+    if (threadIdx.x == 0) st_elem<W>(out, 0, tot);
+}
+
+int64_t batchrec_blocks(int64_t n) {
+    int64_t b = (n + NT * 8 - 1) / (NT * 8);
+    if (b < 1) b = 1;
+    if (b > 1216) b = 1216;
+    return b;
+}
+
+}  // namespace
+
+cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u64* chi_hat,
+                                 const u64* Dc, const u64* mDc, u64* cs, cudaStream_t st) {
+    if (words == 1) check_compact_kernel<1><<<1, NT, 0, st>>>(M, alpha, chi_hat, Dc, mDc, cs);
+    else check_compact_kernel<2><<<1, NT, 0, st>>>(M, alpha, chi_hat, Dc, mDc, cs);
+    return cudaGetLastError();
+}
+
+size_t check_batchrec_workspace(int64_t M, int64_t N, int words) {
+    return (size_t)batchrec_blocks(M * N) * 8 * (size_t)words;
+}
+
+cudaError_t launch_check_batchrec(int64_t M, int64_t N, int words, const u64* alpha,
+                                  const u64* chi, const u64* Wm, const u64* mW, u64* cs,
+                                  void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int64_t n = M * N;
+    const int64_t blocks = batchrec_blocks(n);
+    if (ws_bytes < check_batchrec_workspace(M, N, words)) return cudaErrorInvalidValue;
+    u64* part = (u64*)ws;
+    if (words == 1) {
+        batchrec_partial_kernel<1><<<(unsigned)blocks, NT, 0, st>>>(n, alpha, chi, Wm, mW, part);
+        sum_kernel<1><<<1, NT, 0, st>>>(blocks, part, cs);
+    } else {
+        batchrec_partial_kernel<2><<<(unsigned)blocks, NT, 0, st>>>(n, alpha, chi, Wm, mW, part);
+        sum_kernel<2><<<1, NT, 0, st>>>(blocks, part, cs);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mpcl

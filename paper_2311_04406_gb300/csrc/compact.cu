@@ -1,0 +1,271 @@
+// compact.cu -- the CompactTag tag of one party (§3.1-§3.3), HBM-bound.
+//
+//   a3  mZ   = mR - alpha * D~                       (Fig. Pi_OptMAC step 3)
+//   a4  mR.chi, D~.chi, mC.chi (M) ; mB.chi, F.chi (K) (Fig. Pi_Compress)
+//   a5  mZc  = mC.chi + E.(mB.chi) + mA.(F.chi) + alpha * E.(F.chi)
+//       mDc  = mR.chi - mZc,  Dc = D~.chi            (Eq. (compute-zcomptag))
+//
+// Three launches on the caller's stream:
+//   1. rows_kernel   one pass over the five N-wide matrices.  A warp owns a
+//                    (row, column-chunk) task: it streams mR, D~, mC (writing
+//                    mZ on the fly) or mB, F, and leaves per-chunk partial
+//                    dot products with chi in the workspace.  Each input word
+//                    is read from HBM exactly once.
+//   2. finalize_kernel  sums the K-side partials into the vectors mB.chi, F.chi.
+//   3. vec_kernel    one warp per output row: the two M x K GEMVs over E and
+//                    mA against those vectors, then mZc, mDc and Dc.
+// Every sum is a wrapping sum mod 2^(64 W), so the split into chunks does not
+// change any result bit.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpcl {
+
+namespace {
+
+constexpr int WARPS = 8;
+constexpr int NT = WARPS * 32;
+
+template <int W>
+__device__ __forceinline__ typename Elem<W>::T warp_sum(typename Elem<W>::T v) {
+    if constexpr (W == 1) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            u64 lo = (u64)v, hi = (u64)(v >> 64);
+            lo = __shfl_xor_sync(0xffffffffu, lo, o);
+            hi = __shfl_xor_sync(0xffffffffu, hi, o);
+            v += (u128)lo | ((u128)hi << 64);
+        }
+        return v;
+    }
+}
+
+struct Split {
+    int64_t S;    // chunks per row
+    int64_t cw;   // columns per chunk (even)
+};
+
+Split choose_split(int64_t M, int64_t K, int64_t N) {
+    Split sp{1, N < 2 ? 2 : ((N + 1) / 2) * 2};
+    const int64_t rows = M + K;
+    const int64_t want_warps = 152 * 32;
+    if (rows > 0 && rows < want_warps && N > 1024) {
+        int64_t S = (want_warps + rows - 1) / rows;
+        int64_t Smax = (N + 511) / 512;
+        if (S > Smax) S = Smax;
+        if (S < 1) S = 1;
+        int64_t cw = (N + S - 1) / S;
+        cw = ((cw + 63) / 64) * 64;
+        sp.S = (N + cw - 1) / cw;
+        sp.cw = cw;
+    }
+    return sp;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct WsLayout {
+    size_t pmr, pd, pmc, qmb, qf, vmb, vf, total;
+};
+
+WsLayout ws_layout(int64_t M, int64_t K, int64_t N, int words) {
+    Split sp = choose_split(M, K, N);
+    size_t e = 8 * (size_t)words;
+    WsLayout L{};
+    size_t off = 0;
+    L.pmr = off; off += align256(e * M * sp.S);
+    L.pd = off;  off += align256(e * M * sp.S);
+    L.pmc = off; off += align256(e * M * sp.S);
+    L.qmb = off; off += align256(e * K * sp.S);
+    L.qf = off;  off += align256(e * K * sp.S);
+    L.vmb = off; off += align256(e * K);
+    L.vf = off;  off += align256(e * K);
+    L.total = off;
+    return L;
+}
+
+struct RowsParams {
+    int64_t M, K, N, S, cw;
+    const u64 *alpha, *mR, *Dt, *mC, *mB, *F, *chi;
+    u64* mZ;
+    u64 *pmr, *pd, *pmc, *qmb, *qf;
+};
+
+// VEC = 2: two Z_2^64 elements per 16-byte access (needs even N).
+template <int W, int VEC>
+__global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
+    using T = typename Elem<W>::T;
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const int64_t tasksA = p.M * p.S, tasksB = p.K * p.S;
+    if (g >= tasksA + tasksB) return;
+    const bool isA = g < tasksA;
+    const int64_t t = isA ? g : g - tasksA;
+    const int64_t row = t / p.S, s = t % p.S;
+    const int64_t c0 = s * p.cw;
+    int64_t c1 = c0 + p.cw;
+    if (c1 > p.N) c1 = p.N;
+    const T alpha = ld_elem<W>(p.alpha, 0);
+    T s1 = 0, s2 = 0, s3 = 0;
+    if (isA) {
+        const int64_t base = row * p.N;
+        if constexpr (VEC == 2) {
+            for (int64_t c = c0 + 2 * lane; c < c1; c += 64) {
+                ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2*>(p.chi + c));
+                ulonglong2 r = ld_stream2(p.mR + base + c);
+                ulonglong2 d = ld_stream2(p.Dt + base + c);
+                ulonglong2 m = ld_stream2(p.mC + base + c);
+                s1 += r.x * x.x + r.y * x.y;
+                s2 += d.x * x.x + d.y * x.y;
+                s3 += m.x * x.x + m.y * x.y;
+                ulonglong2 z;
+                z.x = r.x - alpha * d.x;
+                z.y = r.y - alpha * d.y;
+                st_stream2(p.mZ + base + c, z);
+            }
+        } else {
+            for (int64_t c = c0 + lane; c < c1; c += 32) {
+                T x = ldg_elem<W>(p.chi, c);
+                T r = ldg_elem<W>(p.mR, base + c);
+                T d = ldg_elem<W>(p.Dt, base + c);
+                T m = ldg_elem<W>(p.mC, base + c);
+                s1 += r * x;
+                s2 += d * x;
+                s3 += m * x;
+                st_elem<W>(p.mZ, base + c, r - alpha * d);
+            }
+        }
+        s1 = warp_sum<W>(s1);
+        s2 = warp_sum<W>(s2);
+        s3 = warp_sum<W>(s3);
+        if (lane == 0) {
+            st_elem<W>(p.pmr, t, s1);
+            st_elem<W>(p.pd, t, s2);
+            st_elem<W>(p.pmc, t, s3);
+        }
+    } else {
+        const int64_t base = row * p.N;
+        if constexpr (VEC == 2) {
+            for (int64_t c = c0 + 2 * lane; c < c1; c += 64) {
+                ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2*>(p.chi + c));
+                ulonglong2 b = ld_stream2(p.mB + base + c);
+                ulonglong2 f = ld_stream2(p.F + base + c);
+                s1 += b.x * x.x + b.y * x.y;
+                s2 += f.x * x.x + f.y * x.y;
+            }
+        } else {
+            for (int64_t c = c0 + lane; c < c1; c += 32) {
+                T x = ldg_elem<W>(p.chi, c);
+                s1 += ldg_elem<W>(p.mB, base + c) * x;
+                s2 += ldg_elem<W>(p.F, base + c) * x;
+            }
+        }
+        s1 = warp_sum<W>(s1);
+        s2 = warp_sum<W>(s2);
+        if (lane == 0) {
+            st_elem<W>(p.qmb, t, s1);
+            st_elem<W>(p.qf, t, s2);
+        }
+    }
+}
+
+template <int W>
+__global__ void finalize_kernel(int64_t K, int64_t S, const u64* qmb, const u64* qf,
+                                u64* vmb, u64* vf) {
+    using T = typename Elem<W>::T;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        T a = 0, b = 0;
+        for (int64_t s = 0; s < S; ++s) {
+            a += ld_elem<W>(qmb, k * S + s);
+            b += ld_elem<W>(qf, k * S + s);
+        }
+        st_elem<W>(vmb, k, a);
+        st_elem<W>(vf, k, b);
+    }
+}
+
+struct VecParams {
+    int64_t M, K, S;
+    const u64 *alpha, *E, *mA, *vmb, *vf, *pmr, *pd, *pmc;
+    u64 *mDc, *Dc;
+};
+
+template <int W>
+__global__ void __launch_bounds__(NT) vec_kernel(VecParams p) {
+    using T = typename Elem<W>::T;
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    if (r >= p.M) return;
+    T e_mb = 0, ma_u = 0, e_u = 0;
+    const int64_t base = r * p.K;
+    for (int64_t k = lane; k < p.K; k += 32) {
+        T e = ldg_elem<W>(p.E, base + k);
+        T ma = ldg_elem<W>(p.mA, base + k);
+        T mb = ld_elem<W>(p.vmb, k);
+        T u = ld_elem<W>(p.vf, k);
+        e_mb += e * mb;
+        ma_u += ma * u;
+        e_u += e * u;
+    }
+    e_mb = warp_sum<W>(e_mb);
+    ma_u = warp_sum<W>(ma_u);
+    e_u = warp_sum<W>(e_u);
+    if (lane == 0) {
+        T mrc = 0, dc = 0, mcc = 0;
+        for (int64_t s = 0; s < p.S; ++s) {
+            mrc += ld_elem<W>(p.pmr, r * p.S + s);
+            dc += ld_elem<W>(p.pd, r * p.S + s);
+            mcc += ld_elem<W>(p.pmc, r * p.S + s);
+        }
+        const T alpha = ld_elem<W>(p.alpha, 0);
+        T mzc = mcc + e_mb + ma_u + alpha * e_u;
+        st_elem<W>(p.mDc, r, mrc - mzc);
+        st_elem<W>(p.Dc, r, dc);
+    }
+}
+
+template <int W>
+cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
+    Split sp = choose_split(a.M, a.K, a.N);
+    WsLayout L = ws_layout(a.M, a.K, a.N, W);
+    RowsParams rp{a.M, a.K, a.N, sp.S, sp.cw, a.alpha, a.mR, a.Dt, a.mC, a.mB, a.F, a.chi, a.mZ,
+                  (u64*)(ws + L.pmr), (u64*)(ws + L.pd), (u64*)(ws + L.pmc),
+                  (u64*)(ws + L.qmb), (u64*)(ws + L.qf)};
+    const int64_t tasks = (a.M + a.K) * sp.S;
+    if (tasks > 0) {
+        const unsigned blocks = (unsigned)((tasks + WARPS - 1) / WARPS);
+        if (W == 1 && (a.N % 2) == 0)
+            rows_kernel<W, 2><<<blocks, NT, 0, st>>>(rp);
+        else
+            rows_kernel<W, 1><<<blocks, NT, 0, st>>>(rp);
+    }
+    if (a.K > 0) {
+        unsigned fb = (unsigned)((a.K + 255) / 256);
+        if (fb > 1024) fb = 1024;
+        finalize_kernel<W><<<fb, 256, 0, st>>>(a.K, sp.S, rp.qmb, rp.qf,
+                                                (u64*)(ws + L.vmb), (u64*)(ws + L.vf));
+    }
+    VecParams vp{a.M, a.K, sp.S, a.alpha, a.E, a.mA, (const u64*)(ws + L.vmb),
+                 (const u64*)(ws + L.vf), rp.pmr, rp.pd, rp.pmc, a.mDc, a.Dc};
+    vec_kernel<W><<<(unsigned)((a.M + WARPS - 1) / WARPS), NT, 0, st>>>(vp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words) {
+    return ws_layout(M, K, N, words).total;
+}
+
+cudaError_t launch_compact(const CompactArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (a.M == 0) return cudaSuccess;
+    if (ws_bytes < compact_workspace(a.M, a.K, a.N, a.words)) return cudaErrorInvalidValue;
+    return a.words == 1 ? run<1>(a, (char*)ws, st) : run<2>(a, (char*)ws, st);
+}
+
+}  // namespace mpcl

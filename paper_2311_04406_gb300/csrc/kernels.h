@@ -1,0 +1,68 @@
+// kernels.h -- internal launcher interface between the C ABI (api.cu) and the
+// kernel files.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpcl {
+
+using u64 = unsigned long long;
+
+// The fused ring GEMM behind both a1 and a2.  With the 2K rewrite
+//   Z = C + [E | X + c E] . [B ; F]
+// a1 (share) uses (X, B, C) = (A_i, B_i, C_i), c = 1 for party 0 else 0, and
+// a2 (full tag) uses (X, B, C) = (mA_i, mB_i, mC_i), c = alpha_i:
+//   C + E.B + (X + cE).F = C + E.B + X.F + c (E.F).
+enum CoefMode { COEF_ZERO = 0, COEF_ONE = 1, COEF_ALPHA = 2 };
+
+struct GemmArgs {
+    int64_t M, K, N;
+    int words;
+    const u64* E;      // M x K
+    const u64* F;      // K x N
+    const u64* X;      // M x K
+    const u64* B;      // K x N
+    const u64* C;      // M x N
+    u64* Z;            // M x N
+    int coef;          // CoefMode
+    const u64* alpha;  // one element (COEF_ALPHA)
+};
+
+cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t st);
+
+// tensor-core ring GEMM (fp16 digit products, exact); returns
+// cudaErrorNotSupported when the shape is not handled by it.
+cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words);
+bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words);
+
+// CompactTag path (a3, a4, a5)
+struct CompactArgs {
+    int64_t M, K, N;
+    int words;
+    const u64* alpha;
+    const u64* E;
+    const u64* F;
+    const u64* mA;
+    const u64* mB;
+    const u64* mC;
+    const u64* mR;
+    const u64* Dt;
+    const u64* chi;
+    u64* mZ;   // M x N
+    u64* mDc;  // M
+    u64* Dc;   // M
+};
+size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words);
+cudaError_t launch_compact(const CompactArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// checks (a6)
+cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u64* chi_hat,
+                                 const u64* Dc, const u64* mDc, u64* cs, cudaStream_t st);
+size_t check_batchrec_workspace(int64_t M, int64_t N, int words);
+cudaError_t launch_check_batchrec(int64_t M, int64_t N, int words, const u64* alpha,
+                                  const u64* chi, const u64* W, const u64* mW, u64* cs,
+                                  void* ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace mpcl
