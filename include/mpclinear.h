@@ -76,6 +76,7 @@ enum {
 #define MPC_E_MODE (-7)        /* unknown tag/check mode */
 #define MPC_E_PARTY (-8)       /* party index outside [0, nparties) */
 #define MPC_E_TIMEOUT (-9)     /* a device-side wait gave up (status read back) */
+#define MPC_E_SCRATCH_LIMIT (-10) /* layer needs more than MPC_NOALLOC_SCRATCH_BYTES */
 
 /*
  * a1. Share of Z = X . W from the triple, Eq. (compute-z) and Fig. Pi_MatMul
@@ -134,6 +135,33 @@ int mpc_tag_check(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
                   const uint64_t *chi_hat, const uint64_t *opened,
                   const uint64_t *tag_i, uint64_t *cs_i,
                   void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Allocation-free variant of mpc_linear_tag(layer, MPC_TAG_COMPACT, ...).  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory -- e.g. a host runtime reaching this library through
+ * a plain C FFI with no CUDA allocator of its own, or a serving process whose
+ * device memory is wholly owned by another framework's pool -- and so cannot
+ * pass a workspace.  Same arguments, results and layouts as the COMPACT tag
+ * call, minus the workspace.
+ *
+ * Scratch comes from one static device array of MPC_NOALLOC_SCRATCH_BYTES
+ * (4 MiB) that every GPU loading this library holds until the process exits.
+ * Layers whose mpc_workspace_size(layer, MPC_WS_TAG_COMPACT) exceeds it are
+ * rejected with MPC_E_SCRATCH_LIMIT before any launch.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose kernels overlap on the GPU (unordered streams) race, so order
+ * them.  Nothing in this call allocates or frees memory.
+ */
+#define MPC_NOALLOC_SCRATCH_BYTES (4u << 20)
+int mpc_linear_tag_compact_noalloc(const mpc_layer *layer, const uint64_t *alpha_i,
+                                   const uint64_t *E, const uint64_t *F,
+                                   const uint64_t *mA_i, const uint64_t *mB_i,
+                                   const uint64_t *mC_i, const uint64_t *mR_i,
+                                   const uint64_t *Dtilde, const uint64_t *chi,
+                                   uint64_t *mZ_i, uint64_t *mDc_i, uint64_t *Dc,
+                                   void *stream);
 
 /* Bytes of workspace the call `which` (MPC_WS_*) needs for this layer; 0 for
  * an invalid layer.  A larger workspace is always accepted. */

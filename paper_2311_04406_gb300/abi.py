@@ -26,7 +26,10 @@ MPC_WS_SHARE, MPC_WS_TAG_FULL, MPC_WS_TAG_COMPACT, MPC_WS_CHECK_COMPACT, MPC_WS_
 
 # the functions include/mpclinear.h declares
 ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_workspace_size",
-                 "mpc_gemm_path", "mpc_status_str", "mpc_version")
+                 "mpc_gemm_path", "mpc_status_str", "mpc_version",
+                 "mpc_linear_tag_compact_noalloc")
+MPC_E_SCRATCH_LIMIT = -10
+MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
 class mpc_ring(ctypes.Structure):
@@ -74,6 +77,8 @@ def load(build_if_missing: bool = False):
         lib.mpc_workspace_size.restype = ctypes.c_size_t
         lib.mpc_status_str.argtypes = [ctypes.c_int]
         lib.mpc_status_str.restype = ctypes.c_char_p
+        lib.mpc_linear_tag_compact_noalloc.argtypes = [L] + [P] * 12 + [P]
+        lib.mpc_linear_tag_compact_noalloc.restype = ctypes.c_int
         lib.mpc_gemm_path.argtypes = [L]
         lib.mpc_gemm_path.restype = ctypes.c_int
         lib.mpc_version.argtypes = []
@@ -165,3 +170,13 @@ def mpc_tag_check(layer, mode, alpha_i, chi_hat, opened, tag_i, cs_i, ws=None, s
         ctypes.byref(layer), int(mode), _ptr(alpha_i), _ptr(chi_hat), _ptr(opened), _ptr(tag_i),
         _ptr(cs_i), wp, wb, _stream(stream)))
     return cs_i
+
+
+def mpc_linear_tag_compact_noalloc(layer, alpha_i, E, F, mA_i, mB_i, mC_i, mR_i, Dtilde, chi,
+                                   mZ_i, mDc_i, Dc, stream=None):
+    """CompactTag tag without a workspace: scratch comes from the library's
+    static device buffer (see include/mpclinear.h for the rules of use)."""
+    _check("mpc_linear_tag_compact_noalloc", load().mpc_linear_tag_compact_noalloc(
+        ctypes.byref(layer), _ptr(alpha_i), _ptr(E), _ptr(F), _ptr(mA_i), _ptr(mB_i), _ptr(mC_i),
+        _ptr(mR_i), _ptr(Dtilde), _ptr(chi), _ptr(mZ_i), _ptr(mDc_i), _ptr(Dc), _stream(stream)))
+    return mZ_i

@@ -90,6 +90,8 @@ const char* mpc_status_str(int s) {
         case MPC_E_MODE: return "unknown tag or check mode";
         case MPC_E_PARTY: return "party index outside [0, nparties)";
         case MPC_E_TIMEOUT: return "a device-side wait gave up";
+        case MPC_E_SCRATCH_LIMIT:
+            return "layer needs more scratch than the static MPC_NOALLOC_SCRATCH_BYTES buffer holds";
         default: return "unknown status";
     }
 }
