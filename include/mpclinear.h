@@ -172,6 +172,17 @@ size_t mpc_workspace_size(const mpc_layer *layer, int which);
  * layer (status code).  Pure host query; launches nothing. */
 int mpc_gemm_path(const mpc_layer *layer);
 
+/* Number of kernels the call `which` (MPC_WS_* numbering) enqueues for this
+ * layer (0 for empty layers); negative status for an invalid layer.  Pure
+ * host query. */
+int mpc_launch_count(const mpc_layer *layer, int which);
+
+/* Synchronous: reads and clears the device flag that a kernel sets when one of
+ * its bounded waits gave up (so that it returned instead of hanging).
+ * Returns MPC_E_TIMEOUT if it was set since the last query, MPC_OK if not,
+ * MPC_E_CUDA if the flag could not be read.  Uses the current device. */
+int mpc_device_status(void);
+
 /* Static string for a status code. */
 const char *mpc_status_str(int status);
 

@@ -26,7 +26,8 @@ MPC_WS_SHARE, MPC_WS_TAG_FULL, MPC_WS_TAG_COMPACT, MPC_WS_CHECK_COMPACT, MPC_WS_
 
 # the functions include/mpclinear.h declares
 ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_workspace_size",
-                 "mpc_gemm_path", "mpc_status_str", "mpc_version",
+                 "mpc_gemm_path", "mpc_launch_count", "mpc_device_status", "mpc_status_str",
+                 "mpc_version",
                  "mpc_linear_tag_compact_noalloc")
 MPC_E_SCRATCH_LIMIT = -10
 MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -79,6 +80,10 @@ def load(build_if_missing: bool = False):
         lib.mpc_status_str.restype = ctypes.c_char_p
         lib.mpc_linear_tag_compact_noalloc.argtypes = [L] + [P] * 12 + [P]
         lib.mpc_linear_tag_compact_noalloc.restype = ctypes.c_int
+        lib.mpc_launch_count.argtypes = [L, ctypes.c_int]
+        lib.mpc_launch_count.restype = ctypes.c_int
+        lib.mpc_device_status.argtypes = []
+        lib.mpc_device_status.restype = ctypes.c_int
         lib.mpc_gemm_path.argtypes = [L]
         lib.mpc_gemm_path.restype = ctypes.c_int
         lib.mpc_version.argtypes = []
@@ -126,6 +131,15 @@ def mpc_version() -> int:
 
 def mpc_gemm_path(layer: mpc_layer) -> int:
     return int(load().mpc_gemm_path(ctypes.byref(layer)))
+
+
+def mpc_launch_count(layer: mpc_layer, which: int) -> int:
+    return int(load().mpc_launch_count(ctypes.byref(layer), int(which)))
+
+
+def mpc_device_status() -> int:
+    """MPC_E_TIMEOUT (-9) if a kernel's bounded wait gave up since the last query."""
+    return int(load().mpc_device_status())
 
 
 def mpc_workspace_size(layer: mpc_layer, which: int) -> int:

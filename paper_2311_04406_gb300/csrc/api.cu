@@ -60,7 +60,8 @@ size_t gemm_ws(const mpc_layer* L) {
 int run_gemm(const mpcl::GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (g.M == 0 || g.N == 0) return MPC_OK;
     if (mpcl::gemm_tc_eligible(g.M, g.K, g.N, g.words)) {
-        if (ws_bytes < mpcl::gemm_tc_workspace(g.M, g.K, g.N, g.words)) return MPC_E_WORKSPACE;
+        if (!ws || ws_bytes < mpcl::gemm_tc_workspace(g.M, g.K, g.N, g.words)) return MPC_E_WORKSPACE;
+        if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
         return cuda_status(mpcl::launch_gemm_tc(g, ws, ws_bytes, st));
     }
     return cuda_status(mpcl::launch_gemm_simt(g, st));
@@ -76,6 +77,29 @@ int mpc_gemm_path(const mpc_layer* L) {
     int st = check_layer(L);
     if (st != MPC_OK) return st;
     return mpcl::gemm_tc_eligible(L->M, L->K, L->N, L->ring.words) ? 1 : 0;
+}
+
+int mpc_launch_count(const mpc_layer* L, int which) {
+    int st = check_layer(L);
+    if (st != MPC_OK) return st;
+    const int64_t M = L->M, K = L->K, N = L->N;
+    const int w = L->ring.words;
+    switch (which) {
+        case MPC_WS_SHARE:
+        case MPC_WS_TAG_FULL:
+            if (M == 0 || N == 0) return 0;
+            return mpcl::gemm_tc_eligible(M, K, N, w) ? mpcl::gemm_tc_launches(M, K, N, w) : 1;
+        case MPC_WS_TAG_COMPACT: return mpcl::compact_launches(M, K, N);
+        case MPC_WS_CHECK_COMPACT: return 1;
+        case MPC_WS_CHECK_BATCHREC: return 2;
+        default: return MPC_E_MODE;
+    }
+}
+
+int mpc_device_status(void) {
+    bool set = false;
+    if (mpcl::tc_timeout_flag(&set) != 0) return MPC_E_CUDA;
+    return set ? MPC_E_TIMEOUT : MPC_OK;
 }
 
 const char* mpc_status_str(int s) {

@@ -258,6 +258,12 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
 
 }  // namespace
 
+int compact_launches(int64_t M, int64_t K, int64_t N) {
+    if (M == 0) return 0;
+    Split sp = choose_split(M, K, N);
+    return ((M + K) * sp.S > 0 ? 1 : 0) + (K > 0 ? 1 : 0) + 1;
+}
+
 size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words) {
     return ws_layout(M, K, N, words).total;
 }

@@ -36,6 +36,8 @@ cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t st);
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words);
 bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words);
+int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words);
+int tc_timeout_flag(bool* set);   // synchronous; 0 on success
 
 // CompactTag path (a3, a4, a5)
 struct CompactArgs {
@@ -55,6 +57,7 @@ struct CompactArgs {
     u64* Dc;   // M
 };
 size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words);
+int compact_launches(int64_t M, int64_t K, int64_t N);
 cudaError_t launch_compact(const CompactArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
 
 // checks (a6)

@@ -1,0 +1,83 @@
+"""Parity of the tensor-core ring GEMM (fp16 digit products on tcgen05).
+
+Shapes are chosen above the library's tensor-core threshold so that the
+tcgen05 kernel runs (checked with mpc_gemm_path): ragged row and column tiles,
+split-K plans and single-pass plans, the share (c = 0 and c = 1) and the full
+tag (c = alpha), and digit patterns at the ends of the signed range -- all
+digits -128 makes every accumulator reach exactly 2^24, the bound the exact
+fp32 accumulation relies on.  Results must equal the oracle bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from oracle import dealer
+from paper_2311_04406_gb300 import abi, build
+
+from gpuhelp import gpu_share, gpu_tag_full
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(130, 256, 70), (300, 640, 96), (128, 32, 1024), (500, 96, 1000), (1, 4096, 512),
+          (257, 1024, 34)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    abi.load()
+
+
+def _path(M, K, N):
+    return abi.mpc_gemm_path(abi.make_layer(M, K, N))
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=str)
+def test_tc_path_parity(shape):
+    M, K, N = shape
+    assert _path(M, K, N) == 1, "shape should take the tensor-core path"
+    d = dealer.deal(synth.Z64, M, K, N, n=2, seed=M * 7 + K)
+    for i, p in enumerate(d.parties):
+        Z = gpu_share(synth.Z64, i, d.E, d.F, p.A, p.B, p.C)
+        assert np.array_equal(Z, O.linear_share(64, i, d.E, d.F, p.A, p.B, p.C)), f"share party {i}"
+        mZ = gpu_tag_full(synth.Z64, i, p.alpha, d.E, d.F, p.mA, p.mB, p.mC)
+        assert np.array_equal(mZ, O.linear_tag_full(64, p.alpha, d.E, d.F, p.mA, p.mB, p.mC)), \
+            f"full tag party {i}"
+    assert abi.mpc_device_status() == 0
+
+
+PATTERNS = [0x7F7F7F7F7F7F7F80,   # every signed digit -128
+            0x7F7F7F7F7F7F7F7F,   # every digit 127
+            0xFFFFFFFFFFFFFFFF, 0x8080808080808080, 0x0000000000000080, 0x0123456789ABCDEF]
+
+
+@pytest.mark.parametrize("pat", PATTERNS, ids=hex)
+@pytest.mark.parametrize("shape", [(130, 256, 70), (128, 1024, 64)], ids=str)
+def test_tc_digit_extremes(pat, shape):
+    M, K, N = shape
+    assert _path(M, K, N) == 1
+    mk = lambda *s: np.full(s, pat, dtype=np.uint64)
+    E, F, A, B, C = mk(M, K), mk(K, N), mk(M, K), mk(K, N), mk(M, N)
+    for party in (0, 1):
+        assert np.array_equal(gpu_share(synth.Z64, party, E, F, A, B, C),
+                              O.linear_share(64, party, E, F, A, B, C))
+    alpha = np.array([pat], dtype=np.uint64)
+    assert np.array_equal(gpu_tag_full(synth.Z64, 1, alpha, E, F, A, B, C),
+                          O.linear_tag_full(64, alpha, E, F, A, B, C))
+    assert abi.mpc_device_status() == 0
+
+
+def test_tc_mixed_extremes():
+    """Rows and columns alternating between the digit extremes, so diagonal
+    sums mix +2^14 and -2^14 products."""
+    M, K, N = 130, 512, 66
+    lo, hi = np.uint64(0x7F7F7F7F7F7F7F80), np.uint64(0x7F7F7F7F7F7F7F7F)
+    a = np.where((np.arange(M * K) % 3) == 0, lo, hi).astype(np.uint64)
+    b = np.where((np.arange(K * N) % 5) == 0, lo, np.uint64(0x8080808080808080)).astype(np.uint64)
+    E, A = a.reshape(M, K), a[::-1].copy().reshape(M, K)
+    F, B = b.reshape(K, N), b[::-1].copy().reshape(K, N)
+    C = synth.uniform(5, 5, 0, (M, N), 64)
+    for party in (0, 1):
+        assert np.array_equal(gpu_share(synth.Z64, party, E, F, A, B, C),
+                              O.linear_share(64, party, E, F, A, B, C))
