@@ -7,7 +7,7 @@
 #include <cstdint>
 #include <cstring>
 
-#include "../../include/mpclinear.h"
+#include "mpclinear.h"
 #include "kernels.h"
 
 using mpcl::u64;

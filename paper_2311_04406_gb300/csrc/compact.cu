@@ -195,27 +195,58 @@ struct VecParams {
     u64 *mDc, *Dc;
 };
 
-template <int W>
-__global__ void __launch_bounds__(NT) vec_kernel(VecParams p) {
+// `wpr` warps share one row (1, 2, 4 or 8), each taking every wpr-th chunk of
+// 32 (or 64, vectorised) K values; their partial sums meet in shared memory.
+template <int W, int VEC>
+__global__ void __launch_bounds__(NT) vec_kernel(VecParams p, int wpr) {
     using T = typename Elem<W>::T;
-    const int lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-    if (r >= p.M) return;
+    __shared__ T part[3][WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows_per_block = WARPS / wpr;
+    const int64_t r = (int64_t)blockIdx.x * rows_per_block + warp / wpr;
+    const int sub = warp % wpr;
     T e_mb = 0, ma_u = 0, e_u = 0;
-    const int64_t base = r * p.K;
-    for (int64_t k = lane; k < p.K; k += 32) {
-        T e = ldg_elem<W>(p.E, base + k);
-        T ma = ldg_elem<W>(p.mA, base + k);
-        T mb = ld_elem<W>(p.vmb, k);
-        T u = ld_elem<W>(p.vf, k);
-        e_mb += e * mb;
-        ma_u += ma * u;
-        e_u += e * u;
+    if (r < p.M) {
+        const int64_t base = r * p.K;
+        if constexpr (VEC == 2) {
+#pragma unroll 4
+            for (int64_t k = 2 * (sub * 32 + lane); k < p.K; k += 64 * wpr) {
+                ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(p.E + base + k));
+                ulonglong2 ma = __ldg(reinterpret_cast<const ulonglong2*>(p.mA + base + k));
+                ulonglong2 mb = *reinterpret_cast<const ulonglong2*>(p.vmb + k);
+                ulonglong2 u = *reinterpret_cast<const ulonglong2*>(p.vf + k);
+                e_mb += e.x * mb.x + e.y * mb.y;
+                ma_u += ma.x * u.x + ma.y * u.y;
+                e_u += e.x * u.x + e.y * u.y;
+            }
+        } else {
+#pragma unroll 4
+            for (int64_t k = sub * 32 + lane; k < p.K; k += 32 * wpr) {
+                T e = ldg_elem<W>(p.E, base + k);
+                T ma = ldg_elem<W>(p.mA, base + k);
+                T mb = ld_elem<W>(p.vmb, k);
+                T u = ld_elem<W>(p.vf, k);
+                e_mb += e * mb;
+                ma_u += ma * u;
+                e_u += e * u;
+            }
+        }
+        e_mb = warp_sum<W>(e_mb);
+        ma_u = warp_sum<W>(ma_u);
+        e_u = warp_sum<W>(e_u);
     }
-    e_mb = warp_sum<W>(e_mb);
-    ma_u = warp_sum<W>(ma_u);
-    e_u = warp_sum<W>(e_u);
     if (lane == 0) {
+        part[0][warp] = e_mb;
+        part[1][warp] = ma_u;
+        part[2][warp] = e_u;
+    }
+    __syncthreads();
+    if (r < p.M && sub == 0 && lane == 0) {
+        for (int j = 1; j < wpr; ++j) {
+            e_mb += part[0][warp + j];
+            ma_u += part[1][warp + j];
+            e_u += part[2][warp + j];
+        }
         T mrc = 0, dc = 0, mcc = 0;
         for (int64_t s = 0; s < p.S; ++s) {
             mrc += ld_elem<W>(p.pmr, r * p.S + s);
@@ -227,6 +258,10 @@ __global__ void __launch_bounds__(NT) vec_kernel(VecParams p) {
         st_elem<W>(p.mDc, r, mrc - mzc);
         st_elem<W>(p.Dc, r, dc);
     }
+}
+
+int vec_warps_per_row(int64_t K) {
+    return K >= 2048 ? 8 : K >= 1024 ? 4 : K >= 256 ? 2 : 1;
 }
 
 template <int W>
@@ -252,7 +287,13 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
     }
     VecParams vp{a.M, a.K, sp.S, a.alpha, a.E, a.mA, (const u64*)(ws + L.vmb),
                  (const u64*)(ws + L.vf), rp.pmr, rp.pd, rp.pmc, a.mDc, a.Dc};
-    vec_kernel<W><<<(unsigned)((a.M + WARPS - 1) / WARPS), NT, 0, st>>>(vp);
+    const int wpr = vec_warps_per_row(a.K);
+    const int64_t rpb = WARPS / wpr;
+    const unsigned vb = (unsigned)((a.M + rpb - 1) / rpb);
+    if (W == 1 && (a.K % 2) == 0)
+        vec_kernel<W, 2><<<vb, NT, 0, st>>>(vp, wpr);
+    else
+        vec_kernel<W, 1><<<vb, NT, 0, st>>>(vp, wpr);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,13 @@
 //     TMEM column block i + j -- the diagonal it belongs to.  Two 256-column
 //     accumulator sets alternate, so draining one overlaps MMAs into the other.
 //   * four drain warps read the diagonals with tcgen05.ld, convert them to
-//     integers and add d_t 2^(8t) into 32 wrapping 64-bit sums per row; at the
-//     end they add C and store Z (or a split-K partial).
+//     integers and add d_t 2^(8t) into 32 wrapping 64-bit sums per row.
+//   * scheduling is persistent: the (output tile, 128-deep K interval) work
+//     units are split evenly over one CTA per SM, so a CTA may cover parts of
+//     two tiles.  The prologue sets Z = C and every CTA adds each finished
+//     tile segment into Z with red.global.add.u64 -- exact and independent of
+//     the order of the additions, because addition mod 2^64 is associative and
+//     commutative.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -95,13 +100,22 @@ __device__ __forceinline__ uint32_t hi32(u64 v) { return (uint32_t)(v >> 32); }
 struct PrologueParams {
     const u64 *E, *X, *alpha;
     int coef;
-    int64_t M, K;
+    int64_t M, K, N;
     int S_tot;     // 2K / KS
     uint8_t* Ap;
+    const u64* C;  // Z = C, the base the GEMM adds its tile segments to
+    u64* Z;
 };
 
 __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    {
+        const int64_t nv = p.M * p.N / 2;   // N is even
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C);
+        ulonglong2* z2 = reinterpret_cast<ulonglong2*>(p.Z);
+        for (int64_t i = id; i < nv; i += stride) z2[i] = __ldg(c2 + i);
+    }
     const int64_t per_tile = (int64_t)p.S_tot * 256;
     const int64_t m_tiles = (p.M + BM - 1) / BM;
     if (id >= m_tiles * per_tile) return;
@@ -172,14 +186,35 @@ __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
 
 struct TcParams {
     const uint8_t* Ap;
-    const u64* C;
     u64* Z;
-    u64* part;
     int64_t M, K, N;
-    int S_tot;
-    int per;
-    int nsplit;
+    int S_tot;       // 16-deep stages per tile (2K / 16)
+    int I;           // 128-deep intervals per tile
+    int64_t n_tiles;
+    int64_t U;       // work units = tiles x I
 };
+
+// The work units [u0, u1) of this CTA; unit u is interval u % I of tile u / I.
+struct Unit {
+    int64_t tile;
+    int ii;          // interval within the tile
+    int nst;         // stages in this interval (8, or fewer at the end of K)
+    bool flush;      // last unit of a segment: add the sums into Z
+};
+
+__device__ __forceinline__ Unit unit_of(const TcParams& p, int64_t u, int64_t u1) {
+    Unit x;
+    x.tile = u / p.I;
+    x.ii = (int)(u % p.I);
+    const int s_begin = x.ii * KD_STAGES;
+    x.nst = min(KD_STAGES, p.S_tot - s_begin);
+    x.flush = (u + 1 == u1) || (x.ii == p.I - 1);
+    return x;
+}
+
+__device__ __forceinline__ void red_add_u64(u64* p, u64 v) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
     *abort_flag = 1;
@@ -205,12 +240,9 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tile = blockIdx.x, m_tile = blockIdx.y, split = blockIdx.z;
-    const int s0 = split * p.per;
-    const int s1 = min(p.S_tot, s0 + p.per);
-    const int ns = s1 - s0;
-    const int nint = (ns + KD_STAGES - 1) / KD_STAGES;
-    const int n0 = n_tile * ND;
+    const int64_t u0 = (int64_t)blockIdx.x * p.U / gridDim.x;
+    const int64_t u1 = (int64_t)(blockIdx.x + 1) * p.U / gridDim.x;
+    const int nv = (int)(u1 - u0);   // intervals of this CTA
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -239,18 +271,24 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
     const uint32_t tmem = *tmem_slot;
 
     if (warp == W_APROD) {
-        if (lane == 0 && ns > 0) {
-            const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + s0) * A_STAGE_BYTES;
+        if (lane == 0) {
             int it = 0;
-            for (; it < ns; ++it) {
-                const int s = it % STAGES;
-                if (!ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
-                    record_timeout(abort_flag);
-                    break;
+            bool ok = true;
+            for (int v = 0; v < nv && ok; ++v) {
+                const Unit x = unit_of(p, u0 + v, u1);
+                const int64_t m_tile = x.tile / p.n_tiles;
+                const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + x.ii * KD_STAGES) * A_STAGE_BYTES;
+                for (int j = 0; j < x.nst; ++j, ++it) {
+                    const int s = it % STAGES;
+                    if (!ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
+                        record_timeout(abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    ptx::mbar_arrive_expect_tx(&full[s], A_STAGE_BYTES);
+                    ptx::bulk_g2s(sA + s * A_STAGE_BYTES, src + (size_t)j * A_STAGE_BYTES, A_STAGE_BYTES,
+                                  &full[s]);
                 }
-                ptx::mbar_arrive_expect_tx(&full[s], A_STAGE_BYTES);
-                ptx::bulk_g2s(sA + s * A_STAGE_BYTES, src + (size_t)it * A_STAGE_BYTES, A_STAGE_BYTES,
-                              &full[s]);
             }
             // copies still in flight (only possible after a timeout) must land
             // before the CTA's shared memory is released
@@ -258,22 +296,28 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                 ptx::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, abort_flag, WAIT_LIMIT);
         }
     } else if (warp == W_BPROD) {
-        if (lane == 0 && ns > 0) {
+        if (lane == 0) {
             ptx::prefetch_tmap(&tmB);
             ptx::prefetch_tmap(&tmF);
             int it = 0;
-            for (; it < ns; ++it) {
-                const int r = it % RAW;
-                if (!ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
-                    record_timeout(abort_flag);
-                    break;
+            bool ok = true;
+            for (int v = 0; v < nv && ok; ++v) {
+                const Unit x = unit_of(p, u0 + v, u1);
+                const int n0 = (int)(x.tile % p.n_tiles) * ND;
+                for (int j = 0; j < x.nst; ++j, ++it) {
+                    const int r = it % RAW;
+                    if (!ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
+                        record_timeout(abort_flag);
+                        ok = false;
+                        break;
+                    }
+                    ptx::mbar_arrive_expect_tx(&rawFull[r], RAW_BYTES);
+                    const int64_t kv0 = (int64_t)(x.ii * KD_STAGES + j) * KS;
+                    if (kv0 < p.K)
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, n0, (int)kv0, &rawFull[r]);
+                    else
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, n0, (int)(kv0 - p.K), &rawFull[r]);
                 }
-                ptx::mbar_arrive_expect_tx(&rawFull[r], RAW_BYTES);
-                const int64_t kv0 = (int64_t)(s0 + it) * KS;
-                if (kv0 < p.K)
-                    ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, n0, (int)kv0, &rawFull[r]);
-                else
-                    ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, n0, (int)(kv0 - p.K), &rawFull[r]);
             }
             for (int j = max(0, it - RAW); j < it; ++j)
                 ptx::mbar_wait(&rawFull[j % RAW], (j / RAW) & 1, abort_flag, WAIT_LIMIT);
@@ -283,7 +327,9 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
         const int n8 = lane & 7, half = (lane >> 3) & 1, kg = lane >> 4;
         const int ncol = cw * 8 + n8;               // column within the tile
         const int krow = kg * 8 + half * 4;         // first of 4 K rows
-        for (int it = 0; it < ns; ++it) {
+        int total = 0;
+        for (int v = 0; v < nv; ++v) total += unit_of(p, u0 + v, u1).nst;
+        for (int it = 0; it < total; ++it) {
             const int r = it % RAW;
             if (!ptx::mbar_wait(&rawFull[r], (it / RAW) & 1, abort_flag, WAIT_LIMIT)) {
                 record_timeout(abort_flag);
@@ -293,6 +339,10 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
             u64 x[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) x[e] = raw[(krow + e) * ND + ncol] + DIGIT_BIAS;
+            // the next TMA write into this slot is an async-proxy access: order
+            // these generic-proxy reads before it (without this fence the TMA
+            // overwrote tiles still being read, measured on GB300)
+            ptx::fence_proxy_async_smem();
             ptx::mbar_arrive(&rawEmpty[r]);
             const int s = it % STAGES;
             if (!ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
@@ -318,38 +368,39 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
             ptx::mbar_arrive(&full[s]);
         }
     } else if (warp == W_MMA) {
-        if (lane == 0 && ns > 0) {
+        if (lane == 0) {
             const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
             bool ok = true;
-            for (int it = 0; it < ns && ok; ++it) {
-                const int v = it / KD_STAGES, set = v & 1;
-                const bool first = (it % KD_STAGES) == 0;
-                if (first) {
-                    if (!ptx::mbar_wait(&accEmpty[set], ((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
+            int it = 0;
+            for (int v = 0; v < nv && ok; ++v) {
+                const Unit x = unit_of(p, u0 + v, u1);
+                const int set = v & 1;
+                if (!ptx::mbar_wait(&accEmpty[set], ((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
+                    record_timeout(abort_flag);
+                    break;
+                }
+                ptx::tc_fence_after();
+                for (int j = 0; j < x.nst; ++j, ++it) {
+                    const int s = it % STAGES;
+                    if (!ptx::mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT)) {
                         record_timeout(abort_flag);
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                }
-                const int s = it % STAGES;
-                if (!ptx::mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT)) {
-                    record_timeout(abort_flag);
-                    ok = false;
-                    break;
-                }
-                ptx::tc_fence_after();
-                const uint64_t bdesc = ptx::smem_desc_kmajor(bBase + s * B_STAGE_BYTES, CORE_LBO, CORE_SBO);
+                    const uint64_t bdesc =
+                        ptx::smem_desc_kmajor(bBase + s * B_STAGE_BYTES, CORE_LBO, CORE_SBO);
 #pragma unroll
-                for (int i = 0; i < NDIG; ++i) {
-                    const uint64_t adesc = ptx::smem_desc_kmajor(
-                        aBase + s * A_STAGE_BYTES + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
-                    const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
-                    ptx::mma_f16(tmem + set * (NDIG * ND) + i * ND, adesc, bdesc, idesc,
-                                 (first && i == 0) ? 0u : 1u);
+                    for (int i = 0; i < NDIG; ++i) {
+                        const uint64_t adesc = ptx::smem_desc_kmajor(
+                            aBase + s * A_STAGE_BYTES + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
+                        const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
+                        ptx::mma_f16(tmem + set * (NDIG * ND) + i * ND, adesc, bdesc, idesc,
+                                     (j == 0 && i == 0) ? 0u : 1u);
+                    }
+                    ptx::mma_commit(&empty[s]);
                 }
-                ptx::mma_commit(&empty[s]);
-                if ((it % KD_STAGES) == KD_STAGES - 1 || it == ns - 1) ptx::mma_commit(&accFull[set]);
+                ptx::mma_commit(&accFull[set]);
             }
             // all MMAs of this CTA complete before TMEM is released
             ptx::mma_commit(mmaDone);
@@ -362,13 +413,12 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
         u64 sum[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
-        bool ok = true;
-        for (int v = 0; v < nint; ++v) {
+        for (int v = 0; v < nv; ++v) {
+            const Unit x = unit_of(p, u0 + v, u1);
             const int set = v & 1;
             bool got = ptx::mbar_wait(&accFull[set], (v >> 1) & 1, abort_flag, WAIT_LIMIT);
             if (!__all_sync(0xffffffffu, got)) {
                 if (lane == 0) record_timeout(abort_flag);
-                ok = false;
                 break;
             }
             ptx::tc_fence_after();
@@ -388,41 +438,19 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                     sum[c] += (u64)d << (8 * t);
                 }
             }
-        }
-        const int64_t m = (int64_t)m_tile * BM + row;
-        if (ok && m < p.M) {
-            if (p.nsplit == 1) {
-                const u64* crow = p.C + m * p.N + n0;
-                u64* zrow = p.Z + m * p.N + n0;
-                if (n0 + ND <= p.N) {
-#pragma unroll
-                    for (int c = 0; c < ND; c += 2) {
-                        ulonglong2 cv = __ldg(reinterpret_cast<const ulonglong2*>(crow + c));
-                        ulonglong2 o;
-                        o.x = cv.x + sum[c];
-                        o.y = cv.y + sum[c + 1];
-                        *reinterpret_cast<ulonglong2*>(zrow + c) = o;
-                    }
-                } else {
+            if (x.flush) {
+                const int64_t m = (x.tile / p.n_tiles) * BM + row;
+                const int64_t n0 = (x.tile % p.n_tiles) * ND;
+                if (m < p.M) {
+                    u64* zrow = p.Z + m * p.N + n0;
+                    const int64_t rem = p.N - n0;
+                    const int ncols = rem < ND ? (int)rem : ND;
 #pragma unroll
                     for (int c = 0; c < ND; ++c)
-                        if (n0 + c < p.N) zrow[c] = crow[c] + sum[c];
+                        if (c < ncols) red_add_u64(zrow + c, sum[c]);
                 }
-            } else {
-                u64* prow = p.part + ((int64_t)split * p.M + m) * p.N + n0;
-                if (n0 + ND <= p.N) {
 #pragma unroll
-                    for (int c = 0; c < ND; c += 2) {
-                        ulonglong2 o;
-                        o.x = sum[c];
-                        o.y = sum[c + 1];
-                        *reinterpret_cast<ulonglong2*>(prow + c) = o;
-                    }
-                } else {
-#pragma unroll
-                    for (int c = 0; c < ND; ++c)
-                        if (n0 + c < p.N) prow[c] = sum[c];
-                }
+                for (int c = 0; c < ND; ++c) sum[c] = 0;
             }
         }
     }
@@ -432,24 +460,14 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
     if (warp == W_APROD) ptx::tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// split-K: Z = C + sum of the partial products
-__global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t MN, int nsplit, const u64* C,
-                                                            const u64* part, u64* Z) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        u64 acc = __ldg(C + i);
-        for (int s = 0; s < nsplit; ++s) acc += part[(int64_t)s * MN + i];
-        Z[i] = acc;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // host side
 
 struct Plan {
     int64_t m_tiles, n_tiles;
-    int S_tot, per, nsplit;
-    size_t ap_bytes, part_bytes;
+    int S_tot, I;
+    int64_t U;
+    size_t ap_bytes;
 };
 
 Plan make_plan(int64_t M, int64_t K, int64_t N) {
@@ -457,22 +475,17 @@ Plan make_plan(int64_t M, int64_t K, int64_t N) {
     pl.m_tiles = (M + BM - 1) / BM;
     pl.n_tiles = (N + ND - 1) / ND;
     pl.S_tot = (int)(2 * K / KS);
-    const int64_t tiles = pl.m_tiles * pl.n_tiles;
-    int nsplit = 1;
-    if (tiles < 120) {
-        int64_t want = 148 / tiles;
-        int64_t maxs = pl.S_tot / KD_STAGES;
-        if (maxs < 1) maxs = 1;
-        nsplit = (int)(want < maxs ? want : maxs);
-        if (nsplit < 1) nsplit = 1;
-    }
-    int per = (pl.S_tot + nsplit - 1) / nsplit;
-    per = ((per + KD_STAGES - 1) / KD_STAGES) * KD_STAGES;
-    pl.per = per;
-    pl.nsplit = (pl.S_tot + per - 1) / per;
+    pl.I = (pl.S_tot + KD_STAGES - 1) / KD_STAGES;
+    pl.U = pl.m_tiles * pl.n_tiles * pl.I;
     pl.ap_bytes = (size_t)pl.m_tiles * pl.S_tot * A_STAGE_BYTES;
-    pl.part_bytes = pl.nsplit > 1 ? (size_t)pl.nsplit * M * N * 8 : 0;
     return pl;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+    return n;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -519,43 +532,34 @@ bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
 
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words) {
     if (!gemm_tc_eligible(M, K, N, words)) return 0;
-    Plan pl = make_plan(M, K, N);
-    return align256(pl.ap_bytes) + align256(pl.part_bytes);
+    return align256(make_plan(M, K, N).ap_bytes);
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (!gemm_tc_eligible(a.M, a.K, a.N, a.words)) return cudaErrorNotSupported;
     Plan pl = make_plan(a.M, a.K, a.N);
-    if (ws_bytes < align256(pl.ap_bytes) + align256(pl.part_bytes) || ws == nullptr)
-        return cudaErrorInvalidValue;
+    if (ws_bytes < align256(pl.ap_bytes) || ws == nullptr) return cudaErrorInvalidValue;
     uint8_t* Ap = static_cast<uint8_t*>(ws);
-    u64* part = reinterpret_cast<u64*>(Ap + align256(pl.ap_bytes));
 
     CUtensorMap tmB, tmF;
     if (!make_map(&tmB, a.B, a.K, a.N) || !make_map(&tmF, a.F, a.K, a.N)) return cudaErrorInvalidValue;
 
-    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, pl.S_tot, Ap};
+    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, a.N, pl.S_tot, Ap, a.C, a.Z};
     const int64_t pth = pl.m_tiles * pl.S_tot * 256;
     prologue_kernel<<<(unsigned)((pth + 255) / 256), 256, 0, st>>>(pp);
 
     cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    TcParams tp{Ap, a.C, a.Z, part, a.M, a.K, a.N, pl.S_tot, pl.per, pl.nsplit};
-    dim3 grid((unsigned)pl.n_tiles, (unsigned)pl.m_tiles, (unsigned)pl.nsplit);
-    ring_gemm_tc_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(tmB, tmF, tp);
-    if (pl.nsplit > 1) {
-        const int64_t MN = a.M * a.N;
-        int64_t blocks = (MN + 255) / 256;
-        if (blocks > 4096) blocks = 4096;
-        splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(MN, pl.nsplit, a.C, part, a.Z);
-    }
+    TcParams tp{Ap, a.Z, a.M, a.K, a.N, pl.S_tot, pl.I, pl.n_tiles, pl.U};
+    const int64_t grid = pl.U < sm_count() ? pl.U : sm_count();
+    ring_gemm_tc_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(tmB, tmF, tp);
     return cudaGetLastError();
 }
 
 int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words) {
     if (!gemm_tc_eligible(M, K, N, words)) return 0;
-    return make_plan(M, K, N).nsplit > 1 ? 3 : 2;
+    return 2;
 }
 
 // Reads and clears the device flag that a bounded wait sets when it gives up.

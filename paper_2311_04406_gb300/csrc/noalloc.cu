@@ -28,7 +28,7 @@
 #include <cstdint>
 #include <mutex>
 
-#include "../../include/mpclinear.h"
+#include "mpclinear.h"
 #include "kernels.h"
 
 namespace {

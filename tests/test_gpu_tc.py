@@ -81,3 +81,26 @@ def test_tc_mixed_extremes():
     for party in (0, 1):
         assert np.array_equal(gpu_share(synth.Z64, party, E, F, A, B, C),
                               O.linear_share(64, party, E, F, A, B, C))
+
+
+def test_tc_repeated_runs_stable():
+    """Many consecutive runs of a layer whose work units span tile boundaries
+    on every SM: every run must equal the oracle (guards the pipeline's
+    cross-proxy ordering, whose absence corrupted a few tiles per run)."""
+    M, K, N = 128, 2048, 4096
+    assert _path(M, K, N) == 1
+    g = lambda name, shape: synth.uniform(99, synth.TID[name], 0, shape, 64)
+    E, F, A, B, C = g("E", (M, K)), g("F", (K, N)), g("A", (M, K)), g("B", (K, N)), g("C", (M, N))
+    rows = np.repeat(np.array([3, 70, 127]), N).astype(np.int64)
+    cols = np.tile(np.arange(N), 3).astype(np.int64)
+    want = O.linear_share_at(64, 0, E, F, A, B, C, rows, cols)
+    import torch
+    from gpuhelp import dev, empty_like_ring, host
+    L = abi.make_layer(M, K, N, 32, 32, 0, 2)
+    d = [dev(a) for a in (E, F, A, B, C)]
+    ws = torch.empty(abi.mpc_workspace_size(L, abi.MPC_WS_SHARE), dtype=torch.uint8, device="cuda")
+    for rep in range(60):
+        Z = empty_like_ring((M, N), 1)
+        abi.mpc_linear_share(L, *d, Z, ws=ws)
+        assert np.array_equal(host(Z)[rows, cols], want), f"run {rep}"
+    assert abi.mpc_device_status() == 0
