@@ -1,41 +1,45 @@
-// gemm_tc.cu -- exact ring GEMM mod 2^64 on the fp16 tensor cores (tcgen05).
+// gemm_tc.cu -- exact ring GEMM mod 2^64 and mod 2^128 on the fp16 tensor
+// cores (tcgen05).
 //
-// Computes Z = C + L . R mod 2^64 with L = [E | X + cE] (M x 2K) and
+// Computes Z = C + L . R mod 2^(64 W) with L = [E | X + cE] (M x 2K) and
 // R = [B ; F] (2K x N): the 2K form of Eq. (compute-z) and Eq. (compute-ztag)
-// (§2.5) shared by the share and the full tag.
+// (§2.5) shared by the share and the full tag.  W = 1 is Z_2^64, W = 2 is
+// Z_2^128 (two 64-bit words per element, (lo, hi)).
 //
-// Exactness.  sm_103a has no int8 MMA, so every 64-bit word x is written as
-// eight signed byte digits d_t in [-128, 127] with x = sum_t d_t 2^(8t) mod
-// 2^64 (add 0x80 to every byte mod 2^64, subtract 128 from each byte; the carry
-// out of the top byte vanishes mod 2^64).  Digits are exact in fp16, and
-//     L.R mod 2^64 = sum_{i+j<=7} (L_i . R_j) 2^(8(i+j)),
-// 36 digit products.  Products of digits are at most 2^14 in magnitude, so a
-// diagonal accumulator sum_{i+j=t} L_i . R_j over 128 K values holds at most
-// (t+1) * 128 * 2^14 <= 2^24 in magnitude: every partial sum is an integer
-// exactly representable in fp32, so the fp32 tensor-core accumulation is exact.
-// Every 128 K the accumulators are drained to integers and folded into wrapping
-// 64-bit sums.
+// Exactness.  sm_103a has no int8 MMA, so every ring element x is written as
+// D = 8 W signed byte digits d_t in [-128, 127] with x = sum_t d_t 2^(8t) mod
+// 2^(64 W) (add 0x80 to every byte mod 2^(64 W), subtract 128 from each byte;
+// the carry out of the top byte vanishes mod 2^(64 W)).  Digits are exact in
+// fp16, and
+//     L.R mod 2^(64 W) = sum_{i+j<D} (L_i . R_j) 2^(8(i+j)),
+// D (D + 1) / 2 digit products (36 for Z_2^64, 136 for Z_2^128).  A product of
+// two digits is at most 2^14 in magnitude, so the diagonal accumulator
+// sum_{i+j=t} L_i . R_j over Kd K values holds at most D * Kd * 2^14 = 2^24
+// for Kd = 128 (W = 1) or Kd = 64 (W = 2): every partial sum is an integer
+// exactly representable in fp32, so the fp32 tensor-core accumulation is
+// exact.  Every Kd the accumulators are drained to integers and folded into
+// wrapping sums of 64 W bits.
 //
-// Kernel layout (one CTA = 128 rows x 32 output columns x a K range):
-//   * prologue_kernel writes L as 8 fp16 digit planes in exactly the shared
+// Kernel layout (one CTA per SM; output tiles of 128 rows x ND columns):
+//   * prologue_kernel writes L as D fp16 digit planes in exactly the shared
 //     memory image the MMA reads (K-major, no swizzle, 8x16-byte core
-//     matrices), one 32 KB block per (128-row tile, 16-deep K stage), so the
-//     GEMM fetches each A stage with a single bulk TMA copy.
-//   * the GEMM streams raw 64-bit R tiles (16 K x 32 N) with 2-D TMA; four
+//     matrices), one block per (128-row tile, 16-deep K stage), so the GEMM
+//     fetches each A stage with a single bulk TMA copy.  It also sets Z = C.
+//   * the GEMM streams raw R tiles (16 K x ND elements) with 2-D TMA; four
 //     converter warps turn each into a stacked B operand of 256 rows: rows
-//     32j..32j+31 hold digit plane j of the 32 columns.
-//   * one thread issues, per 16-deep K step, 8 MMAs: D[:, 32i : 256] +=
-//     L_i . [R_0 | ... | R_{7-i}], so that the product L_i . R_j lands in
-//     TMEM column block i + j -- the diagonal it belongs to.  Two 256-column
-//     accumulator sets alternate, so draining one overlaps MMAs into the other.
+//     ND j .. ND j + ND - 1 hold digit plane j of the ND columns.
+//   * one thread issues, per 16-deep K step, D MMAs:
+//     acc[:, ND i : 256] += L_i . [R_0 | ... | R_{D-1-i}], so that the product
+//     L_i . R_j lands in TMEM column block i + j -- the diagonal it belongs to.
+//     Two 256-column accumulator sets alternate, so draining one overlaps
+//     MMAs into the other.
 //   * four drain warps read the diagonals with tcgen05.ld, convert them to
-//     integers and add d_t 2^(8t) into 32 wrapping 64-bit sums per row.
-//   * scheduling is persistent: the (output tile, 128-deep K interval) work
-//     units are split evenly over one CTA per SM, so a CTA may cover parts of
-//     two tiles.  The prologue sets Z = C and every CTA adds each finished
-//     tile segment into Z with red.global.add.u64 -- exact and independent of
-//     the order of the additions, because addition mod 2^64 is associative and
-//     commutative.
+//     integers and add d_t 2^(8t) into wrapping sums, one per output column.
+//   * scheduling is persistent: the (output tile, Kd-deep K interval) work
+//     units are split evenly over the CTAs, so a CTA may cover parts of two
+//     tiles.  Each finished tile segment is added into Z with global atomics:
+//     exact and independent of the order of the additions, because addition
+//     mod 2^(64 W) is associative and commutative.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -49,33 +53,50 @@ __device__ unsigned int g_tc_timeout = 0;
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// configuration per ring width
+
+template <int W> struct Cfg;
+template <> struct Cfg<1> {
+    static constexpr int NDIG = 8;     // digits per element
+    static constexpr int ND = 32;      // output columns per tile
+    static constexpr int KD = 8;       // stages per drain interval (Kd = 128)
+    static constexpr int STAGES = 4;   // operand stages in shared memory
+};
+template <> struct Cfg<2> {
+    static constexpr int NDIG = 16;
+    static constexpr int ND = 16;
+    static constexpr int KD = 4;       // Kd = 64
+    static constexpr int STAGES = 2;
+};
+
 constexpr int BM = 128;                  // rows per tile (TMEM lanes)
-constexpr int ND = 32;                   // output columns per tile
-constexpr int NDIG = 8;                  // byte digits per 64-bit word
-constexpr int NSTACK = NDIG * ND;        // rows of the stacked B operand
-constexpr int KS = 16;                   // K per pipeline stage (one MMA K step)
-constexpr int STAGES = 4;                // operand stages in shared memory
+constexpr int KS = 16;                   // K per stage (one MMA K step)
+constexpr int NSTACK = 256;              // rows of the stacked B operand (NDIG * ND)
 constexpr int RAW = 8;                   // raw R tiles in flight
-constexpr int KD_STAGES = 8;             // stages per drain interval (128 K)
 constexpr uint32_t A_PLANE_BYTES = BM * KS * 2;            // 4 KB
-constexpr uint32_t A_STAGE_BYTES = NDIG * A_PLANE_BYTES;   // 32 KB
 constexpr uint32_t B_STAGE_BYTES = NSTACK * KS * 2;        // 8 KB
-constexpr uint32_t RAW_BYTES = KS * ND * 8;                // 4 KB
+constexpr uint32_t RAW_BYTES = 4096;                       // 16 K x (ND * W) words
 constexpr uint32_t CORE_LBO = 128;       // next core matrix along K
 constexpr uint32_t CORE_SBO = 256;       // next group of 8 rows
-constexpr uint32_t TMEM_COLS = 512;      // two accumulator sets of 8 x 32 columns
+constexpr uint32_t TMEM_COLS = 512;      // two accumulator sets of 256 columns
 constexpr int NUM_WARPS = 11;
 constexpr int NTHREADS = NUM_WARPS * 32;
 constexpr int W_APROD = 0, W_CONV0 = 1, W_MMA = 5, W_BPROD = 10;   // warps 6-9 drain
 constexpr int NCONV = 128;               // converter threads
 constexpr int NDRAIN = 128;              // drain threads
 constexpr long long WAIT_LIMIT = 4000000000LL;   // clock cycles (about 2 s)
+constexpr int NBARS = 2 * 4 + 2 * RAW + 2 + 2 + 1;
 
-constexpr uint32_t OFF_B = STAGES * A_STAGE_BYTES;
-constexpr uint32_t OFF_RAW = OFF_B + STAGES * B_STAGE_BYTES;
-constexpr uint32_t OFF_BAR = OFF_RAW + RAW * RAW_BYTES;
-constexpr int NBARS = 2 * STAGES + 2 * RAW + 2 + 2 + 1;
-constexpr uint32_t SMEM_BYTES = OFF_BAR + NBARS * 8 + 16;
+template <int W> struct Layout {
+    static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE_BYTES;
+    static constexpr uint32_t OFF_B = Cfg<W>::STAGES * A_STAGE;
+    static constexpr uint32_t OFF_RAW = OFF_B + Cfg<W>::STAGES * B_STAGE_BYTES;
+    static constexpr uint32_t OFF_BAR = OFF_RAW + RAW * RAW_BYTES;
+    static constexpr uint32_t SMEM = OFF_BAR + NBARS * 8 + 16;
+};
+static_assert(Cfg<1>::NDIG * Cfg<1>::ND == NSTACK && Cfg<2>::NDIG * Cfg<2>::ND == NSTACK, "stack");
+static_assert(Layout<1>::SMEM <= 227 * 1024 && Layout<2>::SMEM <= 227 * 1024, "smem");
 
 constexpr unsigned long long DIGIT_BIAS = 0x8080808080808080ULL;
 constexpr uint32_t F16_1152X2 = 0x64806480u;   // fp16 (1152, 1152)
@@ -91,11 +112,31 @@ __device__ __forceinline__ uint32_t digit_pair(uint32_t a, uint32_t c, uint32_t 
     return o;
 }
 
-__device__ __forceinline__ uint32_t lo32(u64 v) { return (uint32_t)v; }
-__device__ __forceinline__ uint32_t hi32(u64 v) { return (uint32_t)(v >> 32); }
+// A ring element with the digit bias added, as 2 W 32-bit words (little
+// endian): word t / 4, byte t % 4 holds the biased digit t.
+template <int W> struct Biased { uint32_t w[2 * W]; };
+
+template <int W>
+__device__ __forceinline__ Biased<W> biased(const u64* e) {
+    Biased<W> b;
+    if constexpr (W == 1) {
+        const u64 y = e[0] + DIGIT_BIAS;
+        b.w[0] = (uint32_t)y;
+        b.w[1] = (uint32_t)(y >> 32);
+    } else {
+        const u64 lo = e[0] + DIGIT_BIAS;
+        const u64 hi = e[1] + DIGIT_BIAS + (lo < e[0] ? 1ull : 0ull);
+        b.w[0] = (uint32_t)lo;
+        b.w[1] = (uint32_t)(lo >> 32);
+        b.w[2] = (uint32_t)hi;
+        b.w[3] = (uint32_t)(hi >> 32);
+    }
+    return b;
+}
 
 // ---------------------------------------------------------------------------
-// prologue: L = [E | X + cE] as digit planes in the MMA's shared-memory image
+// prologue: L = [E | X + cE] as digit planes in the MMA's shared-memory
+// image, and Z = C
 
 struct PrologueParams {
     const u64 *E, *X, *alpha;
@@ -103,14 +144,18 @@ struct PrologueParams {
     int64_t M, K, N;
     int S_tot;     // 2K / KS
     uint8_t* Ap;
-    const u64* C;  // Z = C, the base the GEMM adds its tile segments to
+    const u64* C;
     u64* Z;
 };
 
+template <int W>
 __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
+    constexpr int NDIG = Cfg<W>::NDIG;
+    constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     {
-        const int64_t nv = p.M * p.N / 2;   // N is even
+        // Z = C (16-byte vectors; M N W is even for every eligible shape)
+        const int64_t nv = p.M * p.N * W / 2;
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C);
         ulonglong2* z2 = reinterpret_cast<ulonglong2*>(p.Z);
@@ -124,59 +169,56 @@ __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
     const int64_t mt = id / per_tile;
     const int64_t m = mt * BM + rg * 8 + r;
     const int64_t kv0 = kstage * KS + kg * 8;
-    u64 x[8];
+    u64 x[8 * W];
     if (m < p.M) {
-        if (kv0 < p.K) {
-            const ulonglong2* src = reinterpret_cast<const ulonglong2*>(p.E + m * p.K + kv0);
+        const bool first_half = kv0 < p.K;
+        const int64_t kk = first_half ? kv0 : kv0 - p.K;
+        const ulonglong2* src =
+            reinterpret_cast<const ulonglong2*>((first_half ? p.E : p.X) + (m * p.K + kk) * W);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                ulonglong2 v = __ldg(src + e);
-                x[2 * e] = v.x;
-                x[2 * e + 1] = v.y;
-            }
-        } else {
-            const int64_t kx = kv0 - p.K;
-            const ulonglong2* sx = reinterpret_cast<const ulonglong2*>(p.X + m * p.K + kx);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                ulonglong2 v = __ldg(sx + e);
-                x[2 * e] = v.x;
-                x[2 * e + 1] = v.y;
-            }
-            if (p.coef != COEF_ZERO) {
+        for (int e = 0; e < 4 * W; ++e) {
+            ulonglong2 v = __ldg(src + e);
+            x[2 * e] = v.x;
+            x[2 * e + 1] = v.y;
+        }
+        if (!first_half && p.coef != COEF_ZERO) {
+            const ulonglong2* se = reinterpret_cast<const ulonglong2*>(p.E + (m * p.K + kk) * W);
+            if constexpr (W == 1) {
                 const u64 c = p.coef == COEF_ONE ? 1ull : p.alpha[0];
-                const ulonglong2* se = reinterpret_cast<const ulonglong2*>(p.E + m * p.K + kx);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     ulonglong2 v = __ldg(se + e);
                     x[2 * e] += c * v.x;
                     x[2 * e + 1] += c * v.y;
                 }
+            } else {
+                const u128 c = p.coef == COEF_ONE ? (u128)1 : ((u128)p.alpha[0] | ((u128)p.alpha[1] << 64));
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    ulonglong2 v = __ldg(se + e);
+                    u128 xv = ((u128)x[2 * e] | ((u128)x[2 * e + 1] << 64)) + c * ((u128)v.x | ((u128)v.y << 64));
+                    x[2 * e] = (u64)xv;
+                    x[2 * e + 1] = (u64)(xv >> 64);
+                }
             }
         }
     } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = 0;
+        for (int e = 0; e < 8 * W; ++e) x[e] = 0;
     }
+    Biased<W> b[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) x[e] += DIGIT_BIAS;
-    uint8_t* dst = p.Ap + ((size_t)mt * p.S_tot + kstage) * A_STAGE_BYTES + rg * CORE_SBO +
-                   kg * CORE_LBO + r * 16;
+    for (int e = 0; e < 8; ++e) b[e] = biased<W>(x + W * e);
+    uint8_t* dst = p.Ap + ((size_t)mt * p.S_tot + kstage) * A_STAGE + rg * CORE_SBO + kg * CORE_LBO + r * 16;
 #pragma unroll
     for (int t = 0; t < NDIG; ++t) {
-        const uint32_t b = t & 3;
+        const int wi = t >> 2;
+        const uint32_t byte = t & 3;
         uint4 o;
-        if (t < 4) {
-            o.x = digit_pair(lo32(x[0]), lo32(x[1]), b);
-            o.y = digit_pair(lo32(x[2]), lo32(x[3]), b);
-            o.z = digit_pair(lo32(x[4]), lo32(x[5]), b);
-            o.w = digit_pair(lo32(x[6]), lo32(x[7]), b);
-        } else {
-            o.x = digit_pair(hi32(x[0]), hi32(x[1]), b);
-            o.y = digit_pair(hi32(x[2]), hi32(x[3]), b);
-            o.z = digit_pair(hi32(x[4]), hi32(x[5]), b);
-            o.w = digit_pair(hi32(x[6]), hi32(x[7]), b);
-        }
+        o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
+        o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
+        o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
+        o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
         *reinterpret_cast<uint4*>(dst + t * A_PLANE_BYTES) = o;
     }
 }
@@ -189,7 +231,9 @@ struct TcParams {
     u64* Z;
     int64_t M, K, N;
     int S_tot;       // 16-deep stages per tile (2K / 16)
-    int I;           // 128-deep intervals per tile
+    int I;           // Kd-deep intervals per tile
+    int KD;          // stages per interval
+    int ND;          // columns per tile
     int64_t n_tiles;
     int64_t U;       // work units = tiles x I
 };
@@ -198,7 +242,7 @@ struct TcParams {
 struct Unit {
     int64_t tile;
     int ii;          // interval within the tile
-    int nst;         // stages in this interval (8, or fewer at the end of K)
+    int nst;         // stages in this interval (KD, or fewer at the end of K)
     bool flush;      // last unit of a segment: add the sums into Z
 };
 
@@ -206,14 +250,10 @@ __device__ __forceinline__ Unit unit_of(const TcParams& p, int64_t u, int64_t u1
     Unit x;
     x.tile = u / p.I;
     x.ii = (int)(u % p.I);
-    const int s_begin = x.ii * KD_STAGES;
-    x.nst = min(KD_STAGES, p.S_tot - s_begin);
+    const int s_begin = x.ii * p.KD;
+    x.nst = min(p.KD, p.S_tot - s_begin);
     x.flush = (u + 1 == u1) || (x.ii == p.I - 1);
     return x;
-}
-
-__device__ __forceinline__ void red_add_u64(u64* p, u64 v) {
-    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
@@ -221,17 +261,36 @@ __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
     atomicExch(&g_tc_timeout, 1u);
 }
 
+// add a 128-bit value into a (lo, hi) word pair: the low word's atomic returns
+// its old value, from which the exact carry of this addition follows
+__device__ __forceinline__ void atomic_add_u128(u64* p, u128 v) {
+    const u64 lo = (u64)v;
+    u64 hi = (u64)(v >> 64);
+    u64 old;
+    asm volatile("atom.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(lo) : "memory");
+    hi += (old + lo < old) ? 1ull : 0ull;
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p + 1), "l"(hi) : "memory");
+}
+__device__ __forceinline__ void red_add_u64(u64* p, u64 v) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int W>
 __global__ void __launch_bounds__(NTHREADS, 1)
 ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmF,
                     TcParams p) {
+    constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND, STAGES = Cfg<W>::STAGES;
+    constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
+    using Sum = typename Elem<W>::T;
+
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;
-    uint8_t* sB = smem + OFF_B;
-    uint8_t* sRaw = smem + OFF_RAW;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OFF_BAR);
+    uint8_t* sB = smem + Layout<W>::OFF_B;
+    uint8_t* sRaw = smem + Layout<W>::OFF_RAW;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Layout<W>::OFF_BAR);
     uint64_t* full = bars;
-    uint64_t* empty = full + STAGES;
-    uint64_t* rawFull = empty + STAGES;
+    uint64_t* empty = full + 4;
+    uint64_t* rawFull = empty + 4;
     uint64_t* rawEmpty = rawFull + RAW;
     uint64_t* accFull = rawEmpty + RAW;
     uint64_t* accEmpty = accFull + 2;
@@ -277,7 +336,7 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
             for (int v = 0; v < nv && ok; ++v) {
                 const Unit x = unit_of(p, u0 + v, u1);
                 const int64_t m_tile = x.tile / p.n_tiles;
-                const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + x.ii * KD_STAGES) * A_STAGE_BYTES;
+                const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + (size_t)x.ii * p.KD) * A_STAGE;
                 for (int j = 0; j < x.nst; ++j, ++it) {
                     const int s = it % STAGES;
                     if (!ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
@@ -285,9 +344,8 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                         ok = false;
                         break;
                     }
-                    ptx::mbar_arrive_expect_tx(&full[s], A_STAGE_BYTES);
-                    ptx::bulk_g2s(sA + s * A_STAGE_BYTES, src + (size_t)j * A_STAGE_BYTES, A_STAGE_BYTES,
-                                  &full[s]);
+                    ptx::mbar_arrive_expect_tx(&full[s], A_STAGE);
+                    ptx::bulk_g2s(sA + s * A_STAGE, src + (size_t)j * A_STAGE, A_STAGE, &full[s]);
                 }
             }
             // copies still in flight (only possible after a timeout) must land
@@ -303,7 +361,8 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
             bool ok = true;
             for (int v = 0; v < nv && ok; ++v) {
                 const Unit x = unit_of(p, u0 + v, u1);
-                const int n0 = (int)(x.tile % p.n_tiles) * ND;
+                // x coordinate in 64-bit words (ND W words per tile)
+                const int x0 = (int)(x.tile % p.n_tiles) * ND * W;
                 for (int j = 0; j < x.nst; ++j, ++it) {
                     const int r = it % RAW;
                     if (!ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
@@ -312,21 +371,36 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                         break;
                     }
                     ptx::mbar_arrive_expect_tx(&rawFull[r], RAW_BYTES);
-                    const int64_t kv0 = (int64_t)(x.ii * KD_STAGES + j) * KS;
+                    const int64_t kv0 = (int64_t)(x.ii * p.KD + j) * KS;
                     if (kv0 < p.K)
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, n0, (int)kv0, &rawFull[r]);
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, x0, (int)kv0, &rawFull[r]);
                     else
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, n0, (int)(kv0 - p.K), &rawFull[r]);
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, x0, (int)(kv0 - p.K), &rawFull[r]);
                 }
             }
             for (int j = max(0, it - RAW); j < it; ++j)
                 ptx::mbar_wait(&rawFull[j % RAW], (j / RAW) & 1, abort_flag, WAIT_LIMIT);
         }
     } else if (warp >= W_CONV0 && warp < W_CONV0 + 4) {
-        const int cw = warp - W_CONV0;
-        const int n8 = lane & 7, half = (lane >> 3) & 1, kg = lane >> 4;
-        const int ncol = cw * 8 + n8;               // column within the tile
-        const int krow = kg * 8 + half * 4;         // first of 4 K rows
+        // Each converter thread turns 4 consecutive K values of one column into
+        // digit planes (half a core-matrix row per plane): all 8 planes for
+        // Z_2^64, 8 of the 16 planes for Z_2^128.
+        const int ct = threadIdx.x - W_CONV0 * 32;   // 0..127
+        int ncol, krow, tlo, boff;
+        if constexpr (W == 1) {
+            const int cw = ct >> 5, n8 = lane & 7, half = (lane >> 3) & 1, kg = lane >> 4;
+            ncol = cw * 8 + n8;
+            krow = kg * 8 + half * 4;
+            tlo = 0;
+            boff = (ncol >> 3) * CORE_SBO + kg * CORE_LBO + (ncol & 7) * 16 + half * 8;
+        } else {
+            const int n = ct & 15, kq = (ct >> 4) & 3, dh = ct >> 6;
+            ncol = n;
+            krow = kq * 4;
+            tlo = dh * 8;
+            boff = (n >> 3) * CORE_SBO + (kq >> 1) * CORE_LBO + (n & 7) * 16 + (kq & 1) * 8;
+        }
+        constexpr int TPT = W == 1 ? NDIG : NDIG / 2;   // planes written per thread
         int total = 0;
         for (int v = 0; v < nv; ++v) total += unit_of(p, u0 + v, u1).nst;
         for (int it = 0; it < total; ++it) {
@@ -336,33 +410,35 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                 break;
             }
             const u64* raw = reinterpret_cast<const u64*>(sRaw + r * RAW_BYTES);
-            u64 x[4];
+            u64 e[4 * W];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) x[e] = raw[(krow + e) * ND + ncol] + DIGIT_BIAS;
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int h = 0; h < W; ++h) e[q * W + h] = raw[((krow + q) * ND + ncol) * W + h];
             // the next TMA write into this slot is an async-proxy access: order
             // these generic-proxy reads before it (without this fence the TMA
             // overwrote tiles still being read, measured on GB300)
             ptx::fence_proxy_async_smem();
             ptx::mbar_arrive(&rawEmpty[r]);
+            Biased<W> b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = biased<W>(e + q * W);
             const int s = it % STAGES;
             if (!ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
                 record_timeout(abort_flag);
                 break;
             }
-            uint8_t* dst = sB + s * B_STAGE_BYTES + cw * CORE_SBO + kg * CORE_LBO + n8 * 16 + half * 8;
+            uint8_t* dst = sB + s * B_STAGE_BYTES + boff;
 #pragma unroll
-            for (int t = 0; t < NDIG; ++t) {
-                const uint32_t b = t & 3;
+            for (int tt = 0; tt < TPT; ++tt) {
+                const int t = tlo + tt;
+                const int wi = t >> 2;
+                const uint32_t byte = t & 3;
                 uint2 o;
-                if (t < 4) {
-                    o.x = digit_pair(lo32(x[0]), lo32(x[1]), b);
-                    o.y = digit_pair(lo32(x[2]), lo32(x[3]), b);
-                } else {
-                    o.x = digit_pair(hi32(x[0]), hi32(x[1]), b);
-                    o.y = digit_pair(hi32(x[2]), hi32(x[3]), b);
-                }
-                // stacked row t * 32 + ncol lies in 8-row group 4t + cw
-                *reinterpret_cast<uint2*>(dst + t * 4 * CORE_SBO) = o;
+                o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
+                o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
+                // stacked row t * ND + ncol: 8-row group (t * ND) / 8 + ncol / 8
+                *reinterpret_cast<uint2*>(dst + t * (ND / 8) * CORE_SBO) = o;
             }
             ptx::fence_proxy_async_smem();
             ptx::mbar_arrive(&full[s]);
@@ -393,9 +469,9 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
 #pragma unroll
                     for (int i = 0; i < NDIG; ++i) {
                         const uint64_t adesc = ptx::smem_desc_kmajor(
-                            aBase + s * A_STAGE_BYTES + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
+                            aBase + s * A_STAGE + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
                         const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
-                        ptx::mma_f16(tmem + set * (NDIG * ND) + i * ND, adesc, bdesc, idesc,
+                        ptx::mma_f16(tmem + set * NSTACK + i * ND, adesc, bdesc, idesc,
                                      (j == 0 && i == 0) ? 0u : 1u);
                     }
                     ptx::mma_commit(&empty[s]);
@@ -410,7 +486,8 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
         // drain warps: TMEM lane quadrant = warp % 4
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
-        u64 sum[ND];
+        constexpr int DPL = 32 / ND;   // diagonals per 32-column TMEM load
+        Sum sum[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
         for (int v = 0; v < nv; ++v) {
@@ -422,32 +499,39 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                 break;
             }
             ptx::tc_fence_after();
-            const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * (NDIG * ND);
+            const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * NSTACK;
 #pragma unroll
-            for (int t = 0; t < NDIG; ++t) {
+            for (int t0 = 0; t0 < NDIG; t0 += DPL) {
                 uint32_t f[32];
-                ptx::tmem_ld32(base + t * ND, f);
+                ptx::tmem_ld32(base + t0 * ND, f);
                 ptx::tmem_wait_ld();
-                if (t == NDIG - 1) {
+                if (t0 + DPL >= NDIG) {
                     ptx::tc_fence_before();
                     ptx::mbar_arrive(&accEmpty[set]);
                 }
 #pragma unroll
-                for (int c = 0; c < ND; ++c) {
-                    const long long d = __float2int_rn(__uint_as_float(f[c]));
-                    sum[c] += (u64)d << (8 * t);
+                for (int q = 0; q < 32; ++q) {
+                    const int t = t0 + q / ND, c = q % ND;
+                    const long long d = __float2int_rn(__uint_as_float(f[q]));
+                    // sign-extend to the ring width, then weight by 2^(8t)
+                    const Sum dv = (Sum)(W == 1 ? (Sum)(u64)d : (Sum)(__int128)d);
+                    sum[c] += dv << (8 * t);
                 }
             }
             if (x.flush) {
                 const int64_t m = (x.tile / p.n_tiles) * BM + row;
                 const int64_t n0 = (x.tile % p.n_tiles) * ND;
                 if (m < p.M) {
-                    u64* zrow = p.Z + m * p.N + n0;
+                    u64* zrow = p.Z + (m * p.N + n0) * W;
                     const int64_t rem = p.N - n0;
                     const int ncols = rem < ND ? (int)rem : ND;
 #pragma unroll
-                    for (int c = 0; c < ND; ++c)
-                        if (c < ncols) red_add_u64(zrow + c, sum[c]);
+                    for (int c = 0; c < ND; ++c) {
+                        if (c < ncols) {
+                            if constexpr (W == 1) red_add_u64(zrow + c, sum[c]);
+                            else atomic_add_u128(zrow + 2 * c, sum[c]);
+                        }
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < ND; ++c) sum[c] = 0;
@@ -465,19 +549,22 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
 
 struct Plan {
     int64_t m_tiles, n_tiles;
-    int S_tot, I;
+    int S_tot, I, KD, ND;
     int64_t U;
     size_t ap_bytes;
 };
 
-Plan make_plan(int64_t M, int64_t K, int64_t N) {
+Plan make_plan(int64_t M, int64_t K, int64_t N, int words) {
     Plan pl{};
+    pl.KD = words == 1 ? Cfg<1>::KD : Cfg<2>::KD;
+    pl.ND = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
+    const uint32_t a_stage = words == 1 ? Layout<1>::A_STAGE : Layout<2>::A_STAGE;
     pl.m_tiles = (M + BM - 1) / BM;
-    pl.n_tiles = (N + ND - 1) / ND;
+    pl.n_tiles = (N + pl.ND - 1) / pl.ND;
     pl.S_tot = (int)(2 * K / KS);
-    pl.I = (pl.S_tot + KD_STAGES - 1) / KD_STAGES;
+    pl.I = (pl.S_tot + pl.KD - 1) / pl.KD;
     pl.U = pl.m_tiles * pl.n_tiles * pl.I;
-    pl.ap_bytes = (size_t)pl.m_tiles * pl.S_tot * A_STAGE_BYTES;
+    pl.ap_bytes = (size_t)pl.m_tiles * pl.S_tot * a_stage;
     return pl;
 }
 
@@ -505,13 +592,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 2-D map over a K x N row-major u64 matrix, box of 16 rows x 32 columns
-bool make_map(CUtensorMap* map, const u64* base, int64_t rows, int64_t cols) {
+// 2-D map over a K x N row-major matrix of `words`-word elements, viewed as
+// K rows of N * words 64-bit words; box of 16 rows x (nd * words) words
+bool make_map(CUtensorMap* map, const u64* base, int64_t rows, int64_t cols, int words, int nd) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 8};
-    cuuint32_t box[2] = {(cuuint32_t)ND, (cuuint32_t)KS};
+    cuuint64_t dims[2] = {(cuuint64_t)(cols * words), (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(cols * words) * 8};
+    cuuint32_t box[2] = {(cuuint32_t)(nd * words), (cuuint32_t)KS};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<u64*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -519,47 +607,52 @@ bool make_map(CUtensorMap* map, const u64* base, int64_t rows, int64_t cols) {
     return r == CUDA_SUCCESS;
 }
 
+template <int W>
+cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t st) {
+    CUtensorMap tmB, tmF;
+    if (!make_map(&tmB, a.B, a.K, a.N, W, Cfg<W>::ND) || !make_map(&tmF, a.F, a.K, a.N, W, Cfg<W>::ND))
+        return cudaErrorInvalidValue;
+    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, a.N, pl.S_tot, Ap, a.C, a.Z};
+    const int64_t pth = pl.m_tiles * pl.S_tot * 256;
+    prologue_kernel<W><<<(unsigned)((pth + 255) / 256), 256, 0, st>>>(pp);
+    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Layout<W>::SMEM);
+    if (e != cudaSuccess) return e;
+    TcParams tp{Ap, a.Z, a.M, a.K, a.N, pl.S_tot, pl.I, pl.KD, pl.ND, pl.n_tiles, pl.U};
+    const int sms = sm_count();
+    const int64_t grid = pl.U < sms ? pl.U : sms;
+    ring_gemm_tc_kernel<W><<<(unsigned)grid, NTHREADS, Layout<W>::SMEM, st>>>(tmB, tmF, tp);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
-    if (words != 1) return false;
-    if (M < 1 || N < 2 || K < 32) return false;
-    if (K % 32 != 0 || N % 2 != 0) return false;
-    if (K > (int64_t(1) << 30) || N > (int64_t(1) << 30)) return false;
+    if (words != 1 && words != 2) return false;
+    if (M < 1 || N < 1 || K < 32 || K % 32 != 0) return false;
+    if (words == 1 && N % 2 != 0) return false;       // TMA row stride: 16-byte multiple
+    if (K > (int64_t(1) << 30) || N > (int64_t(1) << 28)) return false;
     if ((M + BM - 1) / BM > 65535) return false;
-    return 2.0 * (double)M * (double)K * (double)N >= (double)(1 << 22);
+    // smaller products run faster on the integer-pipe kernel
+    const double macs = 2.0 * (double)M * (double)K * (double)N;
+    return macs >= (words == 1 ? (double)(1 << 22) : (double)(1 << 20));
 }
 
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words) {
     if (!gemm_tc_eligible(M, K, N, words)) return 0;
-    return align256(make_plan(M, K, N).ap_bytes);
+    return align256(make_plan(M, K, N, words).ap_bytes);
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (!gemm_tc_eligible(a.M, a.K, a.N, a.words)) return cudaErrorNotSupported;
-    Plan pl = make_plan(a.M, a.K, a.N);
+    Plan pl = make_plan(a.M, a.K, a.N, a.words);
     if (ws_bytes < align256(pl.ap_bytes) || ws == nullptr) return cudaErrorInvalidValue;
     uint8_t* Ap = static_cast<uint8_t*>(ws);
-
-    CUtensorMap tmB, tmF;
-    if (!make_map(&tmB, a.B, a.K, a.N) || !make_map(&tmF, a.F, a.K, a.N)) return cudaErrorInvalidValue;
-
-    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, a.N, pl.S_tot, Ap, a.C, a.Z};
-    const int64_t pth = pl.m_tiles * pl.S_tot * 256;
-    prologue_kernel<<<(unsigned)((pth + 255) / 256), 256, 0, st>>>(pp);
-
-    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    TcParams tp{Ap, a.Z, a.M, a.K, a.N, pl.S_tot, pl.I, pl.n_tiles, pl.U};
-    const int64_t grid = pl.U < sm_count() ? pl.U : sm_count();
-    ring_gemm_tc_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, st>>>(tmB, tmF, tp);
-    return cudaGetLastError();
+    return a.words == 1 ? launch<1>(a, Ap, pl, st) : launch<2>(a, Ap, pl, st);
 }
 
 int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words) {
-    if (!gemm_tc_eligible(M, K, N, words)) return 0;
-    return 2;
+    return gemm_tc_eligible(M, K, N, words) ? 2 : 0;
 }
 
 // Reads and clears the device flag that a bounded wait sets when it gives up.

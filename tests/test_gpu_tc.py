@@ -104,3 +104,43 @@ def test_tc_repeated_runs_stable():
         abi.mpc_linear_share(L, *d, Z, ws=ws)
         assert np.array_equal(host(Z)[rows, cols], want), f"run {rep}"
     assert abi.mpc_device_status() == 0
+
+
+SHAPES_128 = [(130, 64, 70), (64, 256, 33), (200, 512, 100), (1, 1024, 512), (257, 96, 48)]
+
+
+@pytest.mark.parametrize("shape", SHAPES_128, ids=str)
+def test_tc_path_parity_z128(shape):
+    """Z_2^128 (k = s = 64): 16 digits per element, 136 digit products."""
+    M, K, N = shape
+    assert abi.mpc_gemm_path(abi.make_layer(M, K, N, 64, 64)) == 1
+    d = dealer.deal(synth.Z128, M, K, N, n=2, seed=M * 11 + K)
+    for i, p in enumerate(d.parties):
+        Z = gpu_share(synth.Z128, i, d.E, d.F, p.A, p.B, p.C)
+        assert np.array_equal(Z, O.linear_share(128, i, d.E, d.F, p.A, p.B, p.C)), f"share party {i}"
+        mZ = gpu_tag_full(synth.Z128, i, p.alpha, d.E, d.F, p.mA, p.mB, p.mC)
+        assert np.array_equal(mZ, O.linear_tag_full(128, p.alpha, d.E, d.F, p.mA, p.mB, p.mC)), \
+            f"full tag party {i}"
+    assert abi.mpc_device_status() == 0
+
+
+PATTERNS_128 = [(0x7F7F7F7F7F7F7F80, 0x7F7F7F7F7F7F7F7F),   # every digit -128
+                (0x7F7F7F7F7F7F7F7F, 0x7F7F7F7F7F7F7F7F),   # every digit 127
+                (0xFFFFFFFFFFFFFFFF, 0xFFFFFFFFFFFFFFFF),
+                (0x8080808080808080, 0x8080808080808080),
+                (0x0123456789ABCDEF, 0xFEDCBA9876543210)]
+
+
+@pytest.mark.parametrize("pat", PATTERNS_128, ids=lambda p: hex(p[1]))
+def test_tc_digit_extremes_z128(pat):
+    M, K, N = 130, 256, 40
+    assert abi.mpc_gemm_path(abi.make_layer(M, K, N, 64, 64)) == 1
+    mk = lambda *s: np.broadcast_to(np.array(pat, dtype=np.uint64), s + (2,)).copy()
+    E, F, A, B, C = mk(M, K), mk(K, N), mk(M, K), mk(K, N), mk(M, N)
+    for party in (0, 1):
+        assert np.array_equal(gpu_share(synth.Z128, party, E, F, A, B, C),
+                              O.linear_share(128, party, E, F, A, B, C))
+    alpha = np.array([list(pat)], dtype=np.uint64)
+    assert np.array_equal(gpu_tag_full(synth.Z128, 1, alpha, E, F, A, B, C),
+                          O.linear_tag_full(128, alpha, E, F, A, B, C))
+    assert abi.mpc_device_status() == 0
