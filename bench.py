@@ -38,8 +38,16 @@ from paper_2311_04406_gb300 import costmodel  # noqa: E402
 
 METRIC = "ring-GMAC/s and tag-overhead ratio (CompactTag vs full tag), bit-exact; p99"
 PARTIES = 2
-RING = synth.Z64
+RING = synth.Z64          # set from --ring in main()
 SEED = 0xC0FFEE01
+
+WORKLOADS = {
+    "cnn": ("cnn_im2col_conv3x3_32x32x64_and_dense4096_b128", lambda b: synth.cnn_pair()),
+    "single": ("dense_64x128x64", lambda b: [synth.single_dense()]),
+    "vgg16": ("vgg16_32x32x3_b{b}", lambda b: synth.vgg16_layers(b)),
+    "resnet18": ("resnet18_32x32x3_b{b}", lambda b: synth.resnet18_layers(b)),
+    "transformer": ("transformer_h1024_t2048", lambda b: synth.transformer_layers()),
+}
 L2_BYTES = 129 * 2**20
 
 
@@ -154,6 +162,20 @@ def _uniform(seed, name, party, shape, bits):
     return synth.uniform(seed, synth.TID[name], party, shape, bits)
 
 
+def _key(seed, name, party, shape):
+    """Public coins and key shares: uniform in [0, 2^s), stored in ring words."""
+    v = synth.uniform(seed, synth.TID[name], party, shape, RING.s)
+    if RING.words == 1:
+        return v
+    out = np.zeros(tuple(shape) + (2,), dtype=np.uint64)
+    out[..., 0] = v
+    return out
+
+
+def ring_shape(*dims):
+    return tuple(dims) + ((2,) if RING.words == 2 else ())
+
+
 def host_inputs(layers, seed=SEED):
     """Uniform inputs per layer: public E, F, D~, chi, chi^ and per-party shares."""
     out = []
@@ -162,12 +184,12 @@ def host_inputs(layers, seed=SEED):
         M, K, N = L.M, L.K, L.N
         sd = seed + 1000 * li
         pub = dict(E=_uniform(sd, "E", 0, (M, K), b), F=_uniform(sd, "F", 0, (K, N), b),
-                   Dt=_uniform(sd, "Dt", 0, (M, N), b), chi=_uniform(sd, "chi", 0, (N,), RING.s),
-                   chi_hat=_uniform(sd, "chi_hat", 0, (M,), RING.s))
+                   Dt=_uniform(sd, "Dt", 0, (M, N), b), chi=_key(sd, "chi", 0, (N,)),
+                   chi_hat=_key(sd, "chi_hat", 0, (M,)))
         parties = []
         for p in range(PARTIES):
             parties.append(dict(
-                alpha=_uniform(sd, "alpha", p, (1,), RING.s),
+                alpha=_key(sd, "alpha", p, (1,)),
                 A=_uniform(sd, "A", p + 1, (M, K), b), B=_uniform(sd, "B", p + 1, (K, N), b),
                 C=_uniform(sd, "C", p + 1, (M, N), b), mA=_uniform(sd, "mA", p + 1, (M, K), b),
                 mB=_uniform(sd, "mB", p + 1, (K, N), b), mC=_uniform(sd, "mC", p + 1, (M, N), b),
@@ -192,12 +214,12 @@ class GpuRun:
             for p, sh in enumerate(parties):
                 lay = abi.make_layer(M, K, N, RING.k, RING.s, p, PARTIES)
                 d = {k: t(v).cuda() for k, v in sh.items()}
-                d["Z"] = torch.empty(M, N, dtype=torch.int64, device="cuda")
-                d["mZf"] = torch.empty(M, N, dtype=torch.int64, device="cuda")
-                d["mZ"] = torch.empty(M, N, dtype=torch.int64, device="cuda")
-                d["mDc"] = torch.empty(M, dtype=torch.int64, device="cuda")
-                d["Dc"] = torch.empty(M, dtype=torch.int64, device="cuda")
-                d["cs"] = torch.empty(1, dtype=torch.int64, device="cuda")
+                d["Z"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
+                d["mZf"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
+                d["mZ"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
+                d["mDc"] = torch.empty(ring_shape(M), dtype=torch.int64, device="cuda")
+                d["Dc"] = torch.empty(ring_shape(M), dtype=torch.int64, device="cuda")
+                d["cs"] = torch.empty(ring_shape(1), dtype=torch.int64, device="cuda")
                 d["layer"] = lay
                 nws = max(abi.mpc_workspace_size(lay, w) for w in range(5))
                 d["ws"] = torch.empty(max(nws, 256), dtype=torch.uint8, device="cuda")
@@ -317,7 +339,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     abi.load()
-    layers = synth.cnn_pair()
+    wl_name, wl_fn = WORKLOADS[args.workload]
+    layers = wl_fn(args.batch)
+    workload = wl_name.format(b=args.batch)
     run = GpuRun(layers, torch, abi, pinned_host=not args.no_e2e)
     units = step_units(layers)
 
@@ -421,16 +445,18 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(layers, budget_s=args.cpu_seconds)
+    dtype = "u64" if RING.words == 1 else "u128 (two u64 words)"
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "ring-GMAC/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "p50_ms_per_step": pct(step_ms, 50), "p99_ms_per_step": pct(step_ms, 99),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic (uniform ring words from seeded SplitMix64; shapes of the CNN layers)",
-            "config": {"workload": "cnn_im2col_conv3x3_32x32x64_and_dense4096_b128",
-                       "layers": [[L.M, L.K, L.N] for L in layers], "ring": "Z_2^64 (k=32, s=32)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (uniform ring words from seeded SplitMix64; shapes of the paper's layers)",
+            "config": {"workload": workload,
+                       "layers": [[L.M, L.K, L.N] for L in layers],
+                       "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
                        "parties": PARTIES, "parallelism": f"replicas x{ws}",
                        "l2": f"inputs larger than L2 ({run_bytes(layers) / 2**20:.0f} MiB per step > 129 MiB)"},
             "tag_overhead_ratio": sum_co / sum_fu,
@@ -479,14 +505,15 @@ def cpu_sample(layers, frac_rows):
         rows = np.repeat(np.arange(m, dtype=np.int64), N)
         cols = np.tile(np.arange(N, dtype=np.int64), m)
         for p, sh in enumerate(parties):
-            jobs.append(lambda sh=sh, p=p, pub=pub, rows=rows, cols=cols: (
-                O.linear_share_at(64, p, pub["E"], pub["F"], sh["A"], sh["B"], sh["C"], rows, cols),
-                O.linear_tag_full_at(64, sh["alpha"], pub["E"], pub["F"], sh["mA"], sh["mB"],
+            bits = RING.bits
+            jobs.append(lambda sh=sh, p=p, pub=pub, rows=rows, cols=cols, bits=bits: (
+                O.linear_share_at(bits, p, pub["E"], pub["F"], sh["A"], sh["B"], sh["C"], rows, cols),
+                O.linear_tag_full_at(bits, sh["alpha"], pub["E"], pub["F"], sh["mA"], sh["mB"],
                                      sh["mC"], rows, cols)))
             units += 2 * (2 * m * K * N)
-            jobs.append(lambda sh=sh, pub=pub: O.check_compact(
-                64, sh["alpha"], pub["chi_hat"],
-                *O.compact_tag(64, sh["alpha"], pub["E"], pub["F"], sh["mA"], sh["mB"], sh["mC"],
+            jobs.append(lambda sh=sh, pub=pub, bits=bits: O.check_compact(
+                bits, sh["alpha"], pub["chi_hat"],
+                *O.compact_tag(bits, sh["alpha"], pub["E"], pub["F"], sh["mA"], sh["mB"], sh["mC"],
                                sh["mR"], pub["Dt"], pub["chi"])[1::-1]))
             units += costmodel.compact_tag_mults(M, K, N) + M
 
@@ -521,7 +548,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    layers = synth.cnn_pair()
+    wl_name, wl_fn = WORKLOADS[args.workload]
+    layers = wl_fn(args.batch)
     run, units = cpu_sample(layers, 1.0 / 64)
     for _ in range(args.warmup):
         run()
@@ -534,10 +562,12 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ring-GMAC/s",
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot / args.steps * 1e3, "p99_ms_per_step": pct([t * 1e3 for t in times], 99),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64" if RING.words == 1 else "u128 (two u64 words)",
         "data": "synthetic (uniform ring words from seeded SplitMix64)",
-        "config": {"workload": "cnn_im2col_conv3x3_32x32x64_and_dense4096_b128",
-                   "layers": [[L.M, L.K, L.N] for L in layers], "ring": "Z_2^64 (k=32, s=32)",
+        "config": {"workload": wl_name.format(b=args.batch),
+                   "layers": [[L.M, L.K, L.N] for L in layers],
+                   "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
                    "parties": PARTIES, "parallelism": "host cores (oracle)"},
         "cpu_baseline": {"value": value, "unit": "ring-GMAC/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": "per step: share + full tag at the first 1/64 of output rows and "
@@ -556,7 +586,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cnn",
+                    help="layer set (default: the CNN pair, conv 1024x576x64 + dense 128x4096x4096)")
+    ap.add_argument("--batch", type=int, default=1, help="batch size for vgg16 / resnet18")
+    ap.add_argument("--ring", type=int, choices=[64, 128], default=64,
+                    help="share ring Z_2^64 (k=s=32) or Z_2^128 (k=s=64)")
     args = ap.parse_args()
+    global RING
+    RING = synth.Z64 if args.ring == 64 else synth.Z128
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

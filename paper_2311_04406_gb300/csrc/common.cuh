@@ -57,4 +57,25 @@ __device__ __forceinline__ void st_stream2(u64* p, ulonglong2 v) {
     asm volatile("st.global.cs.v2.u64 [%0], {%1, %2};" :: "l"(p), "l"(v.x), "l"(v.y) : "memory");
 }
 
+// Exact wrapping atomic additions into Z (any order gives the same result,
+// since addition mod 2^(64 W) is associative and commutative).
+__device__ __forceinline__ void red_add_u64(u64* p, u64 v) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// 128-bit: the low word's atomic returns its old value, which gives the exact
+// carry of this addition into the high word
+__device__ __forceinline__ void atomic_add_u128(u64* p, u128 v) {
+    const u64 lo = (u64)v;
+    u64 hi = (u64)(v >> 64);
+    u64 old;
+    asm volatile("atom.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(lo) : "memory");
+    hi += (old + lo < old) ? 1ull : 0ull;
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p + 1), "l"(hi) : "memory");
+}
+template <int W>
+__device__ __forceinline__ void atomic_add_elem(u64* p, int64_t i, typename Elem<W>::T v) {
+    if constexpr (W == 1) red_add_u64(p + i, v);
+    else atomic_add_u128(p + 2 * i, v);
+}
+
 }  // namespace mpcl

@@ -1,13 +1,21 @@
 // gemm_simt.cu -- exact ring GEMM on the integer pipes (CUDA cores).
 //
 // Computes Z = C + [E | X + c E] . [B ; F] mod 2^(64 W) (the 2K form of
-// Eq. (compute-z) and Eq. (compute-ztag), §2.5).  Used for layers too small
-// or too thin for the tensor-core kernel (gemm_tc.cu), e.g. K = 27 convs or
-// single-row dense layers, where a 128-row MMA tile would be mostly padding.
+// Eq. (compute-z) and Eq. (compute-ztag), §2.5) for layers the tensor-core
+// kernel (gemm_tc.cu) does not take: Z_2^64 layers with odd N, layers too small
+// to amortise a 128-row MMA tile, and skinny layers (M <= 8, e.g. dense layers
+// at batch 1) whose cost is streaming [B ; F] from memory.
 //
-// Tile: 64 x 64 outputs per 256-thread block, 16-deep K slices staged in
-// shared memory; each thread owns a 4 x 4 strided sub-tile so that shared
-// reads are conflict-free.  Out-of-range rows/columns/K are zero-filled.
+// Two kernels, both optionally split along K over grid.z:
+//   * ring_gemm_simt_kernel: 64 x 64 outputs per 256-thread block, 16-deep K
+//     slices staged in shared memory, each thread owns a 4 x 4 strided
+//     sub-tile (conflict-free shared reads).
+//   * ring_gemv_kernel (M <= 8): one thread per output column keeps M sums;
+//     the M rows of the left operand are staged in shared memory per K chunk
+//     and the right operand is read once, coalesced along N.
+// With a K split, Z is first set to C (a device-to-device copy) and every
+// block adds its partial sums with exact wrapping atomics; without one, the
+// block writes C + sum.  Out-of-range rows/columns/K are zero-filled.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -16,9 +24,30 @@ namespace mpcl {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int GV_M = 8;         // rows handled by the skinny kernel
+constexpr int GV_KC = 128;      // K chunk staged in shared memory
+
+// element kv of row m of the left operand [E | X + cE]
+template <int W>
+__device__ __forceinline__ typename Elem<W>::T left(const GemmArgs& a, typename Elem<W>::T c,
+                                                   int64_t m, int64_t kv) {
+    using T = typename Elem<W>::T;
+    if (kv < a.K) return ldg_elem<W>(a.E, m * a.K + kv);
+    const int64_t kx = kv - a.K;
+    T v = ldg_elem<W>(a.X, m * a.K + kx);
+    if (a.coef != COEF_ZERO) v += c * ldg_elem<W>(a.E, m * a.K + kx);
+    return v;
+}
 
 template <int W>
-__global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a) {
+__device__ __forceinline__ typename Elem<W>::T coef_value(const GemmArgs& a) {
+    if (a.coef == COEF_ONE) return 1;
+    if (a.coef == COEF_ALPHA) return ld_elem<W>(a.alpha, 0);
+    return 0;
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a, int64_t kchunk, int atomic) {
     using T = typename Elem<W>::T;
     __shared__ T Ls[BK][BM + 1];
     __shared__ T Rs[BK][BN];
@@ -27,10 +56,9 @@ __global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a) {
     const int tx = tid % 16, ty = tid / 16;
     const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
     const int64_t M = a.M, K = a.K, N = a.N, K2 = 2 * a.K;
-
-    T c = 0;
-    if (a.coef == COEF_ONE) c = 1;
-    else if (a.coef == COEF_ALPHA) c = ld_elem<W>(a.alpha, 0);
+    const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+    const int64_t kend = kbeg + kchunk < K2 ? kbeg + kchunk : K2;
+    const T c = coef_value<W>(a);
 
     T acc[4][4];
 #pragma unroll
@@ -38,33 +66,21 @@ __global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0;
 
-    for (int64_t k0 = 0; k0 < K2; k0 += BK) {
-        // left operand tile: column kv of [E | X + cE]
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
         for (int r = 0; r < (BM * BK) / NT; ++r) {
             int idx = tid + r * NT;
             int mm = idx / BK, kk = idx % BK;
             int64_t m = m0 + mm, kv = k0 + kk;
-            T v = 0;
-            if (m < M && kv < K2) {
-                if (kv < K) {
-                    v = ldg_elem<W>(a.E, m * K + kv);
-                } else {
-                    int64_t kx = kv - K;
-                    v = ldg_elem<W>(a.X, m * K + kx);
-                    if (a.coef != COEF_ZERO) v += c * ldg_elem<W>(a.E, m * K + kx);
-                }
-            }
-            Ls[kk][mm] = v;
+            Ls[kk][mm] = (m < M && kv < kend) ? left<W>(a, c, m, kv) : (T)0;
         }
-        // right operand tile: row kv of [B ; F]
 #pragma unroll
         for (int r = 0; r < (BK * BN) / NT; ++r) {
             int idx = tid + r * NT;
             int kk = idx / BN, nn = idx % BN;
             int64_t n = n0 + nn, kv = k0 + kk;
             T v = 0;
-            if (n < N && kv < K2) v = kv < K ? ldg_elem<W>(a.B, kv * N + n) : ldg_elem<W>(a.F, (kv - K) * N + n);
+            if (n < N && kv < kend) v = kv < K ? ldg_elem<W>(a.B, kv * N + n) : ldg_elem<W>(a.F, (kv - K) * N + n);
             Rs[kk][nn] = v;
         }
         __syncthreads();
@@ -90,20 +106,89 @@ __global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a) {
         for (int j = 0; j < 4; ++j) {
             int64_t n = n0 + tx + 16 * j;
             if (n >= N) continue;
-            st_elem<W>(a.Z, m * N + n, ldg_elem<W>(a.C, m * N + n) + acc[i][j]);
+            if (atomic) atomic_add_elem<W>(a.Z, m * N + n, acc[i][j]);
+            else st_elem<W>(a.Z, m * N + n, ldg_elem<W>(a.C, m * N + n) + acc[i][j]);
         }
     }
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) ring_gemv_kernel(GemmArgs a, int64_t kchunk, int atomic) {
+    using T = typename Elem<W>::T;
+    __shared__ T Ls[GV_M][GV_KC];
+    const int64_t n = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t K = a.K, N = a.N, K2 = 2 * a.K;
+    const int M = (int)a.M;
+    const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+    const int64_t kend = kbeg + kchunk < K2 ? kbeg + kchunk : K2;
+    const T c = coef_value<W>(a);
+    T acc[GV_M];
+#pragma unroll
+    for (int i = 0; i < GV_M; ++i) acc[i] = 0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += GV_KC) {
+        const int kc = (int)(kend - k0 < GV_KC ? kend - k0 : GV_KC);
+        for (int idx = threadIdx.x; idx < GV_M * GV_KC; idx += NT) {
+            const int mm = idx / GV_KC, kk = idx % GV_KC;
+            Ls[mm][kk] = (mm < M && kk < kc) ? left<W>(a, c, mm, k0 + kk) : (T)0;
+        }
+        __syncthreads();
+        if (n < N) {
+#pragma unroll 4
+            for (int kk = 0; kk < kc; ++kk) {
+                const int64_t kv = k0 + kk;
+                const T r = kv < K ? ldg_elem<W>(a.B, kv * N + n) : ldg_elem<W>(a.F, (kv - K) * N + n);
+#pragma unroll
+                for (int i = 0; i < GV_M; ++i) acc[i] += Ls[i][kk] * r;
+            }
+        }
+        __syncthreads();
+    }
+    if (n >= N) return;
+#pragma unroll
+    for (int i = 0; i < GV_M; ++i) {
+        if (i >= M) break;
+        if (atomic) atomic_add_elem<W>(a.Z, (int64_t)i * N + n, acc[i]);
+        else st_elem<W>(a.Z, (int64_t)i * N + n, ldg_elem<W>(a.C, (int64_t)i * N + n) + acc[i]);
+    }
+}
+
+// K chunks so that the grid covers about two waves of 152 SMs
+int64_t choose_kchunk(int64_t blocks_2d, int64_t K2, int64_t step) {
+    int64_t splits = 304 / (blocks_2d > 0 ? blocks_2d : 1);
+    const int64_t max_splits = (K2 + 4 * step - 1) / (4 * step);   // at least 4 steps per split
+    if (splits > max_splits) splits = max_splits;
+    if (splits < 1) splits = 1;
+    int64_t chunk = (K2 + splits - 1) / splits;
+    chunk = ((chunk + step - 1) / step) * step;
+    return chunk > 0 ? chunk : step;
+}
+
+template <int W>
+cudaError_t run(const GemmArgs& a, cudaStream_t st) {
+    const int64_t K2 = 2 * a.K;
+    const bool skinny = a.M <= GV_M;
+    const int64_t bx = skinny ? (a.N + NT - 1) / NT : (a.N + BN - 1) / BN;
+    const int64_t by = skinny ? 1 : (a.M + BM - 1) / BM;
+    if (by > 65535) return cudaErrorInvalidConfiguration;
+    const int64_t step = skinny ? GV_KC : BK;
+    const int64_t kchunk = choose_kchunk(bx * by, K2, step);
+    const int64_t bz = K2 > 0 ? (K2 + kchunk - 1) / kchunk : 1;
+    const int atomic = bz > 1 ? 1 : 0;
+    if (atomic) {
+        cudaError_t e = cudaMemcpyAsync(a.Z, a.C, (size_t)a.M * a.N * 8 * W, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)bx, (unsigned)by, (unsigned)bz);
+    if (skinny) ring_gemv_kernel<W><<<grid, NT, 0, st>>>(a, kchunk, atomic);
+    else ring_gemm_simt_kernel<W><<<grid, NT, 0, st>>>(a, kchunk, atomic);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t st) {
     if (a.M == 0 || a.N == 0) return cudaSuccess;
-    dim3 grid((unsigned)((a.N + BN - 1) / BN), (unsigned)((a.M + BM - 1) / BM));
-    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    if (a.words == 1) ring_gemm_simt_kernel<1><<<grid, NT, 0, st>>>(a);
-    else ring_gemm_simt_kernel<2><<<grid, NT, 0, st>>>(a);
-    return cudaGetLastError();
+    return a.words == 1 ? run<1>(a, st) : run<2>(a, st);
 }
 
 }  // namespace mpcl

@@ -4,7 +4,8 @@
 // Computes Z = C + L . R mod 2^(64 W) with L = [E | X + cE] (M x 2K) and
 // R = [B ; F] (2K x N): the 2K form of Eq. (compute-z) and Eq. (compute-ztag)
 // (§2.5) shared by the share and the full tag.  W = 1 is Z_2^64, W = 2 is
-// Z_2^128 (two 64-bit words per element, (lo, hi)).
+// Z_2^128 (two 64-bit words per element, (lo, hi)).  Each K half is padded with
+// zeros to Kp, a multiple of 16, so a 16-deep stage never straddles the halves.
 //
 // Exactness.  sm_103a has no int8 MMA, so every ring element x is written as
 // D = 8 W signed byte digits d_t in [-128, 127] with x = sum_t d_t 2^(8t) mod
@@ -142,7 +143,8 @@ struct PrologueParams {
     const u64 *E, *X, *alpha;
     int coef;
     int64_t M, K, N;
-    int S_tot;     // 2K / KS
+    int64_t Kp;    // K rounded up to a multiple of KS
+    int S_tot;     // 2 Kp / KS
     uint8_t* Ap;
     const u64* C;
     u64* Z;
@@ -168,43 +170,50 @@ __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
     const int64_t kstage = (id >> 8) % p.S_tot;
     const int64_t mt = id / per_tile;
     const int64_t m = mt * BM + rg * 8 + r;
-    const int64_t kv0 = kstage * KS + kg * 8;
+    const int64_t kp0 = kstage * KS + kg * 8;      // index in [0, 2 Kp)
+    const bool first_half = kp0 < p.Kp;
+    const int64_t kk = first_half ? kp0 : kp0 - p.Kp;   // K index of the 8 values
     u64 x[8 * W];
-    if (m < p.M) {
-        const bool first_half = kv0 < p.K;
-        const int64_t kk = first_half ? kv0 : kv0 - p.K;
-        const ulonglong2* src =
-            reinterpret_cast<const ulonglong2*>((first_half ? p.E : p.X) + (m * p.K + kk) * W);
 #pragma unroll
-        for (int e = 0; e < 4 * W; ++e) {
-            ulonglong2 v = __ldg(src + e);
-            x[2 * e] = v.x;
-            x[2 * e + 1] = v.y;
+    for (int e = 0; e < 8 * W; ++e) x[e] = 0;
+    if (m < p.M && kk < p.K) {
+        const u64* base = (first_half ? p.E : p.X) + (m * p.K + kk) * W;
+        const u64* ebase = p.E + (m * p.K + kk) * W;
+        const bool whole = kk + 8 <= p.K && (((m * p.K + kk) * W) & 1) == 0;
+        if (whole) {
+            const ulonglong2* src = reinterpret_cast<const ulonglong2*>(base);
+#pragma unroll
+            for (int e = 0; e < 4 * W; ++e) {
+                ulonglong2 v = __ldg(src + e);
+                x[2 * e] = v.x;
+                x[2 * e + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (kk + e < p.K) {
+#pragma unroll
+                    for (int h = 0; h < W; ++h) x[W * e + h] = __ldg(base + W * e + h);
+                }
         }
         if (!first_half && p.coef != COEF_ZERO) {
-            const ulonglong2* se = reinterpret_cast<const ulonglong2*>(p.E + (m * p.K + kk) * W);
             if constexpr (W == 1) {
                 const u64 c = p.coef == COEF_ONE ? 1ull : p.alpha[0];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    ulonglong2 v = __ldg(se + e);
-                    x[2 * e] += c * v.x;
-                    x[2 * e + 1] += c * v.y;
-                }
+                for (int e = 0; e < 8; ++e)
+                    if (kk + e < p.K) x[e] += c * __ldg(ebase + e);
             } else {
                 const u128 c = p.coef == COEF_ONE ? (u128)1 : ((u128)p.alpha[0] | ((u128)p.alpha[1] << 64));
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    ulonglong2 v = __ldg(se + e);
-                    u128 xv = ((u128)x[2 * e] | ((u128)x[2 * e + 1] << 64)) + c * ((u128)v.x | ((u128)v.y << 64));
+                    if (kk + e >= p.K) continue;
+                    const u128 ev = (u128)__ldg(ebase + 2 * e) | ((u128)__ldg(ebase + 2 * e + 1) << 64);
+                    const u128 xv = ((u128)x[2 * e] | ((u128)x[2 * e + 1] << 64)) + c * ev;
                     x[2 * e] = (u64)xv;
                     x[2 * e + 1] = (u64)(xv >> 64);
                 }
             }
         }
-    } else {
-#pragma unroll
-        for (int e = 0; e < 8 * W; ++e) x[e] = 0;
     }
     Biased<W> b[8];
 #pragma unroll
@@ -230,7 +239,8 @@ struct TcParams {
     const uint8_t* Ap;
     u64* Z;
     int64_t M, K, N;
-    int S_tot;       // 16-deep stages per tile (2K / 16)
+    int64_t Kp;      // padded K half
+    int S_tot;       // 16-deep stages per tile (2 Kp / 16)
     int I;           // Kd-deep intervals per tile
     int KD;          // stages per interval
     int ND;          // columns per tile
@@ -259,20 +269,6 @@ __device__ __forceinline__ Unit unit_of(const TcParams& p, int64_t u, int64_t u1
 __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
     *abort_flag = 1;
     atomicExch(&g_tc_timeout, 1u);
-}
-
-// add a 128-bit value into a (lo, hi) word pair: the low word's atomic returns
-// its old value, from which the exact carry of this addition follows
-__device__ __forceinline__ void atomic_add_u128(u64* p, u128 v) {
-    const u64 lo = (u64)v;
-    u64 hi = (u64)(v >> 64);
-    u64 old;
-    asm volatile("atom.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(lo) : "memory");
-    hi += (old + lo < old) ? 1ull : 0ull;
-    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p + 1), "l"(hi) : "memory");
-}
-__device__ __forceinline__ void red_add_u64(u64* p, u64 v) {
-    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 template <int W>
@@ -371,11 +367,12 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                         break;
                     }
                     ptx::mbar_arrive_expect_tx(&rawFull[r], RAW_BYTES);
-                    const int64_t kv0 = (int64_t)(x.ii * p.KD + j) * KS;
-                    if (kv0 < p.K)
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, x0, (int)kv0, &rawFull[r]);
+                    // rows at or beyond K inside a padded half arrive zero-filled
+                    const int64_t kp0 = (int64_t)(x.ii * p.KD + j) * KS;
+                    if (kp0 < p.Kp)
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, x0, (int)kp0, &rawFull[r]);
                     else
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, x0, (int)(kv0 - p.K), &rawFull[r]);
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, x0, (int)(kp0 - p.Kp), &rawFull[r]);
                 }
             }
             for (int j = max(0, it - RAW); j < it; ++j)
@@ -548,7 +545,7 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
 // host side
 
 struct Plan {
-    int64_t m_tiles, n_tiles;
+    int64_t m_tiles, n_tiles, Kp;
     int S_tot, I, KD, ND;
     int64_t U;
     size_t ap_bytes;
@@ -561,7 +558,8 @@ Plan make_plan(int64_t M, int64_t K, int64_t N, int words) {
     const uint32_t a_stage = words == 1 ? Layout<1>::A_STAGE : Layout<2>::A_STAGE;
     pl.m_tiles = (M + BM - 1) / BM;
     pl.n_tiles = (N + pl.ND - 1) / pl.ND;
-    pl.S_tot = (int)(2 * K / KS);
+    pl.Kp = ((K + KS - 1) / KS) * KS;
+    pl.S_tot = (int)(2 * pl.Kp / KS);
     pl.I = (pl.S_tot + pl.KD - 1) / pl.KD;
     pl.U = pl.m_tiles * pl.n_tiles * pl.I;
     pl.ap_bytes = (size_t)pl.m_tiles * pl.S_tot * a_stage;
@@ -612,13 +610,13 @@ cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t 
     CUtensorMap tmB, tmF;
     if (!make_map(&tmB, a.B, a.K, a.N, W, Cfg<W>::ND) || !make_map(&tmF, a.F, a.K, a.N, W, Cfg<W>::ND))
         return cudaErrorInvalidValue;
-    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, a.N, pl.S_tot, Ap, a.C, a.Z};
+    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z};
     const int64_t pth = pl.m_tiles * pl.S_tot * 256;
     prologue_kernel<W><<<(unsigned)((pth + 255) / 256), 256, 0, st>>>(pp);
     cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Layout<W>::SMEM);
     if (e != cudaSuccess) return e;
-    TcParams tp{Ap, a.Z, a.M, a.K, a.N, pl.S_tot, pl.I, pl.KD, pl.ND, pl.n_tiles, pl.U};
+    TcParams tp{Ap, a.Z, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND, pl.n_tiles, pl.U};
     const int sms = sm_count();
     const int64_t grid = pl.U < sms ? pl.U : sms;
     ring_gemm_tc_kernel<W><<<(unsigned)grid, NTHREADS, Layout<W>::SMEM, st>>>(tmB, tmF, tp);
@@ -629,7 +627,7 @@ cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t 
 
 bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
     if (words != 1 && words != 2) return false;
-    if (M < 1 || N < 1 || K < 32 || K % 32 != 0) return false;
+    if (M <= 8 || N < 1 || K < 1) return false;        // skinny layers stream better on the SIMT GEMV
     if (words == 1 && N % 2 != 0) return false;       // TMA row stride: 16-byte multiple
     if (K > (int64_t(1) << 30) || N > (int64_t(1) << 28)) return false;
     if ((M + BM - 1) / BM > 65535) return false;

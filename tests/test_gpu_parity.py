@@ -193,3 +193,26 @@ def test_cnn_layers_full_size(layer):
     assert np.array_equal(mZ, O.optmac(64, x["alpha"], x["mR"], x["Dt"]))
     cs = gpu_check_compact(ring, x["alpha"], x["chi_hat"], Dc, mDc)
     assert np.array_equal(cs.reshape(-1), O.check_compact(64, x["alpha"], x["chi_hat"], rDc, rmDc).reshape(-1))
+
+
+SKINNY = [(synth.Z64, (1, 4096, 512)), (synth.Z64, (8, 300, 70)), (synth.Z64, (3, 2048, 130)),
+          (synth.Z64, (1, 4096, 10)), (synth.Z128, (2, 1024, 96)), (synth.Z128, (7, 33, 5))]
+
+
+@pytest.mark.parametrize("ring,shape", SKINNY, ids=lambda x: str(x) if isinstance(x, tuple) else "")
+def test_skinny_layers(ring, shape):
+    """M <= 8 (dense layers at batch 1-8): the split-K GEMV kernel."""
+    M, K, N = shape
+    assert abi.mpc_gemm_path(abi.make_layer(M, K, N, ring.k, ring.s)) == 0
+    _layer_parity(ring, shape, 2, seed=M + K + N)
+
+
+@pytest.mark.parametrize("ring,shape", [(synth.Z64, (100, 3000, 21)), (synth.Z128, (70, 500, 9))],
+                         ids=lambda x: str(x) if isinstance(x, tuple) else "")
+def test_simt_split_k(ring, shape):
+    """Layers the tensor path does not take (odd N in Z_2^64, small products)
+    with a small output grid: the SIMT tile kernel splits K over blocks and
+    adds the partial sums atomically."""
+    M, K, N = shape
+    assert abi.mpc_gemm_path(abi.make_layer(M, K, N, ring.k, ring.s)) == 0
+    _layer_parity(ring, shape, 2, seed=M * 3 + K)

@@ -19,7 +19,7 @@ from gpuhelp import gpu_share, gpu_tag_full
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(130, 256, 70), (300, 640, 96), (128, 32, 1024), (500, 96, 1000), (1, 4096, 512),
+SHAPES = [(130, 256, 70), (300, 640, 96), (128, 32, 1024), (500, 96, 1000), (9, 4096, 512),
           (257, 1024, 34)]
 
 
@@ -106,7 +106,7 @@ def test_tc_repeated_runs_stable():
     assert abi.mpc_device_status() == 0
 
 
-SHAPES_128 = [(130, 64, 70), (64, 256, 33), (200, 512, 100), (1, 1024, 512), (257, 96, 48)]
+SHAPES_128 = [(130, 64, 70), (64, 256, 33), (200, 512, 100), (9, 1024, 512), (257, 96, 48)]
 
 
 @pytest.mark.parametrize("shape", SHAPES_128, ids=str)
@@ -143,4 +143,23 @@ def test_tc_digit_extremes_z128(pat):
     alpha = np.array([list(pat)], dtype=np.uint64)
     assert np.array_equal(gpu_tag_full(synth.Z128, 1, alpha, E, F, A, B, C),
                           O.linear_tag_full(128, alpha, E, F, A, B, C))
+    assert abi.mpc_device_status() == 0
+
+
+RAGGED_K = [(synth.Z64, (2100, 27, 64)), (synth.Z64, (300, 100, 80)), (synth.Z64, (600, 37, 98)),
+            (synth.Z128, (400, 27, 50)), (synth.Z128, (300, 45, 41))]
+
+
+@pytest.mark.parametrize("ring,shape", RAGGED_K, ids=lambda x: str(x) if isinstance(x, tuple) else "")
+def test_tc_ragged_k(ring, shape):
+    """K not a multiple of 16 (each K half is zero-padded to Kp): im2col layers
+    such as the first 3x3 convolution on 3 channels (K = 27)."""
+    M, K, N = shape
+    assert abi.mpc_gemm_path(abi.make_layer(M, K, N, ring.k, ring.s)) == 1
+    d = dealer.deal(ring, M, K, N, n=2, seed=K * 13 + N)
+    for i, p in enumerate(d.parties):
+        assert np.array_equal(gpu_share(ring, i, d.E, d.F, p.A, p.B, p.C),
+                              O.linear_share(ring.bits, i, d.E, d.F, p.A, p.B, p.C))
+        assert np.array_equal(gpu_tag_full(ring, i, p.alpha, d.E, d.F, p.mA, p.mB, p.mC),
+                              O.linear_tag_full(ring.bits, p.alpha, d.E, d.F, p.mA, p.mB, p.mC))
     assert abi.mpc_device_status() == 0
