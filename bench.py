@@ -240,23 +240,22 @@ class GpuRun:
         L, pub, par = self.items[i]
         d = par[p]
         self.abi.mpc_linear_share(d["layer"], pub["E"], pub["F"], d["A"], d["B"], d["C"], d["Z"],
-                                  ws=d["ws"], stream=self.stream)
+                                  ws=d["ws"])
 
     def full(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
         self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_FULL, d["alpha"], pub["E"], pub["F"],
-                                d["mA"], d["mB"], d["mC"], d["mZf"], ws=d["ws"], stream=self.stream)
+                                d["mA"], d["mB"], d["mC"], d["mZf"], ws=d["ws"])
 
     def compact(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
         self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_COMPACT, d["alpha"], pub["E"], pub["F"],
                                 d["mA"], d["mB"], d["mC"], d["mZ"], mR_i=d["mR"], Dtilde=pub["Dt"],
-                                chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"], ws=d["ws"],
-                                stream=self.stream)
+                                chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"], ws=d["ws"])
         self.abi.mpc_tag_check(d["layer"], self.abi.MPC_CHECK_COMPACT, d["alpha"], pub["chi_hat"],
-                               d["Dc"], d["mDc"], d["cs"], ws=d["ws"], stream=self.stream)
+                               d["Dc"], d["mDc"], d["cs"], ws=d["ws"])
 
     def step(self):
         for i in range(len(self.items)):
@@ -345,10 +344,26 @@ def run_ours(args):
     run = GpuRun(layers, torch, abi, pinned_host=not args.no_e2e)
     units = step_units(layers)
 
-    # warm-up
+    # warm-up (eager), then capture one step into a CUDA graph
     for _ in range(args.warmup):
         run.step()
     torch.cuda.synchronize()
+    graph = None
+    if not args.eager:
+        cap = torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cap):
+            run.step()
+        torch.cuda.current_stream().wait_stream(cap)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap):
+            run.step()
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+    step_fn = graph.replay if graph is not None else run.step
 
     # timed region: K steps, per-step events, barrier + sync on both sides
     barrier(ws)
@@ -358,7 +373,7 @@ def run_ours(args):
     with Clocks(local) as ck:
         ev[0].record(st)
         for k in range(args.steps):
-            run.step()
+            step_fn()
             ev[k + 1].record(st)
         torch.cuda.synchronize()
     barrier(ws)
@@ -367,6 +382,16 @@ def run_ours(args):
     total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
     value = ws * units * args.steps / (total_ms / 1e3) / 1e9
+    # the same steps issued eagerly through the API (host launch overhead included)
+    eager_ms = None
+    if graph is not None:
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            run.step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        eager_ms = e0.elapsed_time(e1) / args.steps
 
     # per-call timings: share / full tag / compact tag (+check), per layer
     reps = max(10, min(50, args.steps * 2))
@@ -452,6 +477,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "ring-GMAC/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "p50_ms_per_step": pct(step_ms, 50), "p99_ms_per_step": pct(step_ms, 99),
+            "step_launch": "CUDA graph replay of one captured step" if graph is not None else "eager API calls",
+            "ms_per_step_eager_api": eager_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (uniform ring words from seeded SplitMix64; shapes of the paper's layers)",
             "config": {"workload": workload,
@@ -584,6 +611,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="time eager API calls instead of graph replay")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cnn",

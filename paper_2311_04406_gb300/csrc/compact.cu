@@ -260,6 +260,42 @@ __global__ void __launch_bounds__(NT) vec_kernel(VecParams p, int wpr) {
     }
 }
 
+// K < 64: one thread per row, the two compressed K-vectors staged in shared
+// memory (a warp per row would leave most lanes idle)
+constexpr int SMALL_K = 64;
+
+template <int W>
+__global__ void __launch_bounds__(NT) vec_small_kernel(VecParams p) {
+    using T = typename Elem<W>::T;
+    __shared__ T smb[SMALL_K], sf[SMALL_K];
+    for (int k = threadIdx.x; k < p.K; k += NT) {
+        smb[k] = ld_elem<W>(p.vmb, k);
+        sf[k] = ld_elem<W>(p.vf, k);
+    }
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (r >= p.M) return;
+    T e_mb = 0, ma_u = 0, e_u = 0;
+    const int64_t base = r * p.K;
+    for (int k = 0; k < (int)p.K; ++k) {
+        const T e = ldg_elem<W>(p.E, base + k);
+        const T ma = ldg_elem<W>(p.mA, base + k);
+        e_mb += e * smb[k];
+        ma_u += ma * sf[k];
+        e_u += e * sf[k];
+    }
+    T mrc = 0, dc = 0, mcc = 0;
+    for (int64_t s = 0; s < p.S; ++s) {
+        mrc += ld_elem<W>(p.pmr, r * p.S + s);
+        dc += ld_elem<W>(p.pd, r * p.S + s);
+        mcc += ld_elem<W>(p.pmc, r * p.S + s);
+    }
+    const T alpha = ld_elem<W>(p.alpha, 0);
+    const T mzc = mcc + e_mb + ma_u + alpha * e_u;
+    st_elem<W>(p.mDc, r, mrc - mzc);
+    st_elem<W>(p.Dc, r, dc);
+}
+
 int vec_warps_per_row(int64_t K) {
     return K >= 2048 ? 8 : K >= 1024 ? 4 : K >= 256 ? 2 : 1;
 }
@@ -287,13 +323,17 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
     }
     VecParams vp{a.M, a.K, sp.S, a.alpha, a.E, a.mA, (const u64*)(ws + L.vmb),
                  (const u64*)(ws + L.vf), rp.pmr, rp.pd, rp.pmc, a.mDc, a.Dc};
-    const int wpr = vec_warps_per_row(a.K);
-    const int64_t rpb = WARPS / wpr;
-    const unsigned vb = (unsigned)((a.M + rpb - 1) / rpb);
-    if (W == 1 && (a.K % 2) == 0)
-        vec_kernel<W, 2><<<vb, NT, 0, st>>>(vp, wpr);
-    else
-        vec_kernel<W, 1><<<vb, NT, 0, st>>>(vp, wpr);
+    if (a.K < SMALL_K) {
+        vec_small_kernel<W><<<(unsigned)((a.M + NT - 1) / NT), NT, 0, st>>>(vp);
+    } else {
+        const int wpr = vec_warps_per_row(a.K);
+        const int64_t rpb = WARPS / wpr;
+        const unsigned vb = (unsigned)((a.M + rpb - 1) / rpb);
+        if (W == 1 && (a.K % 2) == 0)
+            vec_kernel<W, 2><<<vb, NT, 0, st>>>(vp, wpr);
+        else
+            vec_kernel<W, 1><<<vb, NT, 0, st>>>(vp, wpr);
+    }
     return cudaGetLastError();
 }
 

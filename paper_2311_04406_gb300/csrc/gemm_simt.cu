@@ -112,50 +112,70 @@ __global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a, int64_t 
     }
 }
 
-template <int W>
+// VEC = 2: two adjacent Z_2^64 columns per thread, read as one 16-byte vector
+// (needs even N); VEC = 1 otherwise.
+// MM >= M rows are accumulated (1, 2, 4 or 8).
+template <int W, int VEC, int MM>
 __global__ void __launch_bounds__(NT) ring_gemv_kernel(GemmArgs a, int64_t kchunk, int atomic) {
     using T = typename Elem<W>::T;
-    __shared__ T Ls[GV_M][GV_KC];
-    const int64_t n = (int64_t)blockIdx.x * NT + threadIdx.x;
+    __shared__ T Ls[MM][GV_KC];
+    const int64_t n = ((int64_t)blockIdx.x * NT + threadIdx.x) * VEC;
     const int64_t K = a.K, N = a.N, K2 = 2 * a.K;
     const int M = (int)a.M;
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
     const int64_t kend = kbeg + kchunk < K2 ? kbeg + kchunk : K2;
     const T c = coef_value<W>(a);
-    T acc[GV_M];
+    T acc[MM][VEC];
 #pragma unroll
-    for (int i = 0; i < GV_M; ++i) acc[i] = 0;
+    for (int i = 0; i < MM; ++i)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[i][v] = 0;
     for (int64_t k0 = kbeg; k0 < kend; k0 += GV_KC) {
         const int kc = (int)(kend - k0 < GV_KC ? kend - k0 : GV_KC);
-        for (int idx = threadIdx.x; idx < GV_M * GV_KC; idx += NT) {
+        for (int idx = threadIdx.x; idx < MM * GV_KC; idx += NT) {
             const int mm = idx / GV_KC, kk = idx % GV_KC;
             Ls[mm][kk] = (mm < M && kk < kc) ? left<W>(a, c, mm, k0 + kk) : (T)0;
         }
         __syncthreads();
         if (n < N) {
-#pragma unroll 4
+#pragma unroll 8
             for (int kk = 0; kk < kc; ++kk) {
                 const int64_t kv = k0 + kk;
-                const T r = kv < K ? ldg_elem<W>(a.B, kv * N + n) : ldg_elem<W>(a.F, (kv - K) * N + n);
+                const u64* row = kv < K ? a.B + kv * N * W : a.F + (kv - K) * N * W;
+                T r[VEC];
+                if constexpr (VEC == 2) {
+                    const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(row + n));
+                    r[0] = v.x;
+                    r[1] = v.y;
+                } else {
+                    r[0] = ldg_elem<W>(row, n);
+                }
 #pragma unroll
-                for (int i = 0; i < GV_M; ++i) acc[i] += Ls[i][kk] * r;
+                for (int i = 0; i < MM; ++i)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[i][v] += Ls[i][kk] * r[v];
             }
         }
         __syncthreads();
     }
-    if (n >= N) return;
 #pragma unroll
-    for (int i = 0; i < GV_M; ++i) {
-        if (i >= M) break;
-        if (atomic) atomic_add_elem<W>(a.Z, (int64_t)i * N + n, acc[i]);
-        else st_elem<W>(a.Z, (int64_t)i * N + n, ldg_elem<W>(a.C, (int64_t)i * N + n) + acc[i]);
+    for (int v = 0; v < VEC; ++v) {
+        const int64_t col = n + v;
+        if (col >= N) break;
+#pragma unroll
+        for (int i = 0; i < MM; ++i) {
+            if (i >= M) break;
+            if (atomic) atomic_add_elem<W>(a.Z, (int64_t)i * N + col, acc[i][v]);
+            else st_elem<W>(a.Z, (int64_t)i * N + col, ldg_elem<W>(a.C, (int64_t)i * N + col) + acc[i][v]);
+        }
     }
 }
 
-// K chunks so that the grid covers about two waves of 152 SMs
-int64_t choose_kchunk(int64_t blocks_2d, int64_t K2, int64_t step) {
-    int64_t splits = 304 / (blocks_2d > 0 ? blocks_2d : 1);
-    const int64_t max_splits = (K2 + 4 * step - 1) / (4 * step);   // at least 4 steps per split
+// K chunks (multiples of `step`, at least `min_chunk`) so that the grid covers
+// about `waves` x 152 blocks
+int64_t choose_kchunk(int64_t blocks_2d, int64_t K2, int64_t step, int64_t min_chunk, int64_t waves) {
+    int64_t splits = waves * 152 / (blocks_2d > 0 ? blocks_2d : 1);
+    const int64_t max_splits = (K2 + min_chunk - 1) / min_chunk;
     if (splits > max_splits) splits = max_splits;
     if (splits < 1) splits = 1;
     int64_t chunk = (K2 + splits - 1) / splits;
@@ -167,20 +187,34 @@ template <int W>
 cudaError_t run(const GemmArgs& a, cudaStream_t st) {
     const int64_t K2 = 2 * a.K;
     const bool skinny = a.M <= GV_M;
-    const int64_t bx = skinny ? (a.N + NT - 1) / NT : (a.N + BN - 1) / BN;
+    const int vec = (skinny && W == 1 && a.N % 2 == 0) ? 2 : 1;
+    const int64_t bx = skinny ? (a.N + NT * vec - 1) / (NT * vec) : (a.N + BN - 1) / BN;
     const int64_t by = skinny ? 1 : (a.M + BM - 1) / BM;
     if (by > 65535) return cudaErrorInvalidConfiguration;
-    const int64_t step = skinny ? GV_KC : BK;
-    const int64_t kchunk = choose_kchunk(bx * by, K2, step);
+    const int64_t kchunk = skinny ? choose_kchunk(bx * by, K2, 16, 32, 4)
+                                  : choose_kchunk(bx * by, K2, BK, 4 * BK, 2);
     const int64_t bz = K2 > 0 ? (K2 + kchunk - 1) / kchunk : 1;
+    if (bz > 65535) return cudaErrorInvalidConfiguration;
     const int atomic = bz > 1 ? 1 : 0;
     if (atomic) {
         cudaError_t e = cudaMemcpyAsync(a.Z, a.C, (size_t)a.M * a.N * 8 * W, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)bx, (unsigned)by, (unsigned)bz);
-    if (skinny) ring_gemv_kernel<W><<<grid, NT, 0, st>>>(a, kchunk, atomic);
-    else ring_gemm_simt_kernel<W><<<grid, NT, 0, st>>>(a, kchunk, atomic);
+    if (skinny) {
+        const int mm = a.M <= 1 ? 1 : a.M <= 2 ? 2 : a.M <= 4 ? 4 : 8;
+#define MPCL_GEMV(V, R) ring_gemv_kernel<W, V, R><<<grid, NT, 0, st>>>(a, kchunk, atomic)
+        if (vec == 2) {
+            if (mm == 1) MPCL_GEMV(2, 1); else if (mm == 2) MPCL_GEMV(2, 2);
+            else if (mm == 4) MPCL_GEMV(2, 4); else MPCL_GEMV(2, 8);
+        } else {
+            if (mm == 1) MPCL_GEMV(1, 1); else if (mm == 2) MPCL_GEMV(1, 2);
+            else if (mm == 4) MPCL_GEMV(1, 4); else MPCL_GEMV(1, 8);
+        }
+#undef MPCL_GEMV
+    } else {
+        ring_gemm_simt_kernel<W><<<grid, NT, 0, st>>>(a, kchunk, atomic);
+    }
     return cudaGetLastError();
 }
 

@@ -613,9 +613,17 @@ cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t 
     PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z};
     const int64_t pth = pl.m_tiles * pl.S_tot * 256;
     prologue_kernel<W><<<(unsigned)((pth + 255) / 256), 256, 0, st>>>(pp);
-    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Layout<W>::SMEM);
-    if (e != cudaSuccess) return e;
+    // the dynamic shared-memory opt-in is set once per device (a host call that
+    // also keeps graph capture free of attribute changes after the first use)
+    static bool smem_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+    if (dev < 0 || dev >= 64 || !smem_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Layout<W>::SMEM);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) smem_set[dev] = true;
+    }
     TcParams tp{Ap, a.Z, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND, pl.n_tiles, pl.U};
     const int sms = sm_count();
     const int64_t grid = pl.U < sms ? pl.U : sms;

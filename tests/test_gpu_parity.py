@@ -216,3 +216,12 @@ def test_simt_split_k(ring, shape):
     M, K, N = shape
     assert abi.mpc_gemm_path(abi.make_layer(M, K, N, ring.k, ring.s)) == 0
     _layer_parity(ring, shape, 2, seed=M * 3 + K)
+
+
+@pytest.mark.parametrize("ring,shape", [(synth.Z64, (3000, 27, 64)), (synth.Z128, (700, 9, 20)),
+                                        (synth.Z64, (513, 63, 12))],
+                         ids=lambda x: str(x) if isinstance(x, tuple) else "")
+def test_compact_small_k(ring, shape):
+    """K < 64 (e.g. the first im2col convolution, K = 27): the CompactTag GEMV
+    runs one thread per row."""
+    _layer_parity(ring, shape, 2, seed=shape[0] + shape[1])
