@@ -83,6 +83,13 @@ def dist_init():
     return rank, ws
 
 
+def job_throughput(units_per_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job ring-GMAC/s: every rank runs the same workload (replicas, weak
+    scaling), so the job processes world x units per step; the time is the
+    slowest rank's."""
+    return world * units_per_step * steps / (max_ms / 1e3) / 1e9
+
+
 def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
@@ -381,7 +388,7 @@ def run_ours(args):
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = max_over_ranks(total_ms, ws)
     ms_per_step = total_ms / args.steps
-    value = ws * units * args.steps / (total_ms / 1e3) / 1e9
+    value = job_throughput(units, args.steps, ws, total_ms)
     # the same steps issued eagerly through the API (host launch overhead included)
     eager_ms = None
     if graph is not None:
