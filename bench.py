@@ -297,14 +297,30 @@ class GpuRun:
         return sum(h.numel() * 8 for h in self.h_outputs)
 
 
-def time_calls(torch, fn, reps):
-    """Per-call durations (ms) with CUDA events on the launching stream."""
+def time_calls(torch, fn, reps, graph=True):
+    """Per-call device durations (ms) with CUDA events on the launching stream;
+    with graph=True the call is captured once and its graph replayed, so host
+    launch overhead is not counted."""
     st = torch.cuda.current_stream()
+    call = fn
+    if graph:
+        cap = torch.cuda.Stream()
+        cap.wait_stream(st)
+        with torch.cuda.stream(cap):
+            fn()
+        st.wait_stream(cap)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            fn()
+        torch.cuda.synchronize()
+        call = g.replay
+        call()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(reps)]
     for a, b in evs:
         a.record(st)
-        fn()
+        call()
         b.record(st)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in evs]
@@ -402,12 +418,13 @@ def run_ours(args):
 
     # per-call timings: share / full tag / compact tag (+check), per layer
     reps = max(10, min(50, args.steps * 2))
+    graphs = not args.eager
     per_layer = []
     gemm_ms_by_layer = []
     for i, L in enumerate(layers):
-        sh = time_calls(torch, lambda: run.share(i, 1), reps)
-        fu = time_calls(torch, lambda: run.full(i, 1), reps)
-        co = time_calls(torch, lambda: run.compact(i, 1), reps)
+        sh = time_calls(torch, lambda: run.share(i, 1), reps, graphs)
+        fu = time_calls(torch, lambda: run.full(i, 1), reps, graphs)
+        co = time_calls(torch, lambda: run.compact(i, 1), reps, graphs)
         per_layer.append(dict(layer=L.name, M=L.M, K=L.K, N=L.N,
                               share_ms_p50=pct(sh, 50), full_tag_ms_p50=pct(fu, 50),
                               compact_tag_ms_p50=pct(co, 50), compact_tag_ms_p99=pct(co, 99),
@@ -431,7 +448,8 @@ def run_ours(args):
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                 "frac": achieved / bf16, "kernel": "ring_gemm_tc",
                 "launch": f"share and full-tag calls of layer {Lb.M}x{Lb.K}x{Lb.N} "
-                          f"(prologue + GEMM), {len(gemm_calls)} calls, CUDA events",
+                          f"(prologue + GEMM), {len(gemm_calls)} calls, CUDA events"
+                          + (" around graph replays of the call" if graphs else ""),
                 "ring_gmacs": ring_macs / (avg_ms / 1e3) / 1e9,
                 "per_unit": f"2MKN ring MACs per call x {digit} fp16 digit products x 2 flop",
                 "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate), x1.0",
