@@ -69,6 +69,9 @@ def _load():
                 "orc_compress": (None, [_int, _i64, _i64, _u64p, _u64p, _u64p]),
                 "orc_compact_tag": (_int, [_int, _i64, _i64, _i64] + [_u64p] * 12),
                 "orc_check_compact": (None, [_int, _i64] + [_u64p] * 5),
+                "orc_linear_share_trunc": (None, [_int, _i64, _i64, _i64] + [_u64p] * 6),
+                "orc_optmac_trunc": (None, [_int, _int, _i64, _i64, _int, _int] + [_u64p] * 7),
+                "orc_compact_tag_trunc": (_int, [_int, _i64, _i64, _i64] + [_u64p] * 12),
                 "orc_check_compact_literal": (_int, [_int, _int, _i64] + [_u64p] * 5),
                 "orc_check_batchrec": (None, [_int, _i64, _i64] + [_u64p] * 5),
             }
@@ -263,3 +266,42 @@ def check_batchrec(bits, alpha, chi, W, mW):
     out = _new(bits, 1)
     _load().orc_check_batchrec(bits, M, N, _p(_scalar(alpha, bits)), _p(chi), _p(W), _p(mW), _p(out))
     return out
+
+
+# ---------------------------------------------------------------------------
+# truncated layer (Fig. Pi_OptMAC&Trunc, Fig. Pi_CompactMatMul)
+
+def linear_share_trunc(bits, E, F, A, B, C):
+    """Step 2: [Z]_i = [C]_i + E.[B]_i + [A]_i.F for every party (no E.F)."""
+    M, K = E.shape[:2]
+    N = F.shape[1]
+    out = _new(bits, M, N)
+    _load().orc_linear_share_trunc(bits, M, K, N, _p(E), _p(F), _p(A), _p(B), _p(C), _p(out))
+    return out
+
+
+def public_product(bits, E, F):
+    """The public E.F (computed by every party from opened values)."""
+    return ring_gemm(bits, E, F)
+
+
+def optmac_trunc(k, s, f, party, alpha, Rf, mRf, Dt, P):
+    """Steps 3-4: returns ([Z^f]_i, [m(Z^f)]_i)."""
+    bits = k + s
+    M, N = Rf.shape[:2]
+    Zf, mZf = _new(bits, M, N), _new(bits, M, N)
+    _load().orc_optmac_trunc(k, s, M, N, int(f), int(party), _p(_scalar(alpha, bits)), _p(Rf), _p(mRf),
+                             _p(Dt), _p(P), _p(Zf), _p(mZf))
+    return Zf, mZf
+
+
+def compact_tag_trunc(bits, alpha, E, F, mA, mB, mC, mR, Dt, chi):
+    """Steps 6-7 (no E.U^c term): returns (mDc, Dc, mZc)."""
+    M, K = E.shape[:2]
+    N = F.shape[1]
+    mDc, Dc, mZc = _new(bits, M), _new(bits, M), _new(bits, M)
+    rc = _load().orc_compact_tag_trunc(bits, M, K, N, _p(_scalar(alpha, bits)), _p(E), _p(F), _p(mA),
+                                       _p(mB), _p(mC), _p(mR), _p(Dt), _p(chi), _p(mDc), _p(Dc), _p(mZc))
+    if rc != 0:
+        raise MemoryError("oracle compact_tag_trunc: allocation failed")
+    return mDc, Dc, mZc

@@ -162,3 +162,59 @@ def run_layer(d: Deal, tamper=None):
     cs = [O.check_compact(bits, a, d.chi_hat, Dc, m) for a, m in zip(alphas, mDc)]
     return dict(Z=Z, mZ_full=mZ_full, D=D, Dt=Dt, mZ_opt=mZ_opt, mDc=mDc, Dc=Dc,
                 mZc=mZc, cs=cs, cs_total=total(bits, cs))
+
+
+# ---------------------------------------------------------------------------
+# truncated layer: the preprocessing of Fig. Pi_OptMAC&Trunc adds shares of a
+# random R~ in [0, 2^k) and of R~^f = R~ / 2^f (floor), both authenticated.
+
+@dataclass
+class TruncDeal:
+    base: Deal
+    f: int
+    R: np.ndarray                 # R~ (k-bit)
+    Rf: np.ndarray                # R~ >> f
+    Rf_shares: list = field(default_factory=list)
+    mRf_shares: list = field(default_factory=list)
+
+
+def deal_trunc(ring: synth.Ring, M: int, K: int, N: int, n: int = 2, seed: int = 1,
+               f: int = 16) -> TruncDeal:
+    d = deal(ring, M, K, N, n=n, seed=seed)
+    bits = ring.bits
+    T = synth.TID
+    Rk = _store(bits, synth.uniform(seed, T["R"], 99, (M, N), ring.k)) if ring.k <= 64 else None
+    Rf = O.from_int(np.vectorize(lambda v: int(v) >> f, otypes=[object])(O.to_int(Rk, bits)), bits)
+    # re-share R~ (k-bit) and R~^f with tags, replacing the dealer's R
+    R_sh = _share(bits, seed, T["R"], Rk, n, (M, N))
+    mR_sh = _share(bits, seed, T["mR"], O.smul(bits, d.alpha, Rk), n, (M, N))
+    for p, r, mr in zip(d.parties, R_sh, mR_sh):
+        p.R, p.mR = r, mr
+    d.R = Rk
+    Rf_sh = _share(bits, seed, T["Rf"], Rf, n, (M, N))
+    mRf_sh = _share(bits, seed, T["mRf"], O.smul(bits, d.alpha, Rf), n, (M, N))
+    return TruncDeal(d, f, Rk, Rf, Rf_sh, mRf_sh)
+
+
+def run_layer_trunc(t: TruncDeal, tamper=None):
+    """The truncated layer for every party through the oracle.  `tamper`:
+    {"Dt": (flat_index, e)} adds e to the broadcast D~."""
+    tamper = tamper or {}
+    d = t.base
+    bits = d.ring.bits
+    Z = [O.linear_share_trunc(bits, d.E, d.F, p.A, p.B, p.C) for p in d.parties]
+    Dt = total(bits, [O.sub(bits, p.R, z) for p, z in zip(d.parties, Z)])
+    if "Dt" in tamper:
+        j, e = tamper["Dt"]
+        flat = Dt.reshape(-1, O.words(bits))
+        flat[j] = O.from_int(O.to_int(flat[j], bits) + e, bits)
+    P = O.public_product(bits, d.E, d.F)
+    outs = [O.optmac_trunc(d.ring.k, d.ring.s, t.f, i, p.alpha, t.Rf_shares[i], t.mRf_shares[i], Dt, P)
+            for i, p in enumerate(d.parties)]
+    comp = [O.compact_tag_trunc(bits, p.alpha, d.E, d.F, p.mA, p.mB, p.mC, p.mR, Dt, d.chi)
+            for p in d.parties]
+    mDc = [c[0] for c in comp]
+    Dc = comp[0][1]
+    cs = [O.check_compact(bits, p.alpha, d.chi_hat, Dc, m) for p, m in zip(d.parties, mDc)]
+    return dict(Z=Z, Dt=Dt, P=P, Zf=[o[0] for o in outs], mZf=[o[1] for o in outs], mDc=mDc,
+                Dc=Dc, mZc=[c[2] for c in comp], cs=cs, cs_total=total(bits, cs))

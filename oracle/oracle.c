@@ -203,10 +203,10 @@ void orc_compress(int b, i64 rows, i64 cols, const u64 *Mat, const u64 *chi, u64
 /* Outputs: Dc (M), mDc (M); mZc (M) when non-NULL.  Returns -1 when the    */
 /* host allocation of the intermediate vectors fails.                        */
 
-int orc_compact_tag(int b, i64 M, i64 K, i64 N, const u64 *alpha,
-                    const u64 *E, const u64 *F, const u64 *mA, const u64 *mB,
-                    const u64 *mC, const u64 *mR, const u64 *Dt, const u64 *chi,
-                    u64 *mDc, u64 *Dc, u64 *mZc) {
+static int compact_tag(int b, i64 M, i64 K, i64 N, const u64 *alpha,
+                       const u64 *E, const u64 *F, const u64 *mA, const u64 *mB,
+                       const u64 *mC, const u64 *mR, const u64 *Dt, const u64 *chi,
+                       u64 *mDc, u64 *Dc, u64 *mZc, int with_eu) {
     int w = words_of(b); u128 m = mask_of(b); u128 a = ld(alpha, 0, w) & m;
     u128 *scratch = (u128 *)malloc(sizeof(u128) * (size_t)(4 * M + 2 * K + 1));
     if (!scratch) return -1;
@@ -243,7 +243,7 @@ int orc_compact_tag(int b, i64 M, i64 K, i64 N, const u64 *alpha,
             ma_u += ld(mA, r * K + k, w) * Uc[k];
             e_u += e * Uc[k];
         }
-        mZcv[r] = (mCc[r] + e_mb + ma_u + a * e_u) & m;
+        mZcv[r] = (mCc[r] + e_mb + ma_u + (with_eu ? a * e_u : 0)) & m;
     }
     for (i64 r = 0; r < M; ++r) {
         st(Dc, r, w, Dcv[r]);
@@ -252,6 +252,56 @@ int orc_compact_tag(int b, i64 M, i64 K, i64 N, const u64 *alpha,
     }
     free(scratch);
     return 0;
+}
+
+int orc_compact_tag(int b, i64 M, i64 K, i64 N, const u64 *alpha,
+                    const u64 *E, const u64 *F, const u64 *mA, const u64 *mB,
+                    const u64 *mC, const u64 *mR, const u64 *Dt, const u64 *chi,
+                    u64 *mDc, u64 *Dc, u64 *mZc) {
+    return compact_tag(b, M, K, N, alpha, E, F, mA, mB, mC, mR, Dt, chi, mDc, Dc, mZc, 1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Truncated layer, Fig. Pi_CompactMatMul with Fig. Pi_OptMAC&Trunc (§3.4).  */
+/*                                                                           */
+/* Step 2: [Z]_i = [C]_i + E.[B]_i + [A]_i.U for every party (the public     */
+/* E.U enters after truncation, step 4).                                     */
+
+void orc_linear_share_trunc(int b, i64 M, i64 K, i64 N, const u64 *E, const u64 *F,
+                            const u64 *A, const u64 *B, const u64 *C, u64 *Z) {
+    orc_linear_share(b, M, K, N, 1, E, F, A, B, C, Z);   /* a party index > 0 adds no E.U */
+}
+
+/* Steps 3-4 (Pi_OptMAC&Trunc steps 3-4, then P1's public term):            */
+/*   delta = D / 2^f with D = D~ mod 2^k, rho = (E.U mod 2^k) / 2^f          */
+/*   (both floor divisions of the k-bit value), tau = rho - delta;           */
+/*   [Z^f]_i = [R^f]_i + tau (party 0 only; a public constant is added once)  */
+/*   [m(Z^f)]_i = [m(R^f)]_i + [alpha]_i * tau (every party).                */
+/* P is the public product E.U (M x N, mod 2^{k+s}).                         */
+void orc_optmac_trunc(int k, int s, i64 M, i64 N, int f, int party, const u64 *alpha,
+                      const u64 *Rf, const u64 *mRf, const u64 *Dt, const u64 *P,
+                      u64 *Zf, u64 *mZf) {
+    int b = k + s;
+    int w = words_of(b); u128 m = mask_of(b); u128 mk = mask_of(k);
+    u128 a = ld(alpha, 0, w) & m;
+    #pragma omp parallel for schedule(static)
+    for (i64 i = 0; i < M * N; ++i) {
+        u128 delta = (ld(Dt, i, w) & mk) >> f;
+        u128 rho = (ld(P, i, w) & mk) >> f;
+        u128 tau = (rho - delta) & m;
+        st(Zf, i, w, (ld(Rf, i, w) + (party == 0 ? tau : 0)) & m);
+        st(mZf, i, w, (ld(mRf, i, w) + a * tau) & m);
+    }
+}
+
+/* Steps 6-7: the compact tag without an E.U^c term,                         */
+/*   [m(Z)^c]_i = [m(C)^c]_i + E.[m(B)^c]_i + [m(A)]_i.U^c,                  */
+/*   [m(D)^c]_i = [m(R)^c]_i - [m(Z)^c]_i, D^c = D~.chi.                     */
+int orc_compact_tag_trunc(int b, i64 M, i64 K, i64 N, const u64 *alpha,
+                          const u64 *E, const u64 *F, const u64 *mA, const u64 *mB,
+                          const u64 *mC, const u64 *mR, const u64 *Dt, const u64 *chi,
+                          u64 *mDc, u64 *Dc, u64 *mZc) {
+    return compact_tag(b, M, K, N, alpha, E, F, mA, mB, mC, mR, Dt, chi, mDc, Dc, mZc, 0);
 }
 
 /* ------------------------------------------------------------------------- */
