@@ -53,7 +53,7 @@ typedef struct {
     int32_t nparties;
 } mpc_layer;
 
-typedef enum { MPC_TAG_FULL = 0, MPC_TAG_COMPACT = 1 } mpc_tag_mode;
+typedef enum { MPC_TAG_FULL = 0, MPC_TAG_COMPACT = 1, MPC_TAG_COMPACT_TRUNC = 2 } mpc_tag_mode;
 typedef enum { MPC_CHECK_COMPACT = 0, MPC_CHECK_BATCHREC = 1 } mpc_check_mode;
 
 /* `which` argument of mpc_workspace_size */
@@ -62,7 +62,10 @@ enum {
     MPC_WS_TAG_FULL = 1,
     MPC_WS_TAG_COMPACT = 2,
     MPC_WS_CHECK_COMPACT = 3,
-    MPC_WS_CHECK_BATCHREC = 4
+    MPC_WS_CHECK_BATCHREC = 4,
+    MPC_WS_PUBLIC_PRODUCT = 5,
+    MPC_WS_OPTMAC_TRUNC = 6,
+    MPC_WS_SHARE_TRUNC = 7
 };
 
 /* Status codes */
@@ -110,6 +113,12 @@ int mpc_linear_share(const mpc_layer *layer,
  *       mDc_i = mR_i.chi - mZc_i               (output, M)
  *       Dc    = Dtilde.chi                     (output, M; the compressed D)
  *   reads E, F, mA_i, mB_i, mC_i, mR_i (M x N), Dtilde (M x N), chi (N).
+ *
+ * MPC_TAG_COMPACT_TRUNC -- the compact tag of the truncated layer,
+ * Fig. Pi_CompactMatMul steps 6-7 (§3.4.2): as MPC_TAG_COMPACT but without
+ * the E.(F.chi) term (the public E.U enters after truncation), and the
+ * per-element tag comes from mpc_optmac_trunc instead: mZ_i may be NULL, in
+ * which case it is not written.  mR_i is the tag share of the untruncated R.
  *
  * alpha_i: device pointer to one ring element (the key share, §2.4).
  */
@@ -162,6 +171,40 @@ int mpc_linear_tag_compact_noalloc(const mpc_layer *layer, const uint64_t *alpha
                                    const uint64_t *Dtilde, const uint64_t *chi,
                                    uint64_t *mZ_i, uint64_t *mDc_i, uint64_t *Dc,
                                    void *stream);
+
+/*
+ * Truncated layer (Fig. Pi_CompactMatMul with Fig. Pi_OptMAC&Trunc, §3.4).
+ *
+ * mpc_linear_share_trunc -- step 2: Z_i = C_i + E . B_i + A_i . F for every
+ *   party, party 0 included (no E . F: the public product is added after
+ *   truncation).  Arguments and layouts as mpc_linear_share; workspace
+ *   MPC_WS_SHARE_TRUNC.
+ *
+ * mpc_public_product -- P = E . F (M x N), the public product every party
+ *   computes from the opened matrices.  Workspace MPC_WS_PUBLIC_PRODUCT.
+ *
+ * mpc_optmac_trunc -- steps 3-4 (Pi_OptMAC&Trunc steps 3-4 plus P1's public
+ *   term), elementwise over M x N:
+ *     delta = (Dtilde mod 2^k) / 2^f,  rho = (P mod 2^k) / 2^f  (floor),
+ *     tau = rho - delta,
+ *     Zf_i  = Rf_i  + tau          (party 0 only; others copy Rf_i)
+ *     mZf_i = mRf_i + alpha_i tau  (every party)
+ *   Rf_i, mRf_i: shares of R^f = R / 2^f and of its tag; Dtilde: the opened
+ *   D~ = sum_j (R_j - Z_j); P from mpc_public_product.  0 <= f <= k
+ *   (MPC_E_SHAPE otherwise).  No workspace.
+ */
+int mpc_linear_share_trunc(const mpc_layer *layer,
+                           const uint64_t *E, const uint64_t *F,
+                           const uint64_t *A_i, const uint64_t *B_i, const uint64_t *C_i,
+                           uint64_t *Z_i,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+int mpc_public_product(const mpc_layer *layer, const uint64_t *E, const uint64_t *F,
+                       uint64_t *P, void *workspace, size_t ws_bytes, void *stream);
+
+int mpc_optmac_trunc(const mpc_layer *layer, int f, const uint64_t *alpha_i,
+                     const uint64_t *Rf_i, const uint64_t *mRf_i, const uint64_t *Dtilde,
+                     const uint64_t *P, uint64_t *Zf_i, uint64_t *mZf_i, void *stream);
 
 /* Bytes of workspace the call `which` (MPC_WS_*) needs for this layer; 0 for
  * an invalid layer.  A larger workspace is always accepted. */

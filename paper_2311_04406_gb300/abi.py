@@ -20,15 +20,17 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-MPC_TAG_FULL, MPC_TAG_COMPACT = 0, 1
+MPC_TAG_FULL, MPC_TAG_COMPACT, MPC_TAG_COMPACT_TRUNC = 0, 1, 2
 MPC_CHECK_COMPACT, MPC_CHECK_BATCHREC = 0, 1
-MPC_WS_SHARE, MPC_WS_TAG_FULL, MPC_WS_TAG_COMPACT, MPC_WS_CHECK_COMPACT, MPC_WS_CHECK_BATCHREC = range(5)
+(MPC_WS_SHARE, MPC_WS_TAG_FULL, MPC_WS_TAG_COMPACT, MPC_WS_CHECK_COMPACT, MPC_WS_CHECK_BATCHREC,
+ MPC_WS_PUBLIC_PRODUCT, MPC_WS_OPTMAC_TRUNC, MPC_WS_SHARE_TRUNC) = range(8)
 
 # the functions include/mpclinear.h declares
 ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_workspace_size",
                  "mpc_gemm_path", "mpc_launch_count", "mpc_device_status", "mpc_status_str",
                  "mpc_version",
-                 "mpc_linear_tag_compact_noalloc")
+                 "mpc_linear_tag_compact_noalloc", "mpc_linear_share_trunc", "mpc_public_product",
+                 "mpc_optmac_trunc")
 MPC_E_SCRATCH_LIMIT = -10
 MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -80,6 +82,12 @@ def load(build_if_missing: bool = False):
         lib.mpc_status_str.restype = ctypes.c_char_p
         lib.mpc_linear_tag_compact_noalloc.argtypes = [L] + [P] * 12 + [P]
         lib.mpc_linear_tag_compact_noalloc.restype = ctypes.c_int
+        lib.mpc_linear_share_trunc.argtypes = [L] + [P] * 6 + [P, ctypes.c_size_t, P]
+        lib.mpc_linear_share_trunc.restype = ctypes.c_int
+        lib.mpc_public_product.argtypes = [L, P, P, P, P, ctypes.c_size_t, P]
+        lib.mpc_public_product.restype = ctypes.c_int
+        lib.mpc_optmac_trunc.argtypes = [L, ctypes.c_int] + [P] * 7 + [P]
+        lib.mpc_optmac_trunc.restype = ctypes.c_int
         lib.mpc_launch_count.argtypes = [L, ctypes.c_int]
         lib.mpc_launch_count.restype = ctypes.c_int
         lib.mpc_device_status.argtypes = []
@@ -194,3 +202,28 @@ def mpc_linear_tag_compact_noalloc(layer, alpha_i, E, F, mA_i, mB_i, mC_i, mR_i,
         ctypes.byref(layer), _ptr(alpha_i), _ptr(E), _ptr(F), _ptr(mA_i), _ptr(mB_i), _ptr(mC_i),
         _ptr(mR_i), _ptr(Dtilde), _ptr(chi), _ptr(mZ_i), _ptr(mDc_i), _ptr(Dc), _stream(stream)))
     return mZ_i
+
+
+def mpc_linear_share_trunc(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None):
+    """Truncated layer, step 2: Z_i = C_i + E.B_i + A_i.F for every party."""
+    wp, wb = _ws(layer, MPC_WS_SHARE_TRUNC, ws)
+    _check("mpc_linear_share_trunc", load().mpc_linear_share_trunc(
+        ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(A_i), _ptr(B_i), _ptr(C_i), _ptr(Z_i),
+        wp, wb, _stream(stream)))
+    return Z_i
+
+
+def mpc_public_product(layer, E, F, P, ws=None, stream=None):
+    """P = E.F (public)."""
+    wp, wb = _ws(layer, MPC_WS_PUBLIC_PRODUCT, ws)
+    _check("mpc_public_product", load().mpc_public_product(
+        ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(P), wp, wb, _stream(stream)))
+    return P
+
+
+def mpc_optmac_trunc(layer, f, alpha_i, Rf_i, mRf_i, Dtilde, P, Zf_i, mZf_i, stream=None):
+    """Truncated layer, steps 3-4 (OptMAC&Trunc plus the public product term)."""
+    _check("mpc_optmac_trunc", load().mpc_optmac_trunc(
+        ctypes.byref(layer), int(f), _ptr(alpha_i), _ptr(Rf_i), _ptr(mRf_i), _ptr(Dtilde), _ptr(P),
+        _ptr(Zf_i), _ptr(mZf_i), _stream(stream)))
+    return Zf_i, mZf_i

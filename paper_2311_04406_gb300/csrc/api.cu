@@ -51,16 +51,17 @@ int cuda_status(cudaError_t e) {
     return MPC_E_CUDA;
 }
 
-size_t gemm_ws(const mpc_layer* L) {
+size_t gemm_ws(const mpc_layer* L, int one_half = 0) {
     if (mpcl::gemm_tc_eligible(L->M, L->K, L->N, L->ring.words))
-        return mpcl::gemm_tc_workspace(L->M, L->K, L->N, L->ring.words);
+        return mpcl::gemm_tc_workspace(L->M, L->K, L->N, L->ring.words, one_half);
     return 0;
 }
 
 int run_gemm(const mpcl::GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (g.M == 0 || g.N == 0) return MPC_OK;
     if (mpcl::gemm_tc_eligible(g.M, g.K, g.N, g.words)) {
-        if (!ws || ws_bytes < mpcl::gemm_tc_workspace(g.M, g.K, g.N, g.words)) return MPC_E_WORKSPACE;
+        if (!ws || ws_bytes < mpcl::gemm_tc_workspace(g.M, g.K, g.N, g.words, g.one_half))
+            return MPC_E_WORKSPACE;
         if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
         return cuda_status(mpcl::launch_gemm_tc(g, ws, ws_bytes, st));
     }
@@ -86,12 +87,15 @@ int mpc_launch_count(const mpc_layer* L, int which) {
     const int w = L->ring.words;
     switch (which) {
         case MPC_WS_SHARE:
+        case MPC_WS_SHARE_TRUNC:
+        case MPC_WS_PUBLIC_PRODUCT:
         case MPC_WS_TAG_FULL:
             if (M == 0 || N == 0) return 0;
             return mpcl::gemm_tc_eligible(M, K, N, w) ? mpcl::gemm_tc_launches(M, K, N, w) : 1;
         case MPC_WS_TAG_COMPACT: return mpcl::compact_launches(M, K, N);
         case MPC_WS_CHECK_COMPACT: return 1;
         case MPC_WS_CHECK_BATCHREC: return 2;
+        case MPC_WS_OPTMAC_TRUNC: return (M > 0 && N > 0) ? 1 : 0;
         default: return MPC_E_MODE;
     }
 }
@@ -125,7 +129,10 @@ size_t mpc_workspace_size(const mpc_layer* L, int which) {
     const int w = L->ring.words;
     switch (which) {
         case MPC_WS_SHARE:
+        case MPC_WS_SHARE_TRUNC:
         case MPC_WS_TAG_FULL: return gemm_ws(L);
+        case MPC_WS_PUBLIC_PRODUCT: return gemm_ws(L, 1);
+        case MPC_WS_OPTMAC_TRUNC: return 0;
         case MPC_WS_TAG_COMPACT: return mpcl::compact_workspace(L->M, L->K, L->N, w);
         case MPC_WS_CHECK_COMPACT: return 0;
         case MPC_WS_CHECK_BATCHREC: return mpcl::check_batchrec_workspace(L->M, L->N, w);
@@ -147,8 +154,57 @@ int mpc_linear_share(const mpc_layer* L, const uint64_t* E, const uint64_t* F,
     mpcl::GemmArgs g{M, K, N, L->ring.words,
                      (const u64*)E, (const u64*)F, (const u64*)A_i, (const u64*)B_i,
                      (const u64*)C_i, (u64*)Z_i,
-                     L->party == 0 ? mpcl::COEF_ONE : mpcl::COEF_ZERO, nullptr};
+                     L->party == 0 ? mpcl::COEF_ONE : mpcl::COEF_ZERO, nullptr, 0};
     return run_gemm(g, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mpc_linear_share_trunc(const mpc_layer* L, const uint64_t* E, const uint64_t* F,
+                           const uint64_t* A_i, const uint64_t* B_i, const uint64_t* C_i,
+                           uint64_t* Z_i, void* ws, size_t ws_bytes, void* stream) {
+    CHK(check_layer(L));
+    const int64_t M = L->M, K = L->K, N = L->N;
+    CHK(check_ptr(E, M * K));
+    CHK(check_ptr(A_i, M * K));
+    CHK(check_ptr(F, K * N));
+    CHK(check_ptr(B_i, K * N));
+    CHK(check_ptr(C_i, M * N));
+    CHK(check_ptr(Z_i, M * N));
+    mpcl::GemmArgs g{M, K, N, L->ring.words,
+                     (const u64*)E, (const u64*)F, (const u64*)A_i, (const u64*)B_i,
+                     (const u64*)C_i, (u64*)Z_i, mpcl::COEF_ZERO, nullptr, 0};
+    return run_gemm(g, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mpc_public_product(const mpc_layer* L, const uint64_t* E, const uint64_t* F, uint64_t* P,
+                       void* ws, size_t ws_bytes, void* stream) {
+    CHK(check_layer(L));
+    const int64_t M = L->M, K = L->K, N = L->N;
+    CHK(check_ptr(E, M * K));
+    CHK(check_ptr(F, K * N));
+    CHK(check_ptr(P, M * N));
+    // P = (X + 0 E) . F with X = E over the K of one half; no addend
+    mpcl::GemmArgs g{M, K, N, L->ring.words, (const u64*)E, (const u64*)F, (const u64*)E, nullptr,
+                     nullptr, (u64*)P, mpcl::COEF_ZERO, nullptr, 1};
+    return run_gemm(g, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mpc_optmac_trunc(const mpc_layer* L, int f, const uint64_t* alpha_i, const uint64_t* Rf_i,
+                     const uint64_t* mRf_i, const uint64_t* Dtilde, const uint64_t* P,
+                     uint64_t* Zf_i, uint64_t* mZf_i, void* stream) {
+    CHK(check_layer(L));
+    if (f < 0 || f > L->ring.k) return MPC_E_SHAPE;
+    const int64_t MN = L->M * L->N;
+    CHK(check_ptr(alpha_i, 1));
+    CHK(check_ptr(Rf_i, MN));
+    CHK(check_ptr(mRf_i, MN));
+    CHK(check_ptr(Dtilde, MN));
+    CHK(check_ptr(P, MN));
+    CHK(check_ptr(Zf_i, MN));
+    CHK(check_ptr(mZf_i, MN));
+    return cuda_status(mpcl::launch_optmac_trunc(MN, L->ring.words, L->ring.k, f, L->party == 0 ? 1 : 0,
+                                                 (const u64*)alpha_i, (const u64*)Rf_i, (const u64*)mRf_i,
+                                                 (const u64*)Dtilde, (const u64*)P, (u64*)Zf_i,
+                                                 (u64*)mZf_i, (cudaStream_t)stream));
 }
 
 int mpc_linear_tag(const mpc_layer* L, int mode, const uint64_t* alpha_i,
@@ -158,7 +214,7 @@ int mpc_linear_tag(const mpc_layer* L, int mode, const uint64_t* alpha_i,
                    uint64_t* mZ_i, uint64_t* mDc_i, uint64_t* Dc,
                    void* ws, size_t ws_bytes, void* stream) {
     CHK(check_layer(L));
-    if (mode != MPC_TAG_FULL && mode != MPC_TAG_COMPACT) return MPC_E_MODE;
+    if (mode != MPC_TAG_FULL && mode != MPC_TAG_COMPACT && mode != MPC_TAG_COMPACT_TRUNC) return MPC_E_MODE;
     const int64_t M = L->M, K = L->K, N = L->N;
     const int w = L->ring.words;
     CHK(check_ptr(alpha_i, 1));
@@ -167,12 +223,12 @@ int mpc_linear_tag(const mpc_layer* L, int mode, const uint64_t* alpha_i,
     CHK(check_ptr(F, K * N));
     CHK(check_ptr(mB_i, K * N));
     CHK(check_ptr(mC_i, M * N));
-    CHK(check_ptr(mZ_i, M * N));
+    if (mode != MPC_TAG_COMPACT_TRUNC || mZ_i != nullptr) CHK(check_ptr(mZ_i, M * N));
     cudaStream_t st = (cudaStream_t)stream;
     if (mode == MPC_TAG_FULL) {
         mpcl::GemmArgs g{M, K, N, w, (const u64*)E, (const u64*)F, (const u64*)mA_i,
                          (const u64*)mB_i, (const u64*)mC_i, (u64*)mZ_i, mpcl::COEF_ALPHA,
-                         (const u64*)alpha_i};
+                         (const u64*)alpha_i, 0};
         return run_gemm(g, ws, ws_bytes, st);
     }
     CHK(check_ptr(mR_i, M * N));
@@ -185,7 +241,8 @@ int mpc_linear_tag(const mpc_layer* L, int mode, const uint64_t* alpha_i,
         if (!ws || ws_bytes < need) return MPC_E_WORKSPACE;
         if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
     }
-    mpcl::CompactArgs c{M, K, N, w, (const u64*)alpha_i, (const u64*)E, (const u64*)F,
+    mpcl::CompactArgs c{M, K, N, w, mode == MPC_TAG_COMPACT ? 1 : 0, (const u64*)alpha_i,
+                        (const u64*)E, (const u64*)F,
                         (const u64*)mA_i, (const u64*)mB_i, (const u64*)mC_i, (const u64*)mR_i,
                         (const u64*)Dtilde, (const u64*)chi, (u64*)mZ_i, (u64*)mDc_i, (u64*)Dc};
     return cuda_status(mpcl::launch_compact(c, ws, ws_bytes, st));

@@ -91,7 +91,7 @@ WsLayout ws_layout(int64_t M, int64_t K, int64_t N, int words) {
 struct RowsParams {
     int64_t M, K, N, S, cw;
     const u64 *alpha, *mR, *Dt, *mC, *mB, *F, *chi;
-    u64* mZ;
+    u64* mZ;   // NULL: the OptMAC tag is not written
     u64 *pmr, *pd, *pmc, *qmb, *qf;
 };
 
@@ -122,10 +122,12 @@ __global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
                 s1 += r.x * x.x + r.y * x.y;
                 s2 += d.x * x.x + d.y * x.y;
                 s3 += m.x * x.x + m.y * x.y;
-                ulonglong2 z;
-                z.x = r.x - alpha * d.x;
-                z.y = r.y - alpha * d.y;
-                st_stream2(p.mZ + base + c, z);
+                if (p.mZ) {
+                    ulonglong2 z;
+                    z.x = r.x - alpha * d.x;
+                    z.y = r.y - alpha * d.y;
+                    st_stream2(p.mZ + base + c, z);
+                }
             }
         } else {
             for (int64_t c = c0 + lane; c < c1; c += 32) {
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
                 s1 += r * x;
                 s2 += d * x;
                 s3 += m * x;
-                st_elem<W>(p.mZ, base + c, r - alpha * d);
+                if (p.mZ) st_elem<W>(p.mZ, base + c, r - alpha * d);
             }
         }
         s1 = warp_sum<W>(s1);
@@ -191,6 +193,7 @@ __global__ void finalize_kernel(int64_t K, int64_t S, const u64* qmb, const u64*
 
 struct VecParams {
     int64_t M, K, S;
+    int with_eu;
     const u64 *alpha, *E, *mA, *vmb, *vf, *pmr, *pd, *pmc;
     u64 *mDc, *Dc;
 };
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(NT) vec_kernel(VecParams p, int wpr) {
             mcc += ld_elem<W>(p.pmc, r * p.S + s);
         }
         const T alpha = ld_elem<W>(p.alpha, 0);
-        T mzc = mcc + e_mb + ma_u + alpha * e_u;
+        T mzc = mcc + e_mb + ma_u + (p.with_eu ? alpha * e_u : (T)0);
         st_elem<W>(p.mDc, r, mrc - mzc);
         st_elem<W>(p.Dc, r, dc);
     }
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(NT) vec_small_kernel(VecParams p) {
         mcc += ld_elem<W>(p.pmc, r * p.S + s);
     }
     const T alpha = ld_elem<W>(p.alpha, 0);
-    const T mzc = mcc + e_mb + ma_u + alpha * e_u;
+    const T mzc = mcc + e_mb + ma_u + (p.with_eu ? alpha * e_u : (T)0);
     st_elem<W>(p.mDc, r, mrc - mzc);
     st_elem<W>(p.Dc, r, dc);
 }
@@ -321,7 +324,7 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
         finalize_kernel<W><<<fb, 256, 0, st>>>(a.K, sp.S, rp.qmb, rp.qf,
                                                 (u64*)(ws + L.vmb), (u64*)(ws + L.vf));
     }
-    VecParams vp{a.M, a.K, sp.S, a.alpha, a.E, a.mA, (const u64*)(ws + L.vmb),
+    VecParams vp{a.M, a.K, sp.S, a.with_eu, a.alpha, a.E, a.mA, (const u64*)(ws + L.vmb),
                  (const u64*)(ws + L.vf), rp.pmr, rp.pd, rp.pmc, a.mDc, a.Dc};
     if (a.K < SMALL_K) {
         vec_small_kernel<W><<<(unsigned)((a.M + NT - 1) / NT), NT, 0, st>>>(vp);

@@ -27,11 +27,12 @@ constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 constexpr int GV_M = 8;         // rows handled by the skinny kernel
 constexpr int GV_KC = 128;      // K chunk staged in shared memory
 
-// element kv of row m of the left operand [E | X + cE]
+// element kv of row m of the left operand [E | X + cE] (one_half: X + cE)
 template <int W>
 __device__ __forceinline__ typename Elem<W>::T left(const GemmArgs& a, typename Elem<W>::T c,
                                                    int64_t m, int64_t kv) {
     using T = typename Elem<W>::T;
+    if (a.one_half) kv += a.K;
     if (kv < a.K) return ldg_elem<W>(a.E, m * a.K + kv);
     const int64_t kx = kv - a.K;
     T v = ldg_elem<W>(a.X, m * a.K + kx);
@@ -55,10 +56,11 @@ __global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a, int64_t 
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
-    const int64_t M = a.M, K = a.K, N = a.N, K2 = 2 * a.K;
+    const int64_t M = a.M, K = a.K, N = a.N, K2 = a.one_half ? a.K : 2 * a.K;
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
     const int64_t kend = kbeg + kchunk < K2 ? kbeg + kchunk : K2;
     const T c = coef_value<W>(a);
+    const int64_t kr = a.one_half ? K : 0;   // row offset into [B ; F]
 
     T acc[4][4];
 #pragma unroll
@@ -80,7 +82,10 @@ __global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a, int64_t 
             int kk = idx / BN, nn = idx % BN;
             int64_t n = n0 + nn, kv = k0 + kk;
             T v = 0;
-            if (n < N && kv < kend) v = kv < K ? ldg_elem<W>(a.B, kv * N + n) : ldg_elem<W>(a.F, (kv - K) * N + n);
+            if (n < N && kv < kend) {
+                const int64_t kq = kv + kr;
+                v = kq < K ? ldg_elem<W>(a.B, kq * N + n) : ldg_elem<W>(a.F, (kq - K) * N + n);
+            }
             Rs[kk][nn] = v;
         }
         __syncthreads();
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(NT) ring_gemm_simt_kernel(GemmArgs a, int64_t 
             int64_t n = n0 + tx + 16 * j;
             if (n >= N) continue;
             if (atomic) atomic_add_elem<W>(a.Z, m * N + n, acc[i][j]);
-            else st_elem<W>(a.Z, m * N + n, ldg_elem<W>(a.C, m * N + n) + acc[i][j]);
+            else st_elem<W>(a.Z, m * N + n, (a.C ? ldg_elem<W>(a.C, m * N + n) : (T)0) + acc[i][j]);
         }
     }
 }
@@ -120,7 +125,8 @@ __global__ void __launch_bounds__(NT) ring_gemv_kernel(GemmArgs a, int64_t kchun
     using T = typename Elem<W>::T;
     __shared__ T Ls[MM][GV_KC];
     const int64_t n = ((int64_t)blockIdx.x * NT + threadIdx.x) * VEC;
-    const int64_t K = a.K, N = a.N, K2 = 2 * a.K;
+    const int64_t K = a.K, N = a.N, K2 = a.one_half ? a.K : 2 * a.K;
+    const int64_t kr = a.one_half ? K : 0;   // row offset into [B ; F]
     const int M = (int)a.M;
     const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
     const int64_t kend = kbeg + kchunk < K2 ? kbeg + kchunk : K2;
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(NT) ring_gemv_kernel(GemmArgs a, int64_t kchun
         if (n < N) {
 #pragma unroll 8
             for (int kk = 0; kk < kc; ++kk) {
-                const int64_t kv = k0 + kk;
+                const int64_t kv = k0 + kk + kr;
                 const u64* row = kv < K ? a.B + kv * N * W : a.F + (kv - K) * N * W;
                 T r[VEC];
                 if constexpr (VEC == 2) {
@@ -166,7 +172,8 @@ __global__ void __launch_bounds__(NT) ring_gemv_kernel(GemmArgs a, int64_t kchun
         for (int i = 0; i < MM; ++i) {
             if (i >= M) break;
             if (atomic) atomic_add_elem<W>(a.Z, (int64_t)i * N + col, acc[i][v]);
-            else st_elem<W>(a.Z, (int64_t)i * N + col, ldg_elem<W>(a.C, (int64_t)i * N + col) + acc[i][v]);
+            else st_elem<W>(a.Z, (int64_t)i * N + col,
+                            (a.C ? ldg_elem<W>(a.C, (int64_t)i * N + col) : (T)0) + acc[i][v]);
         }
     }
 }
@@ -185,7 +192,7 @@ int64_t choose_kchunk(int64_t blocks_2d, int64_t K2, int64_t step, int64_t min_c
 
 template <int W>
 cudaError_t run(const GemmArgs& a, cudaStream_t st) {
-    const int64_t K2 = 2 * a.K;
+    const int64_t K2 = a.one_half ? a.K : 2 * a.K;
     const bool skinny = a.M <= GV_M;
     const int vec = (skinny && W == 1 && a.N % 2 == 0) ? 2 : 1;
     const int64_t bx = skinny ? (a.N + NT * vec - 1) / (NT * vec) : (a.N + BN - 1) / BN;
@@ -197,7 +204,9 @@ cudaError_t run(const GemmArgs& a, cudaStream_t st) {
     if (bz > 65535) return cudaErrorInvalidConfiguration;
     const int atomic = bz > 1 ? 1 : 0;
     if (atomic) {
-        cudaError_t e = cudaMemcpyAsync(a.Z, a.C, (size_t)a.M * a.N * 8 * W, cudaMemcpyDeviceToDevice, st);
+        const size_t bytes = (size_t)a.M * a.N * 8 * W;
+        cudaError_t e = a.C ? cudaMemcpyAsync(a.Z, a.C, bytes, cudaMemcpyDeviceToDevice, st)
+                            : cudaMemsetAsync(a.Z, 0, bytes, st);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)bx, (unsigned)by, (unsigned)bz);

@@ -142,6 +142,7 @@ __device__ __forceinline__ Biased<W> biased(const u64* e) {
 struct PrologueParams {
     const u64 *E, *X, *alpha;
     int coef;
+    int one_half;
     int64_t M, K, N;
     int64_t Kp;    // K rounded up to a multiple of KS
     int S_tot;     // 2 Kp / KS
@@ -156,12 +157,13 @@ __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
     constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     {
-        // Z = C (16-byte vectors; M N W is even for every eligible shape)
+        // Z = C, or 0 without an addend (16-byte vectors; M N W is even for
+        // every eligible shape)
         const int64_t nv = p.M * p.N * W / 2;
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C);
         ulonglong2* z2 = reinterpret_cast<ulonglong2*>(p.Z);
-        for (int64_t i = id; i < nv; i += stride) z2[i] = __ldg(c2 + i);
+        for (int64_t i = id; i < nv; i += stride) z2[i] = c2 ? __ldg(c2 + i) : make_ulonglong2(0, 0);
     }
     const int64_t per_tile = (int64_t)p.S_tot * 256;
     const int64_t m_tiles = (p.M + BM - 1) / BM;
@@ -171,8 +173,8 @@ __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
     const int64_t mt = id / per_tile;
     const int64_t m = mt * BM + rg * 8 + r;
     const int64_t kp0 = kstage * KS + kg * 8;      // index in [0, 2 Kp)
-    const bool first_half = kp0 < p.Kp;
-    const int64_t kk = first_half ? kp0 : kp0 - p.Kp;   // K index of the 8 values
+    const bool first_half = !p.one_half && kp0 < p.Kp;
+    const int64_t kk = (first_half || p.one_half) ? kp0 : kp0 - p.Kp;   // K index of the 8 values
     u64 x[8 * W];
 #pragma unroll
     for (int e = 0; e < 8 * W; ++e) x[e] = 0;
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
 struct TcParams {
     const uint8_t* Ap;
     u64* Z;
+    int one_half;
     int64_t M, K, N;
     int64_t Kp;      // padded K half
     int S_tot;       // 16-deep stages per tile (2 Kp / 16)
@@ -369,7 +372,9 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                     ptx::mbar_arrive_expect_tx(&rawFull[r], RAW_BYTES);
                     // rows at or beyond K inside a padded half arrive zero-filled
                     const int64_t kp0 = (int64_t)(x.ii * p.KD + j) * KS;
-                    if (kp0 < p.Kp)
+                    if (p.one_half)
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, x0, (int)kp0, &rawFull[r]);
+                    else if (kp0 < p.Kp)
                         ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, x0, (int)kp0, &rawFull[r]);
                     else
                         ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, x0, (int)(kp0 - p.Kp), &rawFull[r]);
@@ -551,7 +556,7 @@ struct Plan {
     size_t ap_bytes;
 };
 
-Plan make_plan(int64_t M, int64_t K, int64_t N, int words) {
+Plan make_plan(int64_t M, int64_t K, int64_t N, int words, int one_half = 0) {
     Plan pl{};
     pl.KD = words == 1 ? Cfg<1>::KD : Cfg<2>::KD;
     pl.ND = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
@@ -559,7 +564,7 @@ Plan make_plan(int64_t M, int64_t K, int64_t N, int words) {
     pl.m_tiles = (M + BM - 1) / BM;
     pl.n_tiles = (N + pl.ND - 1) / pl.ND;
     pl.Kp = ((K + KS - 1) / KS) * KS;
-    pl.S_tot = (int)(2 * pl.Kp / KS);
+    pl.S_tot = (int)((one_half ? 1 : 2) * pl.Kp / KS);
     pl.I = (pl.S_tot + pl.KD - 1) / pl.KD;
     pl.U = pl.m_tiles * pl.n_tiles * pl.I;
     pl.ap_bytes = (size_t)pl.m_tiles * pl.S_tot * a_stage;
@@ -608,9 +613,10 @@ bool make_map(CUtensorMap* map, const u64* base, int64_t rows, int64_t cols, int
 template <int W>
 cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t st) {
     CUtensorMap tmB, tmF;
-    if (!make_map(&tmB, a.B, a.K, a.N, W, Cfg<W>::ND) || !make_map(&tmF, a.F, a.K, a.N, W, Cfg<W>::ND))
-        return cudaErrorInvalidValue;
-    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z};
+    if (!make_map(&tmF, a.F, a.K, a.N, W, Cfg<W>::ND)) return cudaErrorInvalidValue;
+    if (a.one_half) tmB = tmF;
+    else if (!make_map(&tmB, a.B, a.K, a.N, W, Cfg<W>::ND)) return cudaErrorInvalidValue;
+    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z};
     const int64_t pth = pl.m_tiles * pl.S_tot * 256;
     prologue_kernel<W><<<(unsigned)((pth + 255) / 256), 256, 0, st>>>(pp);
     // the dynamic shared-memory opt-in is set once per device (a host call that
@@ -624,7 +630,7 @@ cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t 
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) smem_set[dev] = true;
     }
-    TcParams tp{Ap, a.Z, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND, pl.n_tiles, pl.U};
+    TcParams tp{Ap, a.Z, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND, pl.n_tiles, pl.U};
     const int sms = sm_count();
     const int64_t grid = pl.U < sms ? pl.U : sms;
     ring_gemm_tc_kernel<W><<<(unsigned)grid, NTHREADS, Layout<W>::SMEM, st>>>(tmB, tmF, tp);
@@ -644,14 +650,14 @@ bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
     return macs >= (words == 1 ? (double)(1 << 22) : (double)(1 << 20));
 }
 
-size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words) {
+size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half) {
     if (!gemm_tc_eligible(M, K, N, words)) return 0;
-    return align256(make_plan(M, K, N, words).ap_bytes);
+    return align256(make_plan(M, K, N, words, one_half).ap_bytes);
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (!gemm_tc_eligible(a.M, a.K, a.N, a.words)) return cudaErrorNotSupported;
-    Plan pl = make_plan(a.M, a.K, a.N, a.words);
+    Plan pl = make_plan(a.M, a.K, a.N, a.words, a.one_half);
     if (ws_bytes < align256(pl.ap_bytes) || ws == nullptr) return cudaErrorInvalidValue;
     uint8_t* Ap = static_cast<uint8_t*>(ws);
     return a.words == 1 ? launch<1>(a, Ap, pl, st) : launch<2>(a, Ap, pl, st);

@@ -22,11 +22,12 @@ struct GemmArgs {
     const u64* E;      // M x K
     const u64* F;      // K x N
     const u64* X;      // M x K
-    const u64* B;      // K x N
-    const u64* C;      // M x N
+    const u64* B;      // K x N (unused when one_half)
+    const u64* C;      // M x N, or NULL for a zero addend
     u64* Z;            // M x N
     int coef;          // CoefMode
     const u64* alpha;  // one element (COEF_ALPHA)
+    int one_half;      // 1: Z = C + (X + cE) . F over K only (the public product E.F)
 };
 
 cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t st);
@@ -34,7 +35,7 @@ cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t st);
 // tensor-core ring GEMM (fp16 digit products, exact); returns
 // cudaErrorNotSupported when the shape is not handled by it.
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
-size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words);
+size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half = 0);
 bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words);
 int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words);
 int tc_timeout_flag(bool* set);   // synchronous; 0 on success
@@ -43,6 +44,7 @@ int tc_timeout_flag(bool* set);   // synchronous; 0 on success
 struct CompactArgs {
     int64_t M, K, N;
     int words;
+    int with_eu;       // 1: the compact tag includes alpha E.(F chi) (untruncated layer)
     const u64* alpha;
     const u64* E;
     const u64* F;
@@ -52,13 +54,18 @@ struct CompactArgs {
     const u64* mR;
     const u64* Dt;
     const u64* chi;
-    u64* mZ;   // M x N
+    u64* mZ;   // M x N, or NULL (the OptMAC tag is not written)
     u64* mDc;  // M
     u64* Dc;   // M
 };
 size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words);
 int compact_launches(int64_t M, int64_t K, int64_t N);
 cudaError_t launch_compact(const CompactArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// truncated layer: OptMAC&Trunc elementwise step
+cudaError_t launch_optmac_trunc(int64_t MN, int words, int k, int f, int party0, const u64* alpha,
+                                const u64* Rf, const u64* mRf, const u64* Dt, const u64* P, u64* Zf,
+                                u64* mZf, cudaStream_t st);
 
 // checks (a6)
 cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u64* chi_hat,

@@ -88,7 +88,7 @@ extern "C" int mpc_linear_tag_compact_noalloc(
     void* scratch = nullptr;
     int st = scratch_address(&scratch);
     if (st != MPC_OK) return st;
-    mpcl::CompactArgs c{M, K, N, r.words, (const mpcl::u64*)alpha_i, (const mpcl::u64*)E,
+    mpcl::CompactArgs c{M, K, N, r.words, 1, (const mpcl::u64*)alpha_i, (const mpcl::u64*)E,
                         (const mpcl::u64*)F, (const mpcl::u64*)mA_i, (const mpcl::u64*)mB_i,
                         (const mpcl::u64*)mC_i, (const mpcl::u64*)mR_i, (const mpcl::u64*)Dtilde,
                         (const mpcl::u64*)chi, (mpcl::u64*)mZ_i, (mpcl::u64*)mDc_i, (mpcl::u64*)Dc};

@@ -67,3 +67,41 @@ def gpu_check_batchrec(ring, alpha, chi, W, mW):
     cs = empty_like_ring((1,), ring.words)
     abi.mpc_tag_check(L, abi.MPC_CHECK_BATCHREC, dev(alpha), dev(chi), dev(W), dev(mW), cs)
     return host(cs)
+
+
+def gpu_share_trunc(ring, party, E, F, A, B, C, nparties=2):
+    M, K = E.shape[:2]
+    N = F.shape[1]
+    L = abi.make_layer(M, K, N, ring.k, ring.s, party, nparties)
+    Z = empty_like_ring((M, N), ring.words)
+    abi.mpc_linear_share_trunc(L, dev(E), dev(F), dev(A), dev(B), dev(C), Z)
+    return host(Z)
+
+
+def gpu_public_product(ring, E, F):
+    M, K = E.shape[:2]
+    N = F.shape[1]
+    L = abi.make_layer(M, K, N, ring.k, ring.s)
+    P = empty_like_ring((M, N), ring.words)
+    abi.mpc_public_product(L, dev(E), dev(F), P)
+    return host(P)
+
+
+def gpu_optmac_trunc(ring, party, f, alpha, Rf, mRf, Dt, P, nparties=2):
+    M, N = Rf.shape[:2]
+    L = abi.make_layer(M, 1, N, ring.k, ring.s, party, nparties)
+    Zf = empty_like_ring((M, N), ring.words)
+    mZf = empty_like_ring((M, N), ring.words)
+    abi.mpc_optmac_trunc(L, f, dev(alpha), dev(Rf), dev(mRf), dev(Dt), dev(P), Zf, mZf)
+    return host(Zf), host(mZf)
+
+
+def gpu_tag_compact_trunc(ring, party, alpha, E, F, mA, mB, mC, mR, Dt, chi, nparties=2):
+    M, K = E.shape[:2]
+    N = F.shape[1]
+    L = abi.make_layer(M, K, N, ring.k, ring.s, party, nparties)
+    mDc = empty_like_ring((M,), ring.words)
+    Dc = empty_like_ring((M,), ring.words)
+    abi.mpc_linear_tag(L, abi.MPC_TAG_COMPACT_TRUNC, dev(alpha), dev(E), dev(F), dev(mA), dev(mB),
+                       dev(mC), None, mR_i=dev(mR), Dtilde=dev(Dt), chi=dev(chi), mDc_i=mDc, Dc=Dc)
+    return host(mDc), host(Dc)
