@@ -51,10 +51,18 @@ WORKLOADS = {
 L2_BYTES = 129 * 2**20
 
 
+PROTOCOL = "plain"        # set from --protocol in main()
+TRUNC_F = 16
+
+
 def layer_units(L) -> dict:
     M, K, N = L.M, L.K, L.N
-    return dict(share=2 * M * K * N, full=2 * M * K * N,
-                compact=costmodel.compact_tag_mults(M, K, N), check=M)
+    u = dict(share=2 * M * K * N, full=2 * M * K * N,
+             compact=costmodel.compact_tag_mults(M, K, N), check=M)
+    if PROTOCOL == "trunc":
+        u["public"] = M * K * N          # E.F, computed by every party
+        u["optmac_trunc"] = M * N
+    return u
 
 
 def step_units(layers) -> int:
@@ -201,6 +209,9 @@ def host_inputs(layers, seed=SEED):
                 C=_uniform(sd, "C", p + 1, (M, N), b), mA=_uniform(sd, "mA", p + 1, (M, K), b),
                 mB=_uniform(sd, "mB", p + 1, (K, N), b), mC=_uniform(sd, "mC", p + 1, (M, N), b),
                 mR=_uniform(sd, "mR", p + 1, (M, N), b)))
+            if PROTOCOL == "trunc":
+                parties[-1].update(Rf=_uniform(sd, "Rf", p + 1, (M, N), b),
+                                   mRf=_uniform(sd, "mRf", p + 1, (M, N), b))
         out.append((L, pub, parties))
     return out
 
@@ -222,11 +233,15 @@ class GpuRun:
                 lay = abi.make_layer(M, K, N, RING.k, RING.s, p, PARTIES)
                 d = {k: t(v).cuda() for k, v in sh.items()}
                 d["Z"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
-                d["mZf"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
+                d["mZfull"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
                 d["mZ"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
                 d["mDc"] = torch.empty(ring_shape(M), dtype=torch.int64, device="cuda")
                 d["Dc"] = torch.empty(ring_shape(M), dtype=torch.int64, device="cuda")
                 d["cs"] = torch.empty(ring_shape(1), dtype=torch.int64, device="cuda")
+                if PROTOCOL == "trunc":
+                    d["P"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
+                    d["Zf"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
+                    d["mZf_t"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
                 d["layer"] = lay
                 nws = max(abi.mpc_workspace_size(lay, w) for w in range(5))
                 d["ws"] = torch.empty(max(nws, 256), dtype=torch.uint8, device="cuda")
@@ -238,29 +253,45 @@ class GpuRun:
                 for k, v in pub.items():
                     self.h2d_pairs.append((t(v).pin_memory(), dpub[k]))
             self.items.append((L, dpub, dpar))
-        self.outputs = [d[k] for _, _, dpar in self.items for d in dpar
-                        for k in ("Z", "mZf", "mZ", "mDc", "Dc", "cs")]
+        out_keys = ("Z", "mZfull", "mZ", "mDc", "Dc", "cs") if PROTOCOL == "plain" else \
+            ("Z", "mZfull", "Zf", "mZf_t", "mDc", "Dc", "cs")
+        self.outputs = [d[k] for _, _, dpar in self.items for d in dpar for k in out_keys]
         self.h_outputs = [o.cpu().pin_memory() for o in self.outputs] if pinned_host else []
 
     # one call of each kind
     def share(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
-        self.abi.mpc_linear_share(d["layer"], pub["E"], pub["F"], d["A"], d["B"], d["C"], d["Z"],
-                                  ws=d["ws"])
+        if PROTOCOL == "trunc":
+            # share without E.F, and the public E.F that both protocols add after truncation
+            self.abi.mpc_linear_share_trunc(d["layer"], pub["E"], pub["F"], d["A"], d["B"], d["C"], d["Z"],
+                                            ws=d["ws"])
+            self.abi.mpc_public_product(d["layer"], pub["E"], pub["F"], d["P"], ws=d["ws"])
+        else:
+            self.abi.mpc_linear_share(d["layer"], pub["E"], pub["F"], d["A"], d["B"], d["C"], d["Z"],
+                                      ws=d["ws"])
 
     def full(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
         self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_FULL, d["alpha"], pub["E"], pub["F"],
-                                d["mA"], d["mB"], d["mC"], d["mZf"], ws=d["ws"])
+                                d["mA"], d["mB"], d["mC"], d["mZfull"], ws=d["ws"])
 
     def compact(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
-        self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_COMPACT, d["alpha"], pub["E"], pub["F"],
-                                d["mA"], d["mB"], d["mC"], d["mZ"], mR_i=d["mR"], Dtilde=pub["Dt"],
-                                chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"], ws=d["ws"])
+        if PROTOCOL == "trunc":
+            # OptMAC&Trunc (share and tag), compact tag without the E.U term
+            self.abi.mpc_optmac_trunc(d["layer"], TRUNC_F, d["alpha"], d["Rf"], d["mRf"], pub["Dt"], d["P"],
+                                      d["Zf"], d["mZf_t"])
+            self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_COMPACT_TRUNC, d["alpha"], pub["E"],
+                                    pub["F"], d["mA"], d["mB"], d["mC"], None, mR_i=d["mR"],
+                                    Dtilde=pub["Dt"], chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"],
+                                    ws=d["ws"])
+        else:
+            self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_COMPACT, d["alpha"], pub["E"], pub["F"],
+                                    d["mA"], d["mB"], d["mC"], d["mZ"], mR_i=d["mR"], Dtilde=pub["Dt"],
+                                    chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"], ws=d["ws"])
         self.abi.mpc_tag_check(d["layer"], self.abi.MPC_CHECK_COMPACT, d["alpha"], pub["chi_hat"],
                                d["Dc"], d["mDc"], d["cs"], ws=d["ws"])
 
@@ -273,13 +304,15 @@ class GpuRun:
 
     def launches_per_step(self):
         """Kernels one step enqueues, as the library reports them."""
+        a = self.abi
+        which = (a.MPC_WS_SHARE, a.MPC_WS_TAG_FULL, a.MPC_WS_TAG_COMPACT, a.MPC_WS_CHECK_COMPACT)
+        if PROTOCOL == "trunc":
+            which = (a.MPC_WS_SHARE_TRUNC, a.MPC_WS_TAG_FULL, a.MPC_WS_PUBLIC_PRODUCT,
+                     a.MPC_WS_OPTMAC_TRUNC, a.MPC_WS_TAG_COMPACT, a.MPC_WS_CHECK_COMPACT)
         n = 0
         for L, _, par in self.items:
             for d in par:
-                lay = d["layer"]
-                n += sum(self.abi.mpc_launch_count(lay, w) for w in (
-                    self.abi.MPC_WS_SHARE, self.abi.MPC_WS_TAG_FULL, self.abi.MPC_WS_TAG_COMPACT,
-                    self.abi.MPC_WS_CHECK_COMPACT))
+                n += sum(a.mpc_launch_count(d["layer"], w) for w in which)
         return n
 
     def h2d(self):
@@ -506,7 +539,9 @@ def run_ours(args):
             "ms_per_step_eager_api": eager_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (uniform ring words from seeded SplitMix64; shapes of the paper's layers)",
-            "config": {"workload": workload,
+            "config": {"workload": workload + ("" if PROTOCOL == "plain" else f"_truncated_f{TRUNC_F}"),
+                       "protocol": "CompactTag with OptMAC&Trunc (truncated layer)" if PROTOCOL == "trunc"
+                       else "CompactTag (untruncated layer) beside the SPDZ2k full tag",
                        "layers": [[L.M, L.K, L.N] for L in layers],
                        "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
                        "parties": PARTIES, "parallelism": f"replicas x{ws}",
@@ -644,9 +679,13 @@ def main():
     ap.add_argument("--batch", type=int, default=1, help="batch size for vgg16 / resnet18")
     ap.add_argument("--ring", type=int, choices=[64, 128], default=64,
                     help="share ring Z_2^64 (k=s=32) or Z_2^128 (k=s=64)")
+    ap.add_argument("--protocol", choices=["plain", "trunc"], default="plain",
+                    help="trunc: the truncated layer (share without E.F, public product, "
+                         "OptMAC&Trunc, compact tag without the E.F term)")
     args = ap.parse_args()
-    global RING
+    global RING, PROTOCOL
     RING = synth.Z64 if args.ring == 64 else synth.Z128
+    PROTOCOL = args.protocol
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

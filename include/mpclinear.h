@@ -54,7 +54,11 @@ typedef struct {
 } mpc_layer;
 
 typedef enum { MPC_TAG_FULL = 0, MPC_TAG_COMPACT = 1, MPC_TAG_COMPACT_TRUNC = 2 } mpc_tag_mode;
-typedef enum { MPC_CHECK_COMPACT = 0, MPC_CHECK_BATCHREC = 1 } mpc_check_mode;
+typedef enum {
+    MPC_CHECK_COMPACT = 0,
+    MPC_CHECK_BATCHREC = 1,
+    MPC_CHECK_BATCHREC_SEEDED = 2
+} mpc_check_mode;
 
 /* `which` argument of mpc_workspace_size */
 enum {
@@ -139,6 +143,15 @@ int mpc_linear_tag(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
  * MPC_CHECK_BATCHREC -- tag check of Fig. Pi_BatchRec (§2.5) steps 2-3:
  *   cs_i = sum_{p,q} chi_pq * (mW_i_pq - alpha_i * W_pq)
  *   chi_hat = chi: M x N, opened = W: M x N, tag_i = mW_i: M x N.
+ * MPC_CHECK_BATCHREC_SEEDED -- the same check with the combiners expanded
+ *   from a public coin-tossed seed (F_Rand, App. A.1) instead of stored:
+ *   chi_hat points to ONE 64-bit word, the seed, in device memory, and
+ *   chi_pq (row-major index i = p N + q) = SplitMix64 output i of the sequence
+ *   whose state starts at the seed, mod 2^s (s = layer->ring.s <= 64):
+ *     chi_i = mix(seed + (i + 1) * 0x9E3779B97F4A7C15),
+ *     mix(z) = ((z ^ z>>30) * 0xBF58476D1CE4E5B9 -> z ^ z>>27) * 0x94D049BB133111EB -> z ^ z>>31.
+ *   The check then reads only W and mW_i.
+ * The BATCHREC modes use a workspace (MPC_WS_CHECK_BATCHREC).
  */
 int mpc_tag_check(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
                   const uint64_t *chi_hat, const uint64_t *opened,
@@ -171,6 +184,20 @@ int mpc_linear_tag_compact_noalloc(const mpc_layer *layer, const uint64_t *alpha
                                    const uint64_t *Dtilde, const uint64_t *chi,
                                    uint64_t *mZ_i, uint64_t *mDc_i, uint64_t *Dc,
                                    void *stream);
+
+/*
+ * Pi_BatchRec open phase step 1 (§2.5) for an opened difference V = X - A
+ * (E = X - A or U = Y - B, Fig. Pi_MatMul step 1), rows x cols elements:
+ *   W_i = X_i - A_i + R_i,   mW_i = mX_i - mA_i + mR_i
+ * R_i, mR_i: shares of a mask that is 0 mod 2^k and of its tag (so the opened
+ * W equals V mod 2^k while its top s bits are masked).  A_i and mA_i may be
+ * NULL (V = X).  W_i is the share each party broadcasts; mW_i is kept for the
+ * tag check (mpc_tag_check BATCHREC modes).  No workspace.
+ */
+int mpc_batchrec_mask(const mpc_ring *ring, int64_t rows, int64_t cols,
+                      const uint64_t *X_i, const uint64_t *A_i, const uint64_t *R_i,
+                      const uint64_t *mX_i, const uint64_t *mA_i, const uint64_t *mR_i,
+                      uint64_t *W_i, uint64_t *mW_i, void *stream);
 
 /*
  * Truncated layer (Fig. Pi_CompactMatMul with Fig. Pi_OptMAC&Trunc, §3.4).

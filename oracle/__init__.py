@@ -70,6 +70,8 @@ def _load():
                 "orc_compact_tag": (_int, [_int, _i64, _i64, _i64] + [_u64p] * 12),
                 "orc_check_compact": (None, [_int, _i64] + [_u64p] * 5),
                 "orc_linear_share_trunc": (None, [_int, _i64, _i64, _i64] + [_u64p] * 6),
+                "orc_batchrec_mask": (None, [_int, _i64] + [_u64p] * 8),
+                "orc_chi_seeded": (None, [_int, _int, ctypes.c_uint64, _i64, _u64p]),
                 "orc_optmac_trunc": (None, [_int, _int, _i64, _i64, _int, _int] + [_u64p] * 7),
                 "orc_compact_tag_trunc": (_int, [_int, _i64, _i64, _i64] + [_u64p] * 12),
                 "orc_check_compact_literal": (_int, [_int, _int, _i64] + [_u64p] * 5),
@@ -305,3 +307,25 @@ def compact_tag_trunc(bits, alpha, E, F, mA, mB, mC, mR, Dt, chi):
     if rc != 0:
         raise MemoryError("oracle compact_tag_trunc: allocation failed")
     return mDc, Dc, mZc
+
+
+# ---------------------------------------------------------------------------
+# Pi_BatchRec open phase and seeded combiners
+
+def batchrec_mask(bits, X, A, R, mX, mA, mR):
+    """([W]_i, [m(W)]_i) = ([X]_i - [A]_i + [R]_i, [m(X)]_i - [m(A)]_i + [m(R)]_i)."""
+    W, mW = np.empty_like(X), np.empty_like(X)
+    _load().orc_batchrec_mask(bits, _n(X, bits), _p(X), _p(A), _p(R), _p(mX), _p(mA), _p(mR),
+                              _p(W), _p(mW))
+    return W, mW
+
+
+def chi_seeded(bits, s, seed, shape):
+    """Public combiners in [0, 2^s), s <= 64: the SplitMix64 sequence started at `seed`."""
+    if not 1 <= s <= 64:
+        raise ValueError("combiners are drawn from Z_2^s with s <= 64")
+    shape = tuple(shape)
+    out = _new(bits, *shape)
+    n = int(np.prod(shape, dtype=np.int64)) if shape else 1
+    _load().orc_chi_seeded(bits, s, int(seed) & 0xFFFFFFFFFFFFFFFF, n, _p(out))
+    return out

@@ -218,3 +218,38 @@ def run_layer_trunc(t: TruncDeal, tamper=None):
     cs = [O.check_compact(bits, p.alpha, d.chi_hat, Dc, m) for p, m in zip(d.parties, mDc)]
     return dict(Z=Z, Dt=Dt, P=P, Zf=[o[0] for o in outs], mZf=[o[1] for o in outs], mDc=mDc,
                 Dc=Dc, mZc=[c[2] for c in comp], cs=cs, cs_total=total(bits, cs))
+
+
+# ---------------------------------------------------------------------------
+# Pi_BatchRec: authenticated shares of a value V (as X - A) and of a mask R with
+# R~ = 2^k r (so R~ = 0 mod 2^k), both with tags, for n parties.
+
+@dataclass
+class RecDeal:
+    ring: synth.Ring
+    alpha: np.ndarray
+    alphas: list
+    V: np.ndarray                 # reconstructed X - A
+    X: list = field(default_factory=list)
+    A: list = field(default_factory=list)
+    R: list = field(default_factory=list)
+    mX: list = field(default_factory=list)
+    mA: list = field(default_factory=list)
+    mR: list = field(default_factory=list)
+
+
+def deal_batchrec(ring: synth.Ring, rows: int, cols: int, n: int = 2, seed: int = 1) -> RecDeal:
+    bits = ring.bits
+    T = synth.TID
+    alphas = [key_range(ring, seed, T["alpha"], i, (1,)) for i in range(n)]
+    alpha = total(bits, alphas)
+    shape = (rows, cols)
+    Xt = synth.uniform(seed, T["X"], 50, shape, bits)
+    At = synth.uniform(seed, T["A"], 50, shape, bits)
+    r = synth.uniform(seed, T["W"], 50, shape, ring.s)
+    Rt = O.from_int(np.vectorize(lambda v: int(v) << ring.k, otypes=[object])(O.to_int(_store(bits, r), bits)), bits)
+    d = RecDeal(ring, alpha, alphas, O.sub(bits, Xt, At))
+    for name, V, lst, mlst in (("X", Xt, d.X, d.mX), ("A", At, d.A, d.mA), ("R", Rt, d.R, d.mR)):
+        lst += _share(bits, seed, T[name] + 60, V, n, shape)
+        mlst += _share(bits, seed, T[name] + 160, O.smul(bits, alpha, V), n, shape)
+    return d

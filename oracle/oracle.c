@@ -350,3 +350,37 @@ void orc_check_batchrec(int b, i64 M, i64 N, const u64 *alpha, const u64 *chi,
     }
     st(cs, 0, w, acc & m);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Pi_BatchRec (§2.5), open phase step 1 for an opened difference V = X - A:   */
+/*   [W]_i = [X]_i - [A]_i + [R]_i,  [m(W)]_i = [m(X)]_i - [m(A)]_i + [m(R)]_i  */
+/* where R is a sharing of a matrix that is 0 mod 2^k.  A and mA may be NULL  */
+/* (then V = X).                                                             */
+void orc_batchrec_mask(int b, i64 n, const u64 *X, const u64 *A, const u64 *R,
+                       const u64 *mX, const u64 *mA, const u64 *mR, u64 *W, u64 *mW) {
+    int w = words_of(b); u128 m = mask_of(b);
+    for (i64 i = 0; i < n; ++i) {
+        u128 v = ld(X, i, w) - (A ? ld(A, i, w) : 0) + ld(R, i, w);
+        u128 t = ld(mX, i, w) - (mA ? ld(mA, i, w) : 0) + ld(mR, i, w);
+        st(W, i, w, v & m);
+        st(mW, i, w, t & m);
+    }
+}
+
+/* Public combiners from a coin-tossed seed (F_Rand, App. A.1, expanded by a */
+/* PRG): the SplitMix64 sequence (Steele, Lea & Flood 2014) whose state starts */
+/* at `seed`: chi_i = mix(seed + (i + 1) GAMMA) mod 2^s, s <= 64, with        */
+/* mix(z): z = (z ^ (z >> 30)) C1; z = (z ^ (z >> 27)) C2; z ^ (z >> 31).     */
+static u64 splitmix_mix(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void orc_chi_seeded(int b, int s, u64 seed, i64 n, u64 *out) {
+    int w = words_of(b);
+    const u64 g = 0x9E3779B97F4A7C15ULL;
+    u128 ms = mask_of(s);
+    for (i64 i = 0; i < n; ++i)
+        st(out, i, w, (u128)splitmix_mix(seed + (u64)(i + 1) * g) & ms);
+}

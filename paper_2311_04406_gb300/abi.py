@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 MPC_TAG_FULL, MPC_TAG_COMPACT, MPC_TAG_COMPACT_TRUNC = 0, 1, 2
-MPC_CHECK_COMPACT, MPC_CHECK_BATCHREC = 0, 1
+MPC_CHECK_COMPACT, MPC_CHECK_BATCHREC, MPC_CHECK_BATCHREC_SEEDED = 0, 1, 2
 (MPC_WS_SHARE, MPC_WS_TAG_FULL, MPC_WS_TAG_COMPACT, MPC_WS_CHECK_COMPACT, MPC_WS_CHECK_BATCHREC,
  MPC_WS_PUBLIC_PRODUCT, MPC_WS_OPTMAC_TRUNC, MPC_WS_SHARE_TRUNC) = range(8)
 
@@ -30,7 +30,7 @@ ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_wor
                  "mpc_gemm_path", "mpc_launch_count", "mpc_device_status", "mpc_status_str",
                  "mpc_version",
                  "mpc_linear_tag_compact_noalloc", "mpc_linear_share_trunc", "mpc_public_product",
-                 "mpc_optmac_trunc")
+                 "mpc_optmac_trunc", "mpc_batchrec_mask")
 MPC_E_SCRATCH_LIMIT = -10
 MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
@@ -88,6 +88,9 @@ def load(build_if_missing: bool = False):
         lib.mpc_public_product.restype = ctypes.c_int
         lib.mpc_optmac_trunc.argtypes = [L, ctypes.c_int] + [P] * 7 + [P]
         lib.mpc_optmac_trunc.restype = ctypes.c_int
+        lib.mpc_batchrec_mask.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int64] + \
+            [P] * 8 + [P]
+        lib.mpc_batchrec_mask.restype = ctypes.c_int
         lib.mpc_launch_count.argtypes = [L, ctypes.c_int]
         lib.mpc_launch_count.restype = ctypes.c_int
         lib.mpc_device_status.argtypes = []
@@ -227,3 +230,12 @@ def mpc_optmac_trunc(layer, f, alpha_i, Rf_i, mRf_i, Dtilde, P, Zf_i, mZf_i, str
         ctypes.byref(layer), int(f), _ptr(alpha_i), _ptr(Rf_i), _ptr(mRf_i), _ptr(Dtilde), _ptr(P),
         _ptr(Zf_i), _ptr(mZf_i), _stream(stream)))
     return Zf_i, mZf_i
+
+
+def mpc_batchrec_mask(k, s, rows, cols, X_i, A_i, R_i, mX_i, mA_i, mR_i, W_i, mW_i, stream=None):
+    """Pi_BatchRec open phase step 1: W_i = X_i - A_i + R_i and the same for the tags."""
+    ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
+    _check("mpc_batchrec_mask", load().mpc_batchrec_mask(
+        ctypes.byref(ring), int(rows), int(cols), _ptr(X_i), _ptr(A_i), _ptr(R_i), _ptr(mX_i),
+        _ptr(mA_i), _ptr(mR_i), _ptr(W_i), _ptr(mW_i), _stream(stream)))
+    return W_i, mW_i

@@ -158,6 +158,29 @@ int mpc_linear_share(const mpc_layer* L, const uint64_t* E, const uint64_t* F,
     return run_gemm(g, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+int mpc_batchrec_mask(const mpc_ring* ring, int64_t rows, int64_t cols, const uint64_t* X_i,
+                      const uint64_t* A_i, const uint64_t* R_i, const uint64_t* mX_i,
+                      const uint64_t* mA_i, const uint64_t* mR_i, uint64_t* W_i, uint64_t* mW_i,
+                      void* stream) {
+    if (!ring) return MPC_E_NULL;
+    if (!ring_ok(*ring)) return MPC_E_RING;
+    if (rows < 0 || cols < 0 || rows > kMaxDim || cols > kMaxDim || rows * cols > kMaxElems)
+        return MPC_E_SHAPE;
+    const int64_t n = rows * cols;
+    CHK(check_ptr(X_i, n));
+    CHK(check_ptr(R_i, n));
+    CHK(check_ptr(mX_i, n));
+    CHK(check_ptr(mR_i, n));
+    CHK(check_ptr(W_i, n));
+    CHK(check_ptr(mW_i, n));
+    if (A_i) CHK(check_ptr(A_i, n));
+    if (mA_i) CHK(check_ptr(mA_i, n));
+    return cuda_status(mpcl::launch_batchrec_mask(n, ring->words, (const u64*)X_i, (const u64*)A_i,
+                                                  (const u64*)R_i, (const u64*)mX_i, (const u64*)mA_i,
+                                                  (const u64*)mR_i, (u64*)W_i, (u64*)mW_i,
+                                                  (cudaStream_t)stream));
+}
+
 int mpc_linear_share_trunc(const mpc_layer* L, const uint64_t* E, const uint64_t* F,
                            const uint64_t* A_i, const uint64_t* B_i, const uint64_t* C_i,
                            uint64_t* Z_i, void* ws, size_t ws_bytes, void* stream) {
@@ -264,6 +287,18 @@ int mpc_tag_check(const mpc_layer* L, int mode, const uint64_t* alpha_i,
         return cuda_status(mpcl::launch_check_compact(M, w, (const u64*)alpha_i,
                                                       (const u64*)chi_hat, (const u64*)opened,
                                                       (const u64*)tag_i, (u64*)cs_i, st));
+    }
+    if (mode == MPC_CHECK_BATCHREC_SEEDED) {
+        if (L->ring.s > 64) return MPC_E_RING;
+        CHK(check_ptr(chi_hat, 1));
+        CHK(check_ptr(opened, M * N));
+        CHK(check_ptr(tag_i, M * N));
+        const size_t need = mpcl::check_batchrec_workspace(M, N, w);
+        if (!ws || ws_bytes < need) return MPC_E_WORKSPACE;
+        if (reinterpret_cast<uintptr_t>(ws) % 16 != 0) return MPC_E_ALIGN;
+        return cuda_status(mpcl::launch_check_batchrec_seeded(
+            M, N, w, L->ring.s, (const u64*)alpha_i, (const u64*)chi_hat, (const u64*)opened,
+            (const u64*)tag_i, (u64*)cs_i, ws, ws_bytes, st));
     }
     if (mode != MPC_CHECK_BATCHREC) return MPC_E_MODE;
     CHK(check_ptr(chi_hat, M * N));

@@ -68,6 +68,50 @@ __global__ void __launch_bounds__(NT) batchrec_partial_kernel(int64_t n, const u
     if (threadIdx.x == 0) st_elem<W>(part, blockIdx.x, tot);
 }
 
+// Combiners expanded from a public seed: the SplitMix64 sequence whose state
+// starts at the seed (Steele, Lea & Flood 2014), chi_i = mix(seed + (i+1) g)
+// mod 2^s.  Generated in registers, so the check reads only W and m(W).
+__device__ __forceinline__ u64 splitmix64_at(u64 seed, int64_t i) {
+    u64 z = seed + (u64)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) batchrec_seeded_partial_kernel(int64_t n, int s, const u64* alpha,
+                                                                     const u64* seedp, const u64* Wm,
+                                                                     const u64* mW, u64* part) {
+    using T = typename Elem<W>::T;
+    const T a = ld_elem<W>(alpha, 0);
+    const u64 seed = seedp[0];
+    const u64 ms = s >= 64 ? ~0ull : ((1ull << s) - 1);
+    T acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+        const T x = (T)(splitmix64_at(seed, i) & ms);
+        acc += ldg_elem<W>(mW, i) * x - a * (ldg_elem<W>(Wm, i) * x);
+    }
+    T tot = block_sum<W>(acc);
+    if (threadIdx.x == 0) st_elem<W>(part, blockIdx.x, tot);
+}
+
+// Pi_BatchRec open phase step 1: [W]_i = [X]_i - [A]_i + [R]_i and the same
+// combination of the tag shares (A, mA may be NULL)
+template <int W>
+__global__ void __launch_bounds__(NT) batchrec_mask_kernel(int64_t n, const u64* X, const u64* A,
+                                                           const u64* R, const u64* mX, const u64* mA,
+                                                           const u64* mR, u64* Wo, u64* mWo) {
+    using T = typename Elem<W>::T;
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+        T v = ldg_elem<W>(X, i) + ldg_elem<W>(R, i);
+        T t = ldg_elem<W>(mX, i) + ldg_elem<W>(mR, i);
+        if (A) v -= ldg_elem<W>(A, i);
+        if (mA) t -= ldg_elem<W>(mA, i);
+        st_elem<W>(Wo, i, v);
+        st_elem<W>(mWo, i, t);
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(NT) sum_kernel(int64_t n, const u64* part, u64* out) {
     using T = typename Elem<W>::T;
@@ -90,6 +134,34 @@ cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u
                                  const u64* Dc, const u64* mDc, u64* cs, cudaStream_t st) {
     if (words == 1) check_compact_kernel<1><<<1, NT, 0, st>>>(M, alpha, chi_hat, Dc, mDc, cs);
     else check_compact_kernel<2><<<1, NT, 0, st>>>(M, alpha, chi_hat, Dc, mDc, cs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_batchrec_seeded(int64_t M, int64_t N, int words, int s, const u64* alpha,
+                                         const u64* seed, const u64* Wm, const u64* mW, u64* cs,
+                                         void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int64_t n = M * N;
+    const int64_t blocks = batchrec_blocks(n);
+    if (ws_bytes < (size_t)blocks * 8 * (size_t)words) return cudaErrorInvalidValue;
+    u64* part = (u64*)ws;
+    if (words == 1) {
+        batchrec_seeded_partial_kernel<1><<<(unsigned)blocks, NT, 0, st>>>(n, s, alpha, seed, Wm, mW, part);
+        sum_kernel<1><<<1, NT, 0, st>>>(blocks, part, cs);
+    } else {
+        batchrec_seeded_partial_kernel<2><<<(unsigned)blocks, NT, 0, st>>>(n, s, alpha, seed, Wm, mW, part);
+        sum_kernel<2><<<1, NT, 0, st>>>(blocks, part, cs);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batchrec_mask(int64_t n, int words, const u64* X, const u64* A, const u64* R,
+                                 const u64* mX, const u64* mA, const u64* mR, u64* Wo, u64* mWo,
+                                 cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + NT - 1) / NT;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (words == 1) batchrec_mask_kernel<1><<<(unsigned)blocks, NT, 0, st>>>(n, X, A, R, mX, mA, mR, Wo, mWo);
+    else batchrec_mask_kernel<2><<<(unsigned)blocks, NT, 0, st>>>(n, X, A, R, mX, mA, mR, Wo, mWo);
     return cudaGetLastError();
 }
 

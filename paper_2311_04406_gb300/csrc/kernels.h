@@ -71,6 +71,12 @@ cudaError_t launch_optmac_trunc(int64_t MN, int words, int k, int f, int party0,
 cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u64* chi_hat,
                                  const u64* Dc, const u64* mDc, u64* cs, cudaStream_t st);
 size_t check_batchrec_workspace(int64_t M, int64_t N, int words);
+cudaError_t launch_check_batchrec_seeded(int64_t M, int64_t N, int words, int s, const u64* alpha,
+                                         const u64* seed, const u64* W, const u64* mW, u64* cs,
+                                         void* ws, size_t ws_bytes, cudaStream_t st);
+cudaError_t launch_batchrec_mask(int64_t n, int words, const u64* X, const u64* A, const u64* R,
+                                 const u64* mX, const u64* mA, const u64* mR, u64* W, u64* mW,
+                                 cudaStream_t st);
 cudaError_t launch_check_batchrec(int64_t M, int64_t N, int words, const u64* alpha,
                                   const u64* chi, const u64* W, const u64* mW, u64* cs,
                                   void* ws, size_t ws_bytes, cudaStream_t st);
