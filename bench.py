@@ -47,12 +47,15 @@ WORKLOADS = {
     "vgg16": ("vgg16_32x32x3_b{b}", lambda b: synth.vgg16_layers(b)),
     "resnet18": ("resnet18_32x32x3_b{b}", lambda b: synth.resnet18_layers(b)),
     "transformer": ("transformer_h1024_t2048", lambda b: synth.transformer_layers()),
+    "uneven": ("uneven256_seeded", lambda b: synth.uneven_layers(256)),
+    "serve": ("serve_resnet18_vgg16_b1-32_z128_poisson", None),
 }
 L2_BYTES = 129 * 2**20
 
 
 PROTOCOL = "plain"        # set from --protocol in main()
 TRUNC_F = 16
+PASS = "forward"          # set from --pass in main(); "train" adds the backward layers
 
 
 def layer_units(L) -> dict:
@@ -191,8 +194,20 @@ def ring_shape(*dims):
     return tuple(dims) + ((2,) if RING.words == 2 else ())
 
 
+_HOST_CACHE = {}
+
+
 def host_inputs(layers, seed=SEED):
-    """Uniform inputs per layer: public E, F, D~, chi, chi^ and per-party shares."""
+    """Uniform inputs per layer: public E, F, D~, chi, chi^ and per-party shares
+    (generated once per layer list and seed)."""
+    key = (tuple((L.name, L.M, L.K, L.N) for L in layers), seed, PROTOCOL, RING)
+    if key not in _HOST_CACHE:
+        _HOST_CACHE.clear()
+        _HOST_CACHE[key] = _host_inputs(layers, seed)
+    return _HOST_CACHE[key]
+
+
+def _host_inputs(layers, seed):
     out = []
     b = RING.bits
     for li, L in enumerate(layers):
@@ -225,7 +240,19 @@ class GpuRun:
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64))
         self.items = []
         self.h2d_pairs = []   # (host pinned, device) for the e2e copy
-        for L, pub, parties in hi:
+        # backward layers: operands that are transposes of forward operands
+        # (index of the forward layer, public key, share key, tag key, forward dims)
+        names = {L.name: i for i, L in enumerate(layers)}
+        self.links = {}
+        for i, L in enumerate(layers):
+            for suf, keys in (("_dX", ("F", "B", "mB")), ("_dW", ("E", "A", "mA"))):
+                if L.name.endswith(suf) and L.name[:-3] in names:
+                    j = names[L.name[:-3]]
+                    Lf = layers[j]
+                    dims = (Lf.K, Lf.N) if suf == "_dX" else (Lf.M, Lf.K)
+                    self.links[i] = (j,) + keys + (dims,)
+        for li, (L, pub, parties) in enumerate(hi):
+            derived = set(self.links[li][1:4]) if li in self.links else set()
             M, K, N = L.M, L.K, L.N
             dpub = {k: t(v).cuda() for k, v in pub.items()}
             dpar = []
@@ -248,20 +275,41 @@ class GpuRun:
                 dpar.append(d)
                 if pinned_host:
                     for k, v in sh.items():
-                        self.h2d_pairs.append((t(v).pin_memory(), d[k]))
+                        if k not in derived:
+                            self.h2d_pairs.append((t(v).pin_memory(), d[k]))
             if pinned_host:
                 for k, v in pub.items():
-                    self.h2d_pairs.append((t(v).pin_memory(), dpub[k]))
+                    if k not in derived:
+                        self.h2d_pairs.append((t(v).pin_memory(), dpub[k]))
             self.items.append((L, dpub, dpar))
         out_keys = ("Z", "mZfull", "mZ", "mDc", "Dc", "cs") if PROTOCOL == "plain" else \
             ("Z", "mZfull", "Zf", "mZf_t", "mDc", "Dc", "cs")
         self.outputs = [d[k] for _, _, dpar in self.items for d in dpar for k in out_keys]
         self.h_outputs = [o.cpu().pin_memory() for o in self.outputs] if pinned_host else []
 
+    def _transpose(self, src, dst, rows, cols):
+        self.abi.mpc_transpose(RING.k, RING.s, rows, cols, src, dst)
+
+    def _pre(self, i, p, tag):
+        """A backward layer's party first transposes, locally, the forward
+        operands it reuses: the public opening and its mask share before the
+        share GEMM, its tag share before a tag."""
+        if i not in self.links:
+            return
+        j, kpub, ksh, ktag, (rows, cols) = self.links[i]
+        _, fpub, fpar = self.items[j]
+        _, pub, par = self.items[i]
+        if tag:
+            self._transpose(fpar[p][ktag], par[p][ktag], rows, cols)
+        else:
+            self._transpose(fpub[kpub], pub[kpub], rows, cols)
+            self._transpose(fpar[p][ksh], par[p][ksh], rows, cols)
+
     # one call of each kind
     def share(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
+        self._pre(i, p, tag=False)
         if PROTOCOL == "trunc":
             # share without E.F, and the public E.F that both protocols add after truncation
             self.abi.mpc_linear_share_trunc(d["layer"], pub["E"], pub["F"], d["A"], d["B"], d["C"], d["Z"],
@@ -274,12 +322,14 @@ class GpuRun:
     def full(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
+        self._pre(i, p, tag=True)
         self.abi.mpc_linear_tag(d["layer"], self.abi.MPC_TAG_FULL, d["alpha"], pub["E"], pub["F"],
                                 d["mA"], d["mB"], d["mC"], d["mZfull"], ws=d["ws"])
 
     def compact(self, i, p):
         L, pub, par = self.items[i]
         d = par[p]
+        self._pre(i, p, tag=True)
         if PROTOCOL == "trunc":
             # OptMAC&Trunc (share and tag), compact tag without the E.U term
             self.abi.mpc_optmac_trunc(d["layer"], TRUNC_F, d["alpha"], d["Rf"], d["mRf"], pub["Dt"], d["P"],
@@ -302,6 +352,64 @@ class GpuRun:
                 self.full(i, p)
                 self.compact(i, p)
 
+    # grouped calls: every layer of one party in one call of each kind
+    def setup_grouped(self):
+        a, torch = self.abi, self.torch
+        self.glayers, self.gshare, self.gtag_full, self.gtag_comp, self.gws = [], [], [], [], []
+        for p in range(PARTIES):
+            lays = [par[p]["layer"] for _, _, par in self.items]
+            sh, tf, tc = [], [], []
+            for _, pub, par in self.items:
+                d = par[p]
+                sh.append(dict(E=pub["E"], F=pub["F"], A_i=d["A"], B_i=d["B"], C_i=d["C"], Z_i=d["Z"]))
+                base = dict(alpha_i=d["alpha"], E=pub["E"], F=pub["F"], mA_i=d["mA"], mB_i=d["mB"], mC_i=d["mC"],
+                            mR_i=d["mR"], Dtilde=pub["Dt"], chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"])
+                tf.append(dict(base, mZ_i=d["mZfull"]))
+                tc.append(dict(base, mZ_i=d["mZ"]))
+            need = max(a.mpc_workspace_size_grouped(lays, w)
+                       for w in (a.MPC_WS_SHARE, a.MPC_WS_TAG_FULL, a.MPC_WS_TAG_COMPACT))
+            self.glayers.append(lays)
+            self.gshare.append(sh)
+            self.gtag_full.append(tf)
+            self.gtag_comp.append(tc)
+            self.gws.append(torch.empty(max(need, 256), dtype=torch.uint8, device="cuda"))
+
+    def share_group(self, p):
+        for i in self.links:
+            self._pre(i, p, tag=False)
+        self.abi.mpc_linear_share_grouped(self.glayers[p], self.gshare[p], ws=self.gws[p])
+
+    def full_group(self, p):
+        for i in self.links:
+            self._pre(i, p, tag=True)
+        self.abi.mpc_linear_tag_grouped(self.glayers[p], self.abi.MPC_TAG_FULL, self.gtag_full[p], ws=self.gws[p])
+
+    def compact_group(self, p):
+        for i in self.links:
+            self._pre(i, p, tag=True)
+        self.abi.mpc_linear_tag_grouped(self.glayers[p], self.abi.MPC_TAG_COMPACT, self.gtag_comp[p],
+                                        ws=self.gws[p])
+        for i, (L, pub, par) in enumerate(self.items):
+            d = par[p]
+            self.abi.mpc_tag_check(d["layer"], self.abi.MPC_CHECK_COMPACT, d["alpha"], pub["chi_hat"],
+                                   d["Dc"], d["mDc"], d["cs"], ws=d["ws"])
+
+    def step_grouped(self):
+        for p in range(PARTIES):
+            self.share_group(p)
+            self.full_group(p)
+            self.compact_group(p)
+
+    def launches_per_step_grouped(self):
+        a = self.abi
+        n = 0
+        for p in range(PARTIES):
+            lays = self.glayers[p]
+            n += sum(a.mpc_launch_count_grouped(lays, w)
+                     for w in (a.MPC_WS_SHARE, a.MPC_WS_TAG_FULL, a.MPC_WS_TAG_COMPACT))
+            n += len(lays) + 3 * len(self.links)
+        return n
+
     def launches_per_step(self):
         """Kernels one step enqueues, as the library reports them."""
         a = self.abi
@@ -310,9 +418,11 @@ class GpuRun:
             which = (a.MPC_WS_SHARE_TRUNC, a.MPC_WS_TAG_FULL, a.MPC_WS_PUBLIC_PRODUCT,
                      a.MPC_WS_OPTMAC_TRUNC, a.MPC_WS_TAG_COMPACT, a.MPC_WS_CHECK_COMPACT)
         n = 0
-        for L, _, par in self.items:
+        for i, (L, _, par) in enumerate(self.items):
             for d in par:
                 n += sum(a.mpc_launch_count(d["layer"], w) for w in which)
+                if i in self.links:
+                    n += 4   # two transposes before the share, one before each tag
         return n
 
     def h2d(self):
@@ -386,6 +496,37 @@ def profile_traffic(kernel_tag: str):
         return None
 
 
+def capture(torch, fn):
+    """One call of fn captured into a CUDA graph (after one eager run on the
+    capture stream); returns the graph."""
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        fn()
+    torch.cuda.current_stream().wait_stream(cap)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap):
+        fn()
+    torch.cuda.synchronize()
+    return g
+
+
+def timed_steps(torch, fn, steps):
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+PER_LAYER_TABLE_MAX = 24      # larger layer sets report per-group call timings
+
+
 def run_ours(args):
     import torch
     from paper_2311_04406_gb300 import abi, build
@@ -396,30 +537,26 @@ def run_ours(args):
     abi.load()
     wl_name, wl_fn = WORKLOADS[args.workload]
     layers = wl_fn(args.batch)
-    workload = wl_name.format(b=args.batch)
+    if PASS == "train":
+        layers = layers + synth.backward_layers(layers)
+    workload = wl_name.format(b=args.batch) + ("_train" if PASS == "train" else "")
     run = GpuRun(layers, torch, abi, pinned_host=not args.no_e2e)
     units = step_units(layers)
+    if args.grouped:
+        run.setup_grouped()
+    step_eager = run.step_grouped if args.grouped else run.step
 
     # warm-up (eager), then capture one step into a CUDA graph
     for _ in range(args.warmup):
-        run.step()
+        step_eager()
     torch.cuda.synchronize()
     graph = None
     if not args.eager:
-        cap = torch.cuda.Stream()
-        cap.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(cap):
-            run.step()
-        torch.cuda.current_stream().wait_stream(cap)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=cap):
-            run.step()
-        torch.cuda.synchronize()
+        graph = capture(torch, step_eager)
         for _ in range(args.warmup):
             graph.replay()
         torch.cuda.synchronize()
-    step_fn = graph.replay if graph is not None else run.step
+    step_fn = graph.replay if graph is not None else step_eager
 
     # timed region: K steps, per-step events, barrier + sync on both sides
     barrier(ws)
@@ -439,75 +576,106 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = job_throughput(units, args.steps, ws, total_ms)
     # the same steps issued eagerly through the API (host launch overhead included)
-    eager_ms = None
-    if graph is not None:
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(args.steps):
-            run.step()
-        e1.record(st)
-        torch.cuda.synchronize()
-        eager_ms = e0.elapsed_time(e1) / args.steps
+    eager_ms = timed_steps(torch, step_eager, args.steps) if graph is not None else None
+    # grouped runs: the same step as one call per layer, for comparison
+    per_layer_calls_ms = None
+    if args.grouped and not args.eager:
+        g2 = capture(torch, run.step)
+        g2.replay()
+        per_layer_calls_ms = timed_steps(torch, g2.replay, args.steps)
+        del g2
 
-    # per-call timings: share / full tag / compact tag (+check), per layer
     reps = max(10, min(50, args.steps * 2))
     graphs = not args.eager
-    per_layer = []
-    gemm_ms_by_layer = []
-    for i, L in enumerate(layers):
-        sh = time_calls(torch, lambda: run.share(i, 1), reps, graphs)
-        fu = time_calls(torch, lambda: run.full(i, 1), reps, graphs)
-        co = time_calls(torch, lambda: run.compact(i, 1), reps, graphs)
-        per_layer.append(dict(layer=L.name, M=L.M, K=L.K, N=L.N,
-                              share_ms_p50=pct(sh, 50), full_tag_ms_p50=pct(fu, 50),
-                              compact_tag_ms_p50=pct(co, 50), compact_tag_ms_p99=pct(co, 99),
-                              full_tag_ms_p99=pct(fu, 99),
-                              tag_overhead_ratio=pct(co, 50) / pct(fu, 50),
-                              share_ring_gmacs=2 * L.M * L.K * L.N / (pct(sh, 50) / 1e3) / 1e9,
-                              cost_model_tag_ratio=costmodel.tag_mult_ratio(L.M, L.K, L.N)))
-        gemm_ms_by_layer.append(sh + fu)
-    sum_co = sum(x["compact_tag_ms_p50"] for x in per_layer)
-    sum_fu = sum(x["full_tag_ms_p50"] for x in per_layer)
     hbm, bf16, bf16s, src = peaks()
-    # dominant kernel: the ring GEMM of the largest layer (share and full-tag calls)
-    big = max(range(len(layers)), key=lambda i: layers[i].M * layers[i].K * layers[i].N)
-    Lb = layers[big]
-    gemm_calls = gemm_ms_by_layer[big]
-    avg_ms = sum(gemm_calls) / len(gemm_calls)
-    ring_macs = 2 * Lb.M * Lb.K * Lb.N
-    if abi_path_is_tc(abi, Lb):
-        digit = costmodel.digit_products(RING.bits)
-        achieved = ring_macs * digit * 2 / (avg_ms / 1e3) / 1e12
+    digit = costmodel.digit_products(RING.bits)
+    per_layer, per_group = [], None
+    if args.grouped or len(layers) > PER_LAYER_TABLE_MAX:
+        # per-call timings of one party's grouped calls (the group runs as one
+        # call of each kind in the grouped step, as one call per layer otherwise)
+        if not args.grouped:
+            run.setup_grouped()
+        sh = time_calls(torch, lambda: run.share_group(1), reps, graphs)
+        fu = time_calls(torch, lambda: run.full_group(1), reps, graphs)
+        co = time_calls(torch, lambda: run.compact_group(1), reps, graphs)
+        per_group = dict(layers=len(layers), share_ms_p50=pct(sh, 50), full_tag_ms_p50=pct(fu, 50),
+                         compact_tag_ms_p50=pct(co, 50), compact_tag_ms_p99=pct(co, 99),
+                         full_tag_ms_p99=pct(fu, 99))
+        sum_co, sum_fu = pct(co, 50), pct(fu, 50)
+        tc_layers = [L for L in layers if abi_path_is_tc(abi, L)]
+        tc_macs = sum(2 * L.M * L.K * L.N for L in tc_layers)
+        all_macs = sum(2 * L.M * L.K * L.N for L in layers)
+        gemm_calls = sh + fu
+        avg_ms = sum(gemm_calls) / len(gemm_calls)
+        achieved = tc_macs * digit * 2 / (avg_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
-                "frac": achieved / bf16, "kernel": "ring_gemm_tc",
-                "launch": f"share and full-tag calls of layer {Lb.M}x{Lb.K}x{Lb.N} "
-                          f"(prologue + GEMM), {len(gemm_calls)} calls, CUDA events"
-                          + (" around graph replays of the call" if graphs else ""),
-                "ring_gmacs": ring_macs / (avg_ms / 1e3) / 1e9,
-                "per_unit": f"2MKN ring MACs per call x {digit} fp16 digit products x 2 flop",
+                "frac": achieved / bf16, "kernel": "ring_gemm_tc (grouped persistent launches)",
+                "launch": f"grouped share and full-tag calls of all {len(layers)} layers of one party "
+                          f"({len(tc_layers)} on the tensor cores), {len(gemm_calls)} calls, CUDA events"
+                          + (" around graph replays of the call" if graphs else "")
+                          + "; the call time includes the integer-pipe layers' kernels",
+                "ring_gmacs": all_macs / (avg_ms / 1e3) / 1e9,
+                "per_unit": f"2MKN ring MACs of the tensor-core layers x {digit} fp16 digit products x 2 flop",
                 "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate), x1.0",
-                "traffic": profile_traffic("ring_gemm_tc")}
+                "traffic": None}
+        co_ms = pct(co, 50)
+        co_bytes = sum(8 * RING.words * (4 * L.M * L.N + 2 * L.K * L.N + 2 * L.M * L.K) for L in layers)
+        hbm_kernel = "CompactTag grouped tag call + per-layer checks, all layers of one party"
     else:
-        peak_gops = 152 * 64 * 2.07
-        achieved = ring_macs * 3 / (avg_ms / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                "frac": achieved / peak_gops, "kernel": "ring_gemm_simt",
-                "per_unit": "3 IMAD-class ops per 64-bit ring MAC",
-                "peak_source": "derived: 152 SMs x 64 int32 multiply-add/clk x 2070 MHz",
-                "traffic": profile_traffic("ring_gemm_simt")}
-    co_ms = per_layer[big]["compact_tag_ms_p50"]
-    co_bytes = 8 * RING.words * (4 * Lb.M * Lb.N + 2 * Lb.K * Lb.N + 2 * Lb.M * Lb.K)
+        gemm_ms_by_layer = []
+        for i, L in enumerate(layers):
+            sh = time_calls(torch, lambda: run.share(i, 1), reps, graphs)
+            fu = time_calls(torch, lambda: run.full(i, 1), reps, graphs)
+            co = time_calls(torch, lambda: run.compact(i, 1), reps, graphs)
+            per_layer.append(dict(layer=L.name, M=L.M, K=L.K, N=L.N,
+                                  share_ms_p50=pct(sh, 50), full_tag_ms_p50=pct(fu, 50),
+                                  compact_tag_ms_p50=pct(co, 50), compact_tag_ms_p99=pct(co, 99),
+                                  full_tag_ms_p99=pct(fu, 99),
+                                  tag_overhead_ratio=pct(co, 50) / pct(fu, 50),
+                                  share_ring_gmacs=2 * L.M * L.K * L.N / (pct(sh, 50) / 1e3) / 1e9,
+                                  cost_model_tag_ratio=costmodel.tag_mult_ratio(L.M, L.K, L.N)))
+            gemm_ms_by_layer.append(sh + fu)
+        sum_co = sum(x["compact_tag_ms_p50"] for x in per_layer)
+        sum_fu = sum(x["full_tag_ms_p50"] for x in per_layer)
+        # dominant kernel: the ring GEMM of the largest layer (share and full-tag calls)
+        big = max(range(len(layers)), key=lambda i: layers[i].M * layers[i].K * layers[i].N)
+        Lb = layers[big]
+        gemm_calls = gemm_ms_by_layer[big]
+        avg_ms = sum(gemm_calls) / len(gemm_calls)
+        ring_macs = 2 * Lb.M * Lb.K * Lb.N
+        if abi_path_is_tc(abi, Lb):
+            achieved = ring_macs * digit * 2 / (avg_ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
+                    "frac": achieved / bf16, "kernel": "ring_gemm_tc",
+                    "launch": f"share and full-tag calls of layer {Lb.M}x{Lb.K}x{Lb.N} "
+                              f"(prologue + GEMM), {len(gemm_calls)} calls, CUDA events"
+                              + (" around graph replays of the call" if graphs else ""),
+                    "ring_gmacs": ring_macs / (avg_ms / 1e3) / 1e9,
+                    "per_unit": f"2MKN ring MACs per call x {digit} fp16 digit products x 2 flop",
+                    "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate), x1.0",
+                    "traffic": profile_traffic("ring_gemm_tc")}
+        else:
+            peak_gops = 152 * 64 * 2.07
+            achieved = ring_macs * 3 / (avg_ms / 1e3) / 1e9
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                    "frac": achieved / peak_gops, "kernel": "ring_gemm_simt",
+                    "per_unit": "3 IMAD-class ops per 64-bit ring MAC",
+                    "peak_source": "derived: 152 SMs x 64 int32 multiply-add/clk x 2070 MHz",
+                    "traffic": profile_traffic("ring_gemm_simt")}
+        co_ms = per_layer[big]["compact_tag_ms_p50"]
+        co_bytes = 8 * RING.words * (4 * Lb.M * Lb.N + 2 * Lb.K * Lb.N + 2 * Lb.M * Lb.K)
+        hbm_kernel = "CompactTag tag call (rows + finalize + vec + check kernels)"
     hbm_roof = {"bound": "hbm", "achieved": co_bytes / (co_ms / 1e3) / 1e9, "peak": hbm,
                 "unit": "GB/s", "frac": co_bytes / (co_ms / 1e3) / 1e9 / hbm,
-                "kernel": "CompactTag tag call (rows + finalize + vec + check kernels)",
+                "kernel": hbm_kernel,
                 "per_unit": "8 w (4MN + 2KN + 2MK) bytes per call", "peak_source": f"{src} hbm_gbs",
-                "traffic": profile_traffic("rows_kernel")}
+                "traffic": profile_traffic("rows_kernel") if per_group is None else None}
 
     # end-to-end: the same step through the public API with host buffers
     e2e = None
     if not args.no_e2e:
         e2e_steps = max(3, args.steps // 2)
-        run.h2d(); run.step(); run.d2h()
+        run.h2d(); step_eager(); run.d2h()
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
@@ -515,7 +683,7 @@ def run_ours(args):
         a.record(st)
         for _ in range(e2e_steps):
             run.h2d()
-            run.step()
+            step_eager()
             run.d2h()
         b.record(st)
         torch.cuda.synchronize()
@@ -543,14 +711,20 @@ def run_ours(args):
                        "protocol": "CompactTag with OptMAC&Trunc (truncated layer)" if PROTOCOL == "trunc"
                        else "CompactTag (untruncated layer) beside the SPDZ2k full tag",
                        "layers": [[L.M, L.K, L.N] for L in layers],
+                       "pass": "forward" if PASS == "forward" else
+                       "training: forward + grad X (M,N,K) + grad W (K,M,N) per layer, with device transposes",
                        "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
                        "parties": PARTIES, "parallelism": f"replicas x{ws}",
                        "l2": f"inputs larger than L2 ({run_bytes(layers) / 2**20:.0f} MiB per step > 129 MiB)"},
             "tag_overhead_ratio": sum_co / sum_fu,
             "per_layer": per_layer,
+            "per_group_call": per_group,
+            "grouped": bool(args.grouped),
+            "ms_per_step_per_layer_calls": per_layer_calls_ms,
             "roofline": roof,
             "compact_hbm_roofline": hbm_roof,
-            "gpu_launches": run.launches_per_step() * args.steps,
+            "gpu_launches": (run.launches_per_step_grouped() if args.grouped else run.launches_per_step())
+            * args.steps,
             "clocks": ck.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -636,7 +810,12 @@ def run_reference(args):
     if rank != 0:
         return
     wl_name, wl_fn = WORKLOADS[args.workload]
+    if wl_fn is None:
+        # the serving mix: one ResNet-18 and one VGG16 request at the mean batch
+        wl_fn = lambda b: synth.resnet18_layers(16) + synth.vgg16_layers(16)
     layers = wl_fn(args.batch)
+    if PASS == "train":
+        layers = layers + synth.backward_layers(layers)
     run, units = cpu_sample(layers, 1.0 / 64)
     for _ in range(args.warmup):
         run()
@@ -652,7 +831,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64" if RING.words == 1 else "u128 (two u64 words)",
         "data": "synthetic (uniform ring words from seeded SplitMix64)",
-        "config": {"workload": wl_name.format(b=args.batch),
+        "config": {"workload": wl_name.format(b=args.batch) + ("_train" if PASS == "train" else ""),
                    "layers": [[L.M, L.K, L.N] for L in layers],
                    "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
                    "parties": PARTIES, "parallelism": "host cores (oracle)"},
@@ -660,6 +839,65 @@ def run_reference(args):
                          "sample": "per step: share + full tag at the first 1/64 of output rows and "
                                    "the whole CompactTag tag and check, both layers and parties"},
         "e2e": {"value": value, "unit": "ring-GMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_serve(args):
+    """Serving: ResNet-18 / VGG16 requests (batch 1-32, Z_2^128) through the
+    continuous-batching loop.  A closed-loop run (all requests at t = 0)
+    measures capacity; open-loop runs with Poisson arrivals at fractions of it
+    give the latency percentiles.  value = ring-GMAC/s of the closed-loop run
+    (share products + CompactTag tag and check of every layer)."""
+    import torch
+    from paper_2311_04406_gb300 import abi, build
+    from paper_2311_04406_gb300.serve import Server, make_requests
+    rank, ws = dist_init()
+    if rank != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    abi.load()
+    ring = synth.Z128
+    budget = int(args.serve_budget_gb * 2**30)
+
+    def units_of(reqs):
+        u = 0
+        for r in reqs:
+            for L in r.layers:
+                u += 2 * L.M * L.K * L.N + costmodel.compact_tag_mults(L.M, L.K, L.N) + L.M
+        return u
+
+    srv = Server(ring=ring, mem_budget=budget)
+    srv.run(make_requests(max(4, args.warmup), 1e9, seed=SEED + 1, all_at_once=True))
+    n = args.serve_requests
+    cap_reqs = make_requests(n, 1e9, seed=SEED, all_at_once=True)
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as ck:
+        cap = srv.run(cap_reqs)
+    cap_units = units_of(cap_reqs)
+    value = cap_units / (cap["makespan_ms"] / 1e3) / 1e9
+    runs = []
+    for frac in (0.3, 0.5, 0.7, 0.9):
+        rate = frac * cap["requests_per_s"]
+        reqs = make_requests(n, rate, seed=SEED + int(frac * 100))
+        st = srv.run(reqs)
+        st.update(offered_fraction=frac, offered_rate_per_s=rate)
+        runs.append(st)
+    full = Server(ring=ring, mem_budget=budget, tag="full").run(make_requests(n, 1e9, seed=SEED, all_at_once=True))
+    line = {
+        "metric": METRIC, "value": value, "unit": "ring-GMAC/s", "n_gpus": 1,
+        "steps": n, "warmup": args.warmup, "ms_per_step": cap["makespan_ms"] / n,
+        "step": "one request (closed loop, all requests resident as admitted)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u128 (two u64 words)",
+        "data": "synthetic (request shares from seeded device generators; shapes of ResNet-18 / VGG16 on 32x32x3)",
+        "config": {"workload": WORKLOADS["serve"][0], "ring": "Z_2^128 (k=64, s=64)", "requests_per_run": n,
+                   "memory_budget_gib": args.serve_budget_gb, "party": 0,
+                   "scheduler": "memory-gated FCFS admission, one grouped share + tag call per tick over "
+                                "every admitted request's next layer, 2 ticks in flight"},
+        "capacity": cap, "open_loop": runs,
+        "full_tag_capacity": full,
+        "tag_overhead_ratio": None,
+        "gpu_launches": None, "clocks": ck.summary(), "e2e": None, "cpu_baseline": None,
     }
     print(json.dumps(line))
 
@@ -682,14 +920,27 @@ def main():
     ap.add_argument("--protocol", choices=["plain", "trunc"], default="plain",
                     help="trunc: the truncated layer (share without E.F, public product, "
                          "OptMAC&Trunc, compact tag without the E.F term)")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests per serving run")
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0, help="serving memory budget (GiB)")
+    ap.add_argument("--grouped", action="store_true",
+                    help="one grouped call of each kind per party for all layers (persistent grouped "
+                         "tensor-core launches) instead of one call per layer")
+    ap.add_argument("--pass", dest="pass_", choices=["forward", "train"], default="forward",
+                    help="train: each layer's forward product and its two gradient products "
+                         "(grad X = G.W^T, grad W = X^T.G on transposed mask shares)")
     args = ap.parse_args()
-    global RING, PROTOCOL
+    global RING, PROTOCOL, PASS
+    PASS = args.pass_
     RING = synth.Z64 if args.ring == 64 else synth.Z128
     PROTOCOL = args.protocol
     if args.warmup < 3:
         args.warmup = 3
+    if args.grouped and PROTOCOL != "plain":
+        ap.error("--grouped runs the untruncated layer (--protocol plain)")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -84,6 +84,7 @@ enum {
 #define MPC_E_PARTY (-8)       /* party index outside [0, nparties) */
 #define MPC_E_TIMEOUT (-9)     /* a device-side wait gave up (status read back) */
 #define MPC_E_SCRATCH_LIMIT (-10) /* layer needs more than MPC_NOALLOC_SCRATCH_BYTES */
+#define MPC_E_IO (-11)         /* an autotune table file could not be read or written */
 
 /*
  * a1. Share of Z = X . W from the triple, Eq. (compute-z) and Fig. Pi_MatMul
@@ -159,6 +160,79 @@ int mpc_tag_check(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
                   void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * Grouped calls: many layers in one call (a whole network's linear layers,
+ * or many requests' layers).  Same results, bit for bit, as calling
+ * mpc_linear_share / mpc_linear_tag once per layer in order.  The paper runs
+ * its layers one at a time; grouping exists so that small layers share the
+ * GPU: every tensor-core layer of the group (up to 64 per launch) is scheduled
+ * by ONE persistent prologue + GEMM launch pair whose CTAs work through the
+ * layers' (tile, K interval) units in turn; the remaining layers run the
+ * integer-pipe kernels one by one.
+ *
+ * layers[count], ptrs[count]: HOST arrays, read during the call only.  All
+ * layers share one ring (MPC_E_RING otherwise); the party may differ per
+ * layer.  No output may overlap any input or output of another layer of the
+ * group (the layers run concurrently).  workspace: 256-byte aligned,
+ * mpc_workspace_size_grouped(layers, count, which) bytes.
+ */
+typedef struct {
+    const uint64_t *E, *F, *A_i, *B_i, *C_i;
+    uint64_t *Z_i;
+} mpc_share_ptrs;
+
+typedef struct {
+    const uint64_t *alpha_i, *E, *F, *mA_i, *mB_i, *mC_i, *mR_i, *Dtilde, *chi;
+    uint64_t *mZ_i, *mDc_i, *Dc;
+} mpc_tag_ptrs;
+
+int mpc_linear_share_grouped(const mpc_layer *layers, int count, const mpc_share_ptrs *ptrs,
+                             void *workspace, size_t ws_bytes, void *stream);
+
+/* mode: MPC_TAG_FULL, MPC_TAG_COMPACT or MPC_TAG_COMPACT_TRUNC, as in
+ * mpc_linear_tag, for every layer of the group. */
+int mpc_linear_tag_grouped(const mpc_layer *layers, int count, int mode, const mpc_tag_ptrs *ptrs,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+/* which: MPC_WS_SHARE, MPC_WS_TAG_FULL or MPC_WS_TAG_COMPACT.  0 on invalid
+ * arguments (as mpc_workspace_size). */
+size_t mpc_workspace_size_grouped(const mpc_layer *layers, int count, int which);
+
+/* Kernels one grouped call enqueues (which as above); negative on invalid
+ * arguments. */
+int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
+
+/*
+ * Launch table (autotuner).  The paper has no counterpart: every GEMM path of
+ * this library computes the same exact sums, so the choice of path is a
+ * matter of speed only.  For each layer shape (ring width, M, K, N) the table
+ * holds a choice -- path 1, the tensor-core kernel, with `swizzle` row tiles
+ * per tile-order group (1-64); or path 0, the integer-pipe kernels, with a
+ * K-split target of `waves` x 152 blocks (0 = default).  Untuned shapes use a
+ * built-in rule (tensor cores from 2^22 ring MACs, 2^20 for Z_2^128).  The
+ * table is process-wide and thread-safe; workspace sizes do not depend on it.
+ *
+ * mpc_autotune: for each distinct shape of layers[count], times the
+ *   candidates (swizzle 1/4/8/16 on the tensor cores; K-split 1/2/4/8 on the
+ *   integer pipes, below 2^31 ring MACs) on `stream` and stores the fastest.
+ *   Synchronous; allocates and frees its own scratch operands; do not call it
+ *   during stream capture.  Returns the number of shapes tuned, or a status.
+ * mpc_autotune_set: store a choice (MPC_E_MODE if the tensor-core kernel
+ *   cannot run the shape, or a value is out of range).
+ * mpc_autotune_choice: the choice a call would use now; returns 1 if it comes
+ *   from the table, 0 for the built-in rule.
+ * mpc_autotune_save / _load: the table as text ("mpclinear-autotune 1", then
+ *   "words M K N path swizzle waves" per line); return the number of shapes,
+ *   or MPC_E_IO.  Loading merges into the table.
+ * mpc_autotune_clear: empties the table; returns the number of shapes removed.
+ */
+int mpc_autotune(const mpc_layer *layers, int count, void *stream);
+int mpc_autotune_set(const mpc_layer *layer, int path, int swizzle, int waves);
+int mpc_autotune_choice(const mpc_layer *layer, int *path, int *swizzle, int *waves);
+int mpc_autotune_save(const char *path);
+int mpc_autotune_load(const char *path);
+int mpc_autotune_clear(void);
+
+/*
  * Allocation-free variant of mpc_linear_tag(layer, MPC_TAG_COMPACT, ...).  The
  * paper has no counterpart: this entry point exists for callers that cannot
  * allocate device memory -- e.g. a host runtime reaching this library through
@@ -198,6 +272,16 @@ int mpc_batchrec_mask(const mpc_ring *ring, int64_t rows, int64_t cols,
                       const uint64_t *X_i, const uint64_t *A_i, const uint64_t *R_i,
                       const uint64_t *mX_i, const uint64_t *mA_i, const uint64_t *mR_i,
                       uint64_t *W_i, uint64_t *mW_i, void *stream);
+
+/*
+ * Local transpose, out (cols x rows) = in (rows x cols)^T.  Training's
+ * backward linear layers (§4: grad X = grad Z . W^T, grad W = X^T . grad Z) are
+ * the same per-party Beaver products on transposed operands; shares and tags
+ * transpose locally (the transpose of a sharing is a sharing of the
+ * transpose, §2.4 linearity).  in and out must not overlap.  No workspace.
+ */
+int mpc_transpose(const mpc_ring *ring, int64_t rows, int64_t cols,
+                  const uint64_t *in, uint64_t *out, void *stream);
 
 /*
  * Truncated layer (Fig. Pi_CompactMatMul with Fig. Pi_OptMAC&Trunc, §3.4).

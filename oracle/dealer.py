@@ -253,3 +253,74 @@ def deal_batchrec(ring: synth.Ring, rows: int, cols: int, n: int = 2, seed: int 
         lst += _share(bits, seed, T[name] + 60, V, n, shape)
         mlst += _share(bits, seed, T[name] + 160, O.smul(bits, alpha, V), n, shape)
     return d
+
+
+# ---------------------------------------------------------------------------
+# Training's backward linear layers (§4 training workloads).  Given the forward
+# layer Z = X . W (X = X~ is M x K, W = Y~ is K x N, masked by the triple's A, B
+# as E = X - A, F = W - B), the gradients of a secret upstream gradient G (M x N)
+# are two more Beaver products:
+#   grad X = G . W^T   (M x N by N x K): a layer (M, N, K)
+#   grad W = X^T . G   (K x M by M x N): a layer (K, M, N)
+# The paper does not fix how the backward triples relate to the forward ones.
+# Reading used here: every secret is masked once and the mask is reused in
+# transposed form -- W^T by B^T (so F' = F^T is already public), X^T by A^T
+# (E'' = E^T), and G by one fresh mask A' used on the left of grad X and on the
+# right of grad W (E' = F'' = G - A').  Each party transposes its own shares and
+# tags of A, B locally; only G - A' is opened, and the triples' C parts are
+# fresh: C' = A' . B^T, C'' = A^T . A'.
+
+def transpose(a: np.ndarray) -> np.ndarray:
+    """Matrix transpose of ring-element storage ((rows, cols) or (rows, cols, 2))."""
+    return np.ascontiguousarray(np.swapaxes(a, 0, 1))
+
+
+@dataclass
+class BackDeal:
+    fwd: Deal
+    G: np.ndarray                 # upstream gradient (secret, for invariants only)
+    dX: Deal                      # grad X = G . W^T as a layer (M, N, K)
+    dW: Deal                      # grad W = X^T . G as a layer (K, M, N)
+
+
+def deal_backward(d: Deal, seed: int = 1) -> BackDeal:
+    ring, bits, n = d.ring, d.ring.bits, len(d.parties)
+    M, K, N = d.M, d.K, d.N
+    alpha = d.alpha
+    base = 400                     # tensor ids of the backward streams
+
+    def fresh(tid, shape):
+        return synth.uniform(seed, base + tid, 0, shape, bits)
+
+    def shares(tid, V, shape):
+        return (_share(bits, seed, base + tid, V, n, shape),
+                _share(bits, seed, base + 100 + tid, O.smul(bits, alpha, V), n, shape))
+
+    G = fresh(1, (M, N))
+    Ag = fresh(2, (M, N))                       # mask of G
+    Ag_sh, mAg_sh = shares(2, Ag, (M, N))
+    Eg = O.sub(bits, G, Ag)                     # the one new opening
+    layers = []
+    # grad X = G . W^T: left operand G (mask A'), right operand W^T (mask B^T)
+    Bt = transpose(d.B)
+    Cx = O.ring_gemm(bits, Ag, Bt)
+    Rx = fresh(3, (M, K))
+    Cx_sh, mCx_sh = shares(3, Cx, (M, K))
+    Rx_sh, mRx_sh = shares(4, Rx, (M, K))
+    px = [Party(i, p.alpha, Ag_sh[i], transpose(p.B), Cx_sh[i], Rx_sh[i],
+                mAg_sh[i], transpose(p.mB), mCx_sh[i], mRx_sh[i]) for i, p in enumerate(d.parties)]
+    layers.append(Deal(ring, M, N, K, alpha, G, transpose(d.Y), Ag, Bt, Cx, Rx, Eg, transpose(d.F),
+                       key_range(ring, seed, base + 5, 0, (K,)),
+                       key_range(ring, seed, base + 6, 0, (M,)), px))
+    # grad W = X^T . G: left operand X^T (mask A^T), right operand G (mask A')
+    At = transpose(d.A)
+    Cw = O.ring_gemm(bits, At, Ag)
+    Rw = fresh(7, (K, N))
+    Cw_sh, mCw_sh = shares(7, Cw, (K, N))
+    Rw_sh, mRw_sh = shares(8, Rw, (K, N))
+    pw = [Party(i, p.alpha, transpose(p.A), Ag_sh[i], Cw_sh[i], Rw_sh[i],
+                transpose(p.mA), mAg_sh[i], mCw_sh[i], mRw_sh[i]) for i, p in enumerate(d.parties)]
+    layers.append(Deal(ring, K, M, N, alpha, transpose(d.X), G, At, Ag, Cw, Rw, transpose(d.E), Eg,
+                       key_range(ring, seed, base + 9, 0, (N,)),
+                       key_range(ring, seed, base + 10, 0, (K,)), pw))
+    return BackDeal(d, G, layers[0], layers[1])

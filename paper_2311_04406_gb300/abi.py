@@ -30,8 +30,12 @@ ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_wor
                  "mpc_gemm_path", "mpc_launch_count", "mpc_device_status", "mpc_status_str",
                  "mpc_version",
                  "mpc_linear_tag_compact_noalloc", "mpc_linear_share_trunc", "mpc_public_product",
-                 "mpc_optmac_trunc", "mpc_batchrec_mask")
-MPC_E_SCRATCH_LIMIT = -10
+                 "mpc_optmac_trunc", "mpc_batchrec_mask", "mpc_transpose",
+                 "mpc_linear_share_grouped", "mpc_linear_tag_grouped", "mpc_workspace_size_grouped",
+                 "mpc_launch_count_grouped", "mpc_autotune", "mpc_autotune_set", "mpc_autotune_choice",
+                 "mpc_autotune_save", "mpc_autotune_load", "mpc_autotune_clear")
+(MPC_E_NULL, MPC_E_SHAPE, MPC_E_RING, MPC_E_ALIGN, MPC_E_WORKSPACE, MPC_E_CUDA, MPC_E_MODE, MPC_E_PARTY,
+ MPC_E_TIMEOUT, MPC_E_SCRATCH_LIMIT, MPC_E_IO) = range(-1, -12, -1)
 MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
 
 
@@ -42,6 +46,18 @@ class mpc_ring(ctypes.Structure):
 class mpc_layer(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("K", ctypes.c_int64), ("N", ctypes.c_int64),
                 ("ring", mpc_ring), ("party", ctypes.c_int32), ("nparties", ctypes.c_int32)]
+
+
+SHARE_PTR_FIELDS = ("E", "F", "A_i", "B_i", "C_i", "Z_i")
+TAG_PTR_FIELDS = ("alpha_i", "E", "F", "mA_i", "mB_i", "mC_i", "mR_i", "Dtilde", "chi", "mZ_i", "mDc_i", "Dc")
+
+
+class mpc_share_ptrs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in SHARE_PTR_FIELDS]
+
+
+class mpc_tag_ptrs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in TAG_PTR_FIELDS]
 
 
 class MpcError(RuntimeError):
@@ -91,6 +107,31 @@ def load(build_if_missing: bool = False):
         lib.mpc_batchrec_mask.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int64] + \
             [P] * 8 + [P]
         lib.mpc_batchrec_mask.restype = ctypes.c_int
+        lib.mpc_transpose.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int64, P, P, P]
+        lib.mpc_transpose.restype = ctypes.c_int
+        lib.mpc_linear_share_grouped.argtypes = [L, ctypes.c_int, ctypes.POINTER(mpc_share_ptrs), P,
+                                                 ctypes.c_size_t, P]
+        lib.mpc_linear_share_grouped.restype = ctypes.c_int
+        lib.mpc_linear_tag_grouped.argtypes = [L, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mpc_tag_ptrs), P,
+                                               ctypes.c_size_t, P]
+        lib.mpc_linear_tag_grouped.restype = ctypes.c_int
+        lib.mpc_workspace_size_grouped.argtypes = [L, ctypes.c_int, ctypes.c_int]
+        lib.mpc_workspace_size_grouped.restype = ctypes.c_size_t
+        lib.mpc_launch_count_grouped.argtypes = [L, ctypes.c_int, ctypes.c_int]
+        lib.mpc_launch_count_grouped.restype = ctypes.c_int
+        lib.mpc_autotune.argtypes = [L, ctypes.c_int, P]
+        lib.mpc_autotune.restype = ctypes.c_int
+        lib.mpc_autotune_set.argtypes = [L, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.mpc_autotune_set.restype = ctypes.c_int
+        IP = ctypes.POINTER(ctypes.c_int)
+        lib.mpc_autotune_choice.argtypes = [L, IP, IP, IP]
+        lib.mpc_autotune_choice.restype = ctypes.c_int
+        lib.mpc_autotune_save.argtypes = [ctypes.c_char_p]
+        lib.mpc_autotune_save.restype = ctypes.c_int
+        lib.mpc_autotune_load.argtypes = [ctypes.c_char_p]
+        lib.mpc_autotune_load.restype = ctypes.c_int
+        lib.mpc_autotune_clear.argtypes = []
+        lib.mpc_autotune_clear.restype = ctypes.c_int
         lib.mpc_launch_count.argtypes = [L, ctypes.c_int]
         lib.mpc_launch_count.restype = ctypes.c_int
         lib.mpc_device_status.argtypes = []
@@ -239,3 +280,109 @@ def mpc_batchrec_mask(k, s, rows, cols, X_i, A_i, R_i, mX_i, mA_i, mR_i, W_i, mW
         ctypes.byref(ring), int(rows), int(cols), _ptr(X_i), _ptr(A_i), _ptr(R_i), _ptr(mX_i),
         _ptr(mA_i), _ptr(mR_i), _ptr(W_i), _ptr(mW_i), _stream(stream)))
     return W_i, mW_i
+
+
+def mpc_transpose(k, s, rows, cols, src, dst, stream=None):
+    """dst (cols x rows) = src (rows x cols)^T, ring elements of Z_2^(k+s)."""
+    ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
+    _check("mpc_transpose", load().mpc_transpose(ctypes.byref(ring), int(rows), int(cols), _ptr(src),
+                                                 _ptr(dst), _stream(stream)))
+    return dst
+
+
+# ---------------------------------------------------------------------------
+# grouped calls: `layers` is a list of mpc_layer, `ptrs` a list of dicts keyed
+# by the field names of mpc_share_ptrs / mpc_tag_ptrs (tensors or None)
+
+def _layer_array(layers):
+    arr = (mpc_layer * len(layers))(*layers)
+    return arr
+
+
+def _ptr_array(cls, fields, ptrs):
+    arr = (cls * len(ptrs))()
+    for i, d in enumerate(ptrs):
+        for f in fields:
+            setattr(arr[i], f, _ptr(d.get(f)))
+    return arr
+
+
+def mpc_workspace_size_grouped(layers, which: int) -> int:
+    return int(load().mpc_workspace_size_grouped(_layer_array(layers), len(layers), int(which)))
+
+
+def mpc_launch_count_grouped(layers, which: int) -> int:
+    return int(load().mpc_launch_count_grouped(_layer_array(layers), len(layers), int(which)))
+
+
+def _ws_grouped(layers, which, ws):
+    if ws is not None:
+        return _ptr(ws), ws.numel() * ws.element_size()
+    need = mpc_workspace_size_grouped(layers, which)
+    if need == 0:
+        return None, 0
+    import torch
+    buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+    _ws_grouped.keep = buf
+    return buf.data_ptr(), need
+
+
+def mpc_linear_share_grouped(layers, ptrs, ws=None, stream=None):
+    """Shares of many layers in one call (same results as one mpc_linear_share per layer)."""
+    wp, wb = _ws_grouped(layers, MPC_WS_SHARE, ws)
+    _check("mpc_linear_share_grouped", load().mpc_linear_share_grouped(
+        _layer_array(layers), len(layers), _ptr_array(mpc_share_ptrs, SHARE_PTR_FIELDS, ptrs), wp, wb,
+        _stream(stream)))
+
+
+def mpc_linear_tag_grouped(layers, mode, ptrs, ws=None, stream=None):
+    """Tags of many layers in one call (same results as one mpc_linear_tag per layer)."""
+    which = MPC_WS_TAG_FULL if mode == MPC_TAG_FULL else MPC_WS_TAG_COMPACT
+    wp, wb = _ws_grouped(layers, which, ws)
+    _check("mpc_linear_tag_grouped", load().mpc_linear_tag_grouped(
+        _layer_array(layers), len(layers), int(mode), _ptr_array(mpc_tag_ptrs, TAG_PTR_FIELDS, ptrs), wp, wb,
+        _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# launch table (autotuner)
+
+def mpc_autotune(layers, stream=None) -> int:
+    """Times the GEMM candidates of each distinct layer shape and stores the fastest."""
+    if not layers:
+        return 0
+    n = load().mpc_autotune(_layer_array(layers), len(layers), _stream(stream))
+    if n < 0:
+        _check("mpc_autotune", n)
+    return n
+
+
+def mpc_autotune_set(layer, path: int, swizzle: int = 8, waves: int = 0):
+    _check("mpc_autotune_set", load().mpc_autotune_set(ctypes.byref(layer), int(path), int(swizzle), int(waves)))
+
+
+def mpc_autotune_choice(layer):
+    """(path, swizzle, waves, tuned) the next call for this layer shape would use."""
+    p, g, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    r = load().mpc_autotune_choice(ctypes.byref(layer), ctypes.byref(p), ctypes.byref(g), ctypes.byref(w))
+    if r < 0:
+        _check("mpc_autotune_choice", r)
+    return p.value, g.value, w.value, bool(r)
+
+
+def mpc_autotune_save(path: str) -> int:
+    n = load().mpc_autotune_save(os.fsencode(path))
+    if n < 0:
+        _check("mpc_autotune_save", n)
+    return n
+
+
+def mpc_autotune_load(path: str) -> int:
+    n = load().mpc_autotune_load(os.fsencode(path))
+    if n < 0:
+        _check("mpc_autotune_load", n)
+    return n
+
+
+def mpc_autotune_clear() -> int:
+    return int(load().mpc_autotune_clear())

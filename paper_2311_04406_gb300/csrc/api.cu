@@ -6,6 +6,7 @@
 // input.  Valid calls enqueue kernels on the caller's stream and return.
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "mpclinear.h"
 #include "kernels.h"
@@ -51,20 +52,23 @@ int cuda_status(cudaError_t e) {
     return MPC_E_CUDA;
 }
 
+// Workspace of a GEMM: the tensor-core digit planes whenever that kernel can
+// run the shape, so that any launch-table choice fits the same workspace.
 size_t gemm_ws(const mpc_layer* L, int one_half = 0) {
-    if (mpcl::gemm_tc_eligible(L->M, L->K, L->N, L->ring.words))
-        return mpcl::gemm_tc_workspace(L->M, L->K, L->N, L->ring.words, one_half);
-    return 0;
+    return mpcl::gemm_tc_workspace(L->M, L->K, L->N, L->ring.words, one_half);
 }
 
-int run_gemm(const mpcl::GemmArgs& g, void* ws, size_t ws_bytes, cudaStream_t st) {
+int run_gemm(mpcl::GemmArgs g, void* ws, size_t ws_bytes, cudaStream_t st) {
     if (g.M == 0 || g.N == 0) return MPC_OK;
-    if (mpcl::gemm_tc_eligible(g.M, g.K, g.N, g.words)) {
+    const mpcl::Choice c = mpcl::gemm_choice(g.M, g.K, g.N, g.words);
+    if (c.path == 1) {
         if (!ws || ws_bytes < mpcl::gemm_tc_workspace(g.M, g.K, g.N, g.words, g.one_half))
             return MPC_E_WORKSPACE;
         if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
+        g.gm = c.gm;
         return cuda_status(mpcl::launch_gemm_tc(g, ws, ws_bytes, st));
     }
+    g.simt_waves = c.waves;
     return cuda_status(mpcl::launch_gemm_simt(g, st));
 }
 
@@ -77,7 +81,7 @@ int mpc_version(void) { return 100; }
 int mpc_gemm_path(const mpc_layer* L) {
     int st = check_layer(L);
     if (st != MPC_OK) return st;
-    return mpcl::gemm_tc_eligible(L->M, L->K, L->N, L->ring.words) ? 1 : 0;
+    return mpcl::gemm_choice(L->M, L->K, L->N, L->ring.words).path;
 }
 
 int mpc_launch_count(const mpc_layer* L, int which) {
@@ -91,7 +95,7 @@ int mpc_launch_count(const mpc_layer* L, int which) {
         case MPC_WS_PUBLIC_PRODUCT:
         case MPC_WS_TAG_FULL:
             if (M == 0 || N == 0) return 0;
-            return mpcl::gemm_tc_eligible(M, K, N, w) ? mpcl::gemm_tc_launches(M, K, N, w) : 1;
+            return mpcl::gemm_choice(M, K, N, w).path == 1 ? mpcl::gemm_tc_launches(M, K, N, w) : 1;
         case MPC_WS_TAG_COMPACT: return mpcl::compact_launches(M, K, N);
         case MPC_WS_CHECK_COMPACT: return 1;
         case MPC_WS_CHECK_BATCHREC: return 2;
@@ -120,6 +124,7 @@ const char* mpc_status_str(int s) {
         case MPC_E_TIMEOUT: return "a device-side wait gave up";
         case MPC_E_SCRATCH_LIMIT:
             return "layer needs more scratch than the static MPC_NOALLOC_SCRATCH_BYTES buffer holds";
+        case MPC_E_IO: return "an autotune table file could not be read or written";
         default: return "unknown status";
     }
 }
@@ -156,6 +161,18 @@ int mpc_linear_share(const mpc_layer* L, const uint64_t* E, const uint64_t* F,
                      (const u64*)C_i, (u64*)Z_i,
                      L->party == 0 ? mpcl::COEF_ONE : mpcl::COEF_ZERO, nullptr, 0};
     return run_gemm(g, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mpc_transpose(const mpc_ring* ring, int64_t rows, int64_t cols, const uint64_t* in, uint64_t* out,
+                  void* stream) {
+    if (!ring) return MPC_E_NULL;
+    if (!ring_ok(*ring)) return MPC_E_RING;
+    if (rows < 0 || cols < 0 || rows > kMaxDim || cols > kMaxDim || rows * cols > kMaxElems)
+        return MPC_E_SHAPE;
+    CHK(check_ptr(in, rows * cols));
+    CHK(check_ptr(out, rows * cols));
+    return cuda_status(mpcl::launch_transpose(rows, cols, ring->words, (const u64*)in, (u64*)out,
+                                              (cudaStream_t)stream));
 }
 
 int mpc_batchrec_mask(const mpc_ring* ring, int64_t rows, int64_t cols, const uint64_t* X_i,
@@ -310,6 +327,192 @@ int mpc_tag_check(const mpc_layer* L, int mode, const uint64_t* alpha_i,
     return cuda_status(mpcl::launch_check_batchrec(M, N, w, (const u64*)alpha_i,
                                                    (const u64*)chi_hat, (const u64*)opened,
                                                    (const u64*)tag_i, (u64*)cs_i, ws, ws_bytes, st));
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// grouped calls
+
+namespace {
+
+bool same_ring(const mpc_ring& a, const mpc_ring& b) {
+    return a.k == b.k && a.s == b.s && a.words == b.words;
+}
+
+int check_group(const mpc_layer* layers, int count, const void* ptrs) {
+    if (count < 0) return MPC_E_SHAPE;
+    if (count == 0) return MPC_OK;
+    if (!layers || !ptrs) return MPC_E_NULL;
+    for (int i = 0; i < count; ++i) {
+        CHK(check_layer(&layers[i]));
+        if (!same_ring(layers[i].ring, layers[0].ring)) return MPC_E_RING;
+    }
+    return MPC_OK;
+}
+
+bool on_tc(const mpc_layer& L) {
+    return L.M > 0 && L.N > 0 && mpcl::gemm_choice(L.M, L.K, L.N, L.ring.words).path == 1;
+}
+
+// workspace of a grouped GEMM: the digit planes of every layer the
+// tensor-core kernel can run (whatever the launch table picks)
+size_t group_gemm_ws(const mpc_layer* layers, int count) {
+    size_t t = 0;
+    for (int i = 0; i < count; ++i)
+        if (layers[i].M > 0 && layers[i].N > 0)
+            t += (mpcl::gemm_tc_workspace(layers[i].M, layers[i].K, layers[i].N, layers[i].ring.words) + 255) &
+                 ~size_t(255);
+    return t;
+}
+
+size_t group_compact_ws(const mpc_layer* layers, int count) {
+    size_t t = 0;
+    for (int i = 0; i < count; ++i)
+        t += (mpcl::compact_workspace(layers[i].M, layers[i].K, layers[i].N, layers[i].ring.words) + 255) &
+             ~size_t(255);
+    return t;
+}
+
+// the tensor-core layers as one grouped launch, the others one by one
+int run_gemm_group(const mpc_layer* layers, int count, const mpcl::GemmArgs* g, void* ws, size_t ws_bytes,
+                   cudaStream_t st) {
+    const size_t need = group_gemm_ws(layers, count);
+    if (need > 0) {
+        if (!ws || ws_bytes < need) return MPC_E_WORKSPACE;
+        if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
+    }
+    std::vector<mpcl::GemmArgs> tc, simt;
+    std::vector<uint8_t*> ap;
+    uint8_t* cur = static_cast<uint8_t*>(ws);
+    for (int i = 0; i < count; ++i) {
+        if (g[i].M == 0 || g[i].N == 0) continue;
+        const mpcl::Choice c = mpcl::gemm_choice(g[i].M, g[i].K, g[i].N, g[i].words);
+        mpcl::GemmArgs x = g[i];
+        if (c.path == 1) {
+            x.gm = c.gm;
+            tc.push_back(x);
+            ap.push_back(cur);
+        } else {
+            x.simt_waves = c.waves;
+            simt.push_back(x);
+        }
+        cur += (mpcl::gemm_tc_workspace(g[i].M, g[i].K, g[i].N, g[i].words) + 255) & ~size_t(255);
+    }
+    if (!tc.empty()) CHK(cuda_status(mpcl::launch_gemm_tc_grouped(tc.data(), (int)tc.size(), ap.data(), st)));
+    for (const auto& x : simt) CHK(cuda_status(mpcl::launch_gemm_simt(x, st)));
+    return MPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpc_linear_share_grouped(const mpc_layer* layers, int count, const mpc_share_ptrs* ptrs, void* ws,
+                             size_t ws_bytes, void* stream) {
+    CHK(check_group(layers, count, ptrs));
+    if (count == 0) return MPC_OK;
+    std::vector<mpcl::GemmArgs> g((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const mpc_layer* L = &layers[i];
+        const mpc_share_ptrs& p = ptrs[i];
+        const int64_t M = L->M, K = L->K, N = L->N;
+        CHK(check_ptr(p.E, M * K));
+        CHK(check_ptr(p.A_i, M * K));
+        CHK(check_ptr(p.F, K * N));
+        CHK(check_ptr(p.B_i, K * N));
+        CHK(check_ptr(p.C_i, M * N));
+        CHK(check_ptr(p.Z_i, M * N));
+        g[i] = mpcl::GemmArgs{M, K, N, L->ring.words, (const u64*)p.E, (const u64*)p.F, (const u64*)p.A_i,
+                              (const u64*)p.B_i, (const u64*)p.C_i, (u64*)p.Z_i,
+                              L->party == 0 ? mpcl::COEF_ONE : mpcl::COEF_ZERO, nullptr, 0};
+    }
+    return run_gemm_group(layers, count, g.data(), ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int mpc_linear_tag_grouped(const mpc_layer* layers, int count, int mode, const mpc_tag_ptrs* ptrs, void* ws,
+                           size_t ws_bytes, void* stream) {
+    if (mode != MPC_TAG_FULL && mode != MPC_TAG_COMPACT && mode != MPC_TAG_COMPACT_TRUNC) return MPC_E_MODE;
+    CHK(check_group(layers, count, ptrs));
+    if (count == 0) return MPC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<mpcl::GemmArgs> g;
+    std::vector<mpcl::CompactArgs> c;
+    for (int i = 0; i < count; ++i) {
+        const mpc_layer* L = &layers[i];
+        const mpc_tag_ptrs& p = ptrs[i];
+        const int64_t M = L->M, K = L->K, N = L->N;
+        const int w = L->ring.words;
+        CHK(check_ptr(p.alpha_i, 1));
+        CHK(check_ptr(p.E, M * K));
+        CHK(check_ptr(p.mA_i, M * K));
+        CHK(check_ptr(p.F, K * N));
+        CHK(check_ptr(p.mB_i, K * N));
+        CHK(check_ptr(p.mC_i, M * N));
+        if (mode != MPC_TAG_COMPACT_TRUNC || p.mZ_i != nullptr) CHK(check_ptr(p.mZ_i, M * N));
+        if (mode == MPC_TAG_FULL) {
+            g.push_back(mpcl::GemmArgs{M, K, N, w, (const u64*)p.E, (const u64*)p.F, (const u64*)p.mA_i,
+                                       (const u64*)p.mB_i, (const u64*)p.mC_i, (u64*)p.mZ_i, mpcl::COEF_ALPHA,
+                                       (const u64*)p.alpha_i, 0});
+            continue;
+        }
+        CHK(check_ptr(p.mR_i, M * N));
+        CHK(check_ptr(p.Dtilde, M * N));
+        CHK(check_ptr(p.chi, N));
+        CHK(check_ptr(p.mDc_i, M));
+        CHK(check_ptr(p.Dc, M));
+        c.push_back(mpcl::CompactArgs{M, K, N, w, mode == MPC_TAG_COMPACT ? 1 : 0, (const u64*)p.alpha_i,
+                                      (const u64*)p.E, (const u64*)p.F, (const u64*)p.mA_i, (const u64*)p.mB_i,
+                                      (const u64*)p.mC_i, (const u64*)p.mR_i, (const u64*)p.Dtilde,
+                                      (const u64*)p.chi, (u64*)p.mZ_i, (u64*)p.mDc_i, (u64*)p.Dc});
+    }
+    if (mode == MPC_TAG_FULL) return run_gemm_group(layers, count, g.data(), ws, ws_bytes, st);
+    const size_t need = group_compact_ws(layers, count);
+    if (need > 0) {
+        if (!ws || ws_bytes < need) return MPC_E_WORKSPACE;
+        if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
+    }
+    uint8_t* cur = static_cast<uint8_t*>(ws);
+    for (int i = 0; i < count; ++i) {
+        const size_t b = (mpcl::compact_workspace(c[i].M, c[i].K, c[i].N, c[i].words) + 255) & ~size_t(255);
+        CHK(cuda_status(mpcl::launch_compact(c[i], cur, b, st)));
+        cur += b;
+    }
+    return MPC_OK;
+}
+
+size_t mpc_workspace_size_grouped(const mpc_layer* layers, int count, int which) {
+    if (count <= 0 || !layers) return 0;
+    for (int i = 0; i < count; ++i) {
+        if (check_layer(&layers[i]) != MPC_OK || !same_ring(layers[i].ring, layers[0].ring)) return 0;
+    }
+    switch (which) {
+        case MPC_WS_SHARE:
+        case MPC_WS_TAG_FULL: return group_gemm_ws(layers, count);
+        case MPC_WS_TAG_COMPACT: return group_compact_ws(layers, count);
+        default: return 0;
+    }
+}
+
+int mpc_launch_count_grouped(const mpc_layer* layers, int count, int which) {
+    if (count < 0) return MPC_E_SHAPE;
+    if (count == 0) return 0;
+    if (!layers) return MPC_E_NULL;
+    int tc = 0, n = 0;
+    for (int i = 0; i < count; ++i) {
+        CHK(check_layer(&layers[i]));
+        if (!same_ring(layers[i].ring, layers[0].ring)) return MPC_E_RING;
+        const mpc_layer& L = layers[i];
+        if (which == MPC_WS_SHARE || which == MPC_WS_TAG_FULL) {
+            if (on_tc(L)) ++tc;
+            else if (L.M > 0 && L.N > 0) n += 1;
+        } else if (which == MPC_WS_TAG_COMPACT) {
+            n += mpcl::compact_launches(L.M, L.K, L.N);
+        } else {
+            return MPC_E_MODE;
+        }
+    }
+    return n + mpcl::gemm_tc_grouped_launches(tc);
 }
 
 }  // extern "C"

@@ -198,8 +198,10 @@ cudaError_t run(const GemmArgs& a, cudaStream_t st) {
     const int64_t bx = skinny ? (a.N + NT * vec - 1) / (NT * vec) : (a.N + BN - 1) / BN;
     const int64_t by = skinny ? 1 : (a.M + BM - 1) / BM;
     if (by > 65535) return cudaErrorInvalidConfiguration;
-    const int64_t kchunk = skinny ? choose_kchunk(bx * by, K2, 16, 32, 4)
-                                  : choose_kchunk(bx * by, K2, BK, 4 * BK, 2);
+    // K split so that the grid covers about `waves` x 152 blocks (launch table, else 4 / 2)
+    const int64_t waves = a.simt_waves > 0 ? a.simt_waves : (skinny ? 4 : 2);
+    const int64_t kchunk = skinny ? choose_kchunk(bx * by, K2, 16, 32, waves)
+                                  : choose_kchunk(bx * by, K2, BK, 4 * BK, waves);
     const int64_t bz = K2 > 0 ? (K2 + kchunk - 1) / kchunk : 1;
     if (bz > 65535) return cudaErrorInvalidConfiguration;
     const int atomic = bz > 1 ? 1 : 0;

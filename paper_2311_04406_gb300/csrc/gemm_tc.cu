@@ -44,6 +44,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <new>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "sm100_ptx.cuh"
@@ -136,8 +140,57 @@ __device__ __forceinline__ Biased<W> biased(const u64* e) {
 }
 
 // ---------------------------------------------------------------------------
+// schedule
+//
+// The work units of a launch -- (output tile, Kd-deep K interval) pairs of all
+// its layers, numbered layer by layer, tile by tile -- are dealt to the G CTAs
+// in waves.  Each full wave gives every CTA c consecutive units (c = the
+// largest intervals-per-tile of the launch, so in a one-layer launch a CTA
+// gets exactly one whole tile per wave: the data-parallel schedule).  The
+// units left over after the full waves (fewer than G c) are split evenly over
+// the CTAs (stream-K), which balances layers with fewer tiles than CTAs.
+// Tiles are numbered in groups of GM row tiles, column-major inside a group,
+// so the G consecutive tiles of a wave form a compact block whose operand
+// tiles the CTAs share through L2 while they move through K together.
+struct Sched {
+    int64_t c;       // units per CTA in each full wave
+    int64_t nfull;   // full waves
+    int64_t S;       // units in the full waves (nfull G c)
+    int64_t L;       // units of the last, partial wave
+    int G;           // CTAs
+};
+
+constexpr int GM_DEFAULT = 8;   // row tiles per swizzle group unless the launch table says otherwise
+
+// units of CTA b
+__host__ __device__ __forceinline__ int64_t cta_units(const Sched& s, int64_t b) {
+    return s.nfull * s.c + ((b + 1) * s.L) / s.G - (b * s.L) / s.G;
+}
+
+// end of the range (of one CTA) that holds global unit u
+__host__ __device__ __forceinline__ int64_t range_end_of(const Sched& s, int64_t u) {
+    if (u < s.S) return (u / s.c + 1) * s.c;
+    // owner: the largest b with floor(b L / G) <= u - S
+    const int64_t t = u - s.S;
+    const int64_t b = ((t + 1) * s.G - 1) / s.L;
+    return s.S + ((b + 1) * s.L) / s.G;
+}
+
+// tile index -> (row tile, column tile), GM row tiles per group
+__host__ __device__ __forceinline__ void tile_mn(int64_t t, int64_t m_tiles, int64_t n_tiles, int64_t GM,
+                                                 int64_t* m, int64_t* n) {
+    const int64_t grp = t / (GM * n_tiles);
+    const int64_t r = t - grp * GM * n_tiles;
+    const int64_t left = m_tiles - grp * GM;
+    const int64_t gm = left < GM ? left : GM;
+    *n = r / gm;
+    *m = grp * GM + (r - *n * gm);
+}
+
+
+// ---------------------------------------------------------------------------
 // prologue: L = [E | X + cE] as digit planes in the MMA's shared-memory
-// image, and Z = C
+// image, and Z = C on the tiles whose sums arrive in several pieces
 
 struct PrologueParams {
     const u64 *E, *X, *alpha;
@@ -149,21 +202,55 @@ struct PrologueParams {
     uint8_t* Ap;
     const u64* C;
     u64* Z;
+    int64_t u_first;          // the layer's first global unit
+    int I;                    // intervals per tile
+    int64_t m_tiles, n_tiles;
+    int gm;                   // row tiles per swizzle group
 };
 
+// Up to G layers per launch: block b works for the layer g with
+// b_off[g] <= b < b_off[g + 1] (one block per 128-row tile and 16-deep stage).
+template <int G> struct PrologueGroup {
+    int count;
+    int64_t b_off[G + 1];
+    PrologueParams p[G];
+    Sched sched;              // the GEMM launch's schedule
+};
+
+// thread `id` of `nthreads` working for one layer
 template <int W>
-__global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
+__device__ __forceinline__ void prologue_body(const PrologueParams& p, const Sched& sc, int64_t id,
+                                              int64_t nthreads) {
     constexpr int NDIG = Cfg<W>::NDIG;
     constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     {
-        // Z = C, or 0 without an addend (16-byte vectors; M N W is even for
-        // every eligible shape)
-        const int64_t nv = p.M * p.N * W / 2;
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        // Z = C (0 without an addend) on split tiles: their pieces are added
+        // atomically.  A tile one CTA computes whole is written by that CTA.
+        // 16-byte vectors: two elements of one row for W = 1 (N is even),
+        // one element for W = 2.
+        // Blocks take tiles in turn; a split tile's 128 x ND block is copied by
+        // the 256 threads, 16 vectors (ND elements) per row.
+        constexpr int ND = Cfg<W>::ND;
+        constexpr int VPR = ND * W / 2;                      // 16-byte vectors per tile row
+        const int64_t blk = id >> 8, nblk = nthreads >> 8;
+        const int tid = (int)(id & 255);
         const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C);
         ulonglong2* z2 = reinterpret_cast<ulonglong2*>(p.Z);
-        for (int64_t i = id; i < nv; i += stride) z2[i] = c2 ? __ldg(c2 + i) : make_ulonglong2(0, 0);
+        const int64_t T = p.m_tiles * p.n_tiles;
+        for (int64_t t = blk; t < T; t += nblk) {
+            const int64_t u = p.u_first + t * p.I;
+            if (u + p.I <= range_end_of(sc, u)) continue;   // whole: written by its CTA
+            int64_t mt, nt;
+            tile_mn(t, p.m_tiles, p.n_tiles, p.gm, &mt, &nt);
+            for (int q = tid; q < BM * VPR; q += 256) {
+                const int r = q / VPR, j = q - r * VPR;
+                const int64_t m = mt * BM + r;
+                const int64_t n = nt * ND + (int64_t)j * 2 / W;
+                if (m >= p.M || n >= p.N) continue;
+                const int64_t i = (m * p.N + n) * W / 2;     // vector index
+                z2[i] = c2 ? __ldg(c2 + i) : make_ulonglong2(0, 0);
+            }
+        }
     }
     const int64_t per_tile = (int64_t)p.S_tot * 256;
     const int64_t m_tiles = (p.M + BM - 1) / BM;
@@ -234,12 +321,31 @@ __global__ void __launch_bounds__(256) prologue_kernel(PrologueParams p) {
     }
 }
 
+template <int W, int G>
+__global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ PrologueGroup<G> g) {
+    int gi = 0;
+    if constexpr (G > 1) {
+        // last layer whose first block is at or before this one
+        int lo = 0, hi = g.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.b_off[mid] <= (int64_t)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        gi = lo;
+    }
+    const int64_t lb = (int64_t)blockIdx.x - g.b_off[gi];
+    const int64_t nb = g.b_off[gi + 1] - g.b_off[gi];
+    prologue_body<W>(g.p[gi], g.sched, lb * 256 + threadIdx.x, nb * 256);
+}
+
 // ---------------------------------------------------------------------------
 // the GEMM
 
 struct TcParams {
     const uint8_t* Ap;
     u64* Z;
+    const u64* C;    // addend (NULL: none), read by CTAs that write a whole tile
     int one_half;
     int64_t M, K, N;
     int64_t Kp;      // padded K half
@@ -247,37 +353,117 @@ struct TcParams {
     int I;           // Kd-deep intervals per tile
     int KD;          // stages per interval
     int ND;          // columns per tile
-    int64_t n_tiles;
+    int64_t m_tiles, n_tiles;
     int64_t U;       // work units = tiles x I
+    int gm;          // row tiles per swizzle group
 };
 
-// The work units [u0, u1) of this CTA; unit u is interval u % I of tile u / I.
+// Up to G layers per launch.  Their work units are numbered consecutively:
+// layer g owns units [u_off[g], u_off[g + 1]).  The tensor maps live in the
+// kernel's parameter space (__grid_constant__), as for a single layer.
+template <int G> struct TcGroup {
+    CUtensorMap tmB[G];
+    CUtensorMap tmF[G];
+    TcParams p[G];
+    int64_t u_off[G + 1];
+    Sched sched;
+    int count;
+};
+
+// Unit u (local to its layer) is interval u % I of tile u / I.
 struct Unit {
-    int64_t tile;
+    int64_t mt, nt;  // row tile, column tile
     int ii;          // interval within the tile
     int nst;         // stages in this interval (KD, or fewer at the end of K)
-    bool flush;      // last unit of a segment: add the sums into Z
+    bool flush;      // last unit of a segment: the sums go to Z
 };
 
-__device__ __forceinline__ Unit unit_of(const TcParams& p, int64_t u, int64_t u1) {
-    Unit x;
-    x.tile = u / p.I;
-    x.ii = (int)(u % p.I);
-    const int s_begin = x.ii * p.KD;
-    x.nst = min(p.KD, p.S_tot - s_begin);
-    x.flush = (u + 1 == u1) || (x.ii == p.I - 1);
-    return x;
-}
+// Walks the units of one CTA in order.  Divisions happen only where one of
+// the CTA's ranges of consecutive units starts; inside a range the position
+// (layer, tile in swizzled order, interval) advances incrementally.
+template <int G> struct Walker {
+    const TcGroup<G>& g;
+    const int64_t cta;
+    int64_t v = 0, left = 0, u = 0;
+    int gi = 0;
+    int ii = 0, m_in = 0, gm = 1;      // tile and swizzle counters (tile counts < 2^31)
+    int64_t mt = 0, nt = 0, grp = 0;
+
+    __device__ __forceinline__ Walker(const TcGroup<G>& g_, int64_t cta_) : g(g_), cta(cta_) {}
+
+    __device__ __forceinline__ void decode(const TcParams& p, int64_t ul) {
+        const int64_t GM = p.gm;
+        const int64_t tile = ul / p.I;
+        ii = (int)(ul - tile * p.I);
+        grp = tile / (GM * p.n_tiles);
+        const int64_t r = tile - grp * GM * p.n_tiles;
+        const int64_t lft = p.m_tiles - grp * GM;
+        gm = (int)(lft < GM ? lft : GM);
+        nt = r / gm;
+        m_in = (int)(r - nt * gm);
+        mt = grp * GM + m_in;
+    }
+
+    __device__ __forceinline__ Unit next() {
+        const Sched& s = g.sched;
+        if (left == 0) {
+            const int64_t full = s.nfull * s.c;
+            int64_t len;
+            if (v < full) {
+                u = ((v / s.c) * s.G + cta) * s.c;
+                len = s.c;
+            } else {
+                const int64_t a = (cta * s.L) / s.G, e = ((cta + 1) * s.L) / s.G;
+                u = s.S + a;
+                len = e - a;
+            }
+            left = len - 1;
+            if constexpr (G > 1)
+                while (gi + 1 < g.count && u >= g.u_off[gi + 1]) ++gi;
+            decode(g.p[gi], u - g.u_off[gi]);
+        } else {
+            ++u;
+            --left;
+            const TcParams& p = g.p[gi];
+            if (G > 1 && gi + 1 < g.count && u == g.u_off[gi + 1]) {
+                ++gi;
+                ii = m_in = 0;
+                grp = nt = mt = 0;
+                const int64_t mtl = g.p[gi].m_tiles;
+                gm = (int)(mtl < g.p[gi].gm ? mtl : g.p[gi].gm);
+            } else if (++ii == p.I) {
+                ii = 0;
+                if (++m_in == gm) {
+                    m_in = 0;
+                    if (++nt == p.n_tiles) {
+                        nt = 0;
+                        ++grp;
+                        const int64_t lft = p.m_tiles - grp * p.gm;
+                        gm = (int)(lft < p.gm ? lft : p.gm);
+                    }
+                }
+                mt = grp * p.gm + m_in;
+            }
+        }
+        ++v;
+        const TcParams& p = g.p[gi];
+        Unit x;
+        x.mt = mt;
+        x.nt = nt;
+        x.ii = ii;
+        x.nst = min(p.KD, p.S_tot - x.ii * p.KD);
+        x.flush = (left == 0) || (x.ii == p.I - 1);
+        return x;
+    }
+};
 
 __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
     *abort_flag = 1;
     atomicExch(&g_tc_timeout, 1u);
 }
 
-template <int W>
-__global__ void __launch_bounds__(NTHREADS, 1)
-ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmF,
-                    TcParams p) {
+template <int W, int G>
+__global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_constant__ TcGroup<G> g) {
     constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND, STAGES = Cfg<W>::STAGES;
     constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
     using Sum = typename Elem<W>::T;
@@ -298,9 +484,9 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t u0 = (int64_t)blockIdx.x * p.U / gridDim.x;
-    const int64_t u1 = (int64_t)(blockIdx.x + 1) * p.U / gridDim.x;
-    const int nv = (int)(u1 - u0);   // intervals of this CTA
+    const Sched& sc = g.sched;
+    const int64_t cta = blockIdx.x;
+    const int64_t nv = cta_units(sc, cta);   // units of this CTA
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -332,9 +518,11 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            for (int v = 0; v < nv && ok; ++v) {
-                const Unit x = unit_of(p, u0 + v, u1);
-                const int64_t m_tile = x.tile / p.n_tiles;
+            Walker<G> wk(g, cta);
+            for (int64_t v = 0; v < nv && ok; ++v) {
+                const Unit x = wk.next();
+                const TcParams& p = g.p[wk.gi];
+                const int64_t m_tile = x.mt;
                 const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + (size_t)x.ii * p.KD) * A_STAGE;
                 for (int j = 0; j < x.nst; ++j, ++it) {
                     const int s = it % STAGES;
@@ -354,14 +542,22 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
         }
     } else if (warp == W_BPROD) {
         if (lane == 0) {
-            ptx::prefetch_tmap(&tmB);
-            ptx::prefetch_tmap(&tmF);
             int it = 0;
             bool ok = true;
-            for (int v = 0; v < nv && ok; ++v) {
-                const Unit x = unit_of(p, u0 + v, u1);
+            Walker<G> wk(g, cta);
+            int prefetched = -1;
+            for (int64_t v = 0; v < nv && ok; ++v) {
+                const Unit x = wk.next();
+                const TcParams& p = g.p[wk.gi];
+                const CUtensorMap* tmB = &g.tmB[wk.gi];
+                const CUtensorMap* tmF = &g.tmF[wk.gi];
+                if (prefetched != wk.gi) {
+                    ptx::prefetch_tmap(tmB);
+                    ptx::prefetch_tmap(tmF);
+                    prefetched = wk.gi;
+                }
                 // x coordinate in 64-bit words (ND W words per tile)
-                const int x0 = (int)(x.tile % p.n_tiles) * ND * W;
+                const int x0 = (int)x.nt * ND * W;
                 for (int j = 0; j < x.nst; ++j, ++it) {
                     const int r = it % RAW;
                     if (!ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
@@ -373,11 +569,11 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                     // rows at or beyond K inside a padded half arrive zero-filled
                     const int64_t kp0 = (int64_t)(x.ii * p.KD + j) * KS;
                     if (p.one_half)
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, x0, (int)kp0, &rawFull[r]);
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, tmF, x0, (int)kp0, &rawFull[r]);
                     else if (kp0 < p.Kp)
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmB, x0, (int)kp0, &rawFull[r]);
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, tmB, x0, (int)kp0, &rawFull[r]);
                     else
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, &tmF, x0, (int)(kp0 - p.Kp), &rawFull[r]);
+                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, tmF, x0, (int)(kp0 - p.Kp), &rawFull[r]);
                 }
             }
             for (int j = max(0, it - RAW); j < it; ++j)
@@ -404,7 +600,10 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
         }
         constexpr int TPT = W == 1 ? NDIG : NDIG / 2;   // planes written per thread
         int total = 0;
-        for (int v = 0; v < nv; ++v) total += unit_of(p, u0 + v, u1).nst;
+        {
+            Walker<G> wk(g, cta);
+            for (int64_t v = 0; v < nv; ++v) total += wk.next().nst;
+        }
         for (int it = 0; it < total; ++it) {
             const int r = it % RAW;
             if (!ptx::mbar_wait(&rawFull[r], (it / RAW) & 1, abort_flag, WAIT_LIMIT)) {
@@ -450,10 +649,11 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
             const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
             bool ok = true;
             int it = 0;
-            for (int v = 0; v < nv && ok; ++v) {
-                const Unit x = unit_of(p, u0 + v, u1);
-                const int set = v & 1;
-                if (!ptx::mbar_wait(&accEmpty[set], ((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
+            Walker<G> wk(g, cta);
+            for (int64_t v = 0; v < nv && ok; ++v) {
+                const Unit x = wk.next();
+                const int set = (int)(v & 1);
+                if (!ptx::mbar_wait(&accEmpty[set], (int)((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
                     record_timeout(abort_flag);
                     break;
                 }
@@ -492,10 +692,13 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
         Sum sum[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
-        for (int v = 0; v < nv; ++v) {
-            const Unit x = unit_of(p, u0 + v, u1);
-            const int set = v & 1;
-            bool got = ptx::mbar_wait(&accFull[set], (v >> 1) & 1, abort_flag, WAIT_LIMIT);
+        int seg_ii = -1;   // first interval of the current segment
+        Walker<G> wk(g, cta);
+        for (int64_t v = 0; v < nv; ++v) {
+            const Unit x = wk.next();
+            const TcParams& p = g.p[wk.gi];
+            const int set = (int)(v & 1);
+            bool got = ptx::mbar_wait(&accFull[set], (int)((v >> 1) & 1), abort_flag, WAIT_LIMIT);
             if (!__all_sync(0xffffffffu, got)) {
                 if (lane == 0) record_timeout(abort_flag);
                 break;
@@ -520,18 +723,30 @@ ring_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmB, const __grid_consta
                     sum[c] += dv << (8 * t);
                 }
             }
+            if (seg_ii < 0) seg_ii = x.ii;
             if (x.flush) {
-                const int64_t m = (x.tile / p.n_tiles) * BM + row;
-                const int64_t n0 = (x.tile % p.n_tiles) * ND;
+                // a tile computed whole by this segment is written as C + sum;
+                // pieces of a split tile are added to Z (set to C by the prologue)
+                const bool whole = seg_ii == 0 && x.ii == p.I - 1;
+                seg_ii = -1;
+                const int64_t m = x.mt * BM + row;
+                const int64_t n0 = x.nt * ND;
                 if (m < p.M) {
                     u64* zrow = p.Z + (m * p.N + n0) * W;
+                    const u64* crow = p.C ? p.C + (m * p.N + n0) * W : nullptr;
                     const int64_t rem = p.N - n0;
                     const int ncols = rem < ND ? (int)rem : ND;
+                    if (whole) {
 #pragma unroll
-                    for (int c = 0; c < ND; ++c) {
-                        if (c < ncols) {
-                            if constexpr (W == 1) red_add_u64(zrow + c, sum[c]);
-                            else atomic_add_u128(zrow + 2 * c, sum[c]);
+                        for (int c = 0; c < ND; ++c)
+                            if (c < ncols) st_elem<W>(zrow, c, (crow ? ldg_elem<W>(crow, c) : (Sum)0) + sum[c]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < ND; ++c) {
+                            if (c < ncols) {
+                                if constexpr (W == 1) red_add_u64(zrow + c, sum[c]);
+                                else atomic_add_u128(zrow + 2 * c, sum[c]);
+                            }
                         }
                     }
                 }
@@ -610,53 +825,138 @@ bool make_map(CUtensorMap* map, const u64* base, int64_t rows, int64_t cols, int
     return r == CUDA_SUCCESS;
 }
 
-template <int W>
-cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t st) {
-    CUtensorMap tmB, tmF;
-    if (!make_map(&tmF, a.F, a.K, a.N, W, Cfg<W>::ND)) return cudaErrorInvalidValue;
-    if (a.one_half) tmB = tmF;
-    else if (!make_map(&tmB, a.B, a.K, a.N, W, Cfg<W>::ND)) return cudaErrorInvalidValue;
-    PrologueParams pp{a.E, a.X, a.alpha, a.coef, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z};
-    const int64_t pth = pl.m_tiles * pl.S_tot * 256;
-    prologue_kernel<W><<<(unsigned)((pth + 255) / 256), 256, 0, st>>>(pp);
-    // the dynamic shared-memory opt-in is set once per device (a host call that
-    // also keeps graph capture free of attribute changes after the first use)
+constexpr int GMAX = 64;   // layers per grouped launch (kernel parameters stay below 32 KB)
+static_assert(sizeof(TcGroup<GMAX>) + 64 <= 32764, "kernel parameter space");
+
+// The dynamic shared-memory opt-in is set once per device and kernel (a host
+// call that also keeps graph capture free of attribute changes after the
+// first use).
+template <int W, int G>
+cudaError_t ensure_smem_attr() {
     static bool smem_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
-    if (dev < 0 || dev >= 64 || !smem_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Layout<W>::SMEM);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) smem_set[dev] = true;
-    }
-    TcParams tp{Ap, a.Z, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND, pl.n_tiles, pl.U};
-    const int sms = sm_count();
-    const int64_t grid = pl.U < sms ? pl.U : sms;
-    ring_gemm_tc_kernel<W><<<(unsigned)grid, NTHREADS, Layout<W>::SMEM, st>>>(tmB, tmF, tp);
+    if (dev >= 0 && dev < 64 && smem_set[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Layout<W>::SMEM);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) smem_set[dev] = true;
+    return cudaSuccess;
+}
+
+// Fills entry j of a group for layer `a` (digit planes at Ap).
+template <int W, int G>
+bool fill(TcGroup<G>& tg, PrologueGroup<G>& pg, int j, const GemmArgs& a, uint8_t* Ap, const Plan& pl) {
+    if (!make_map(&tg.tmF[j], a.F, a.K, a.N, W, Cfg<W>::ND)) return false;
+    if (a.one_half) tg.tmB[j] = tg.tmF[j];
+    else if (!make_map(&tg.tmB[j], a.B, a.K, a.N, W, Cfg<W>::ND)) return false;
+    const int gm = a.gm > 0 ? a.gm : GM_DEFAULT;
+    tg.p[j] = TcParams{Ap, a.Z, a.C, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND,
+                       pl.m_tiles, pl.n_tiles, pl.U, gm};
+    pg.p[j] = PrologueParams{a.E, a.X, a.alpha, a.coef, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z,
+                             tg.u_off[j], pl.I, pl.m_tiles, pl.n_tiles, gm};
+    tg.u_off[j + 1] = tg.u_off[j] + pl.U;
+    pg.b_off[j + 1] = pg.b_off[j] + pl.m_tiles * pl.S_tot;
+    return true;
+}
+
+// The schedule of a launch of U units whose largest tile has I_max intervals.
+Sched make_sched(int64_t U, int64_t I_max, int sms) {
+    Sched s{};
+    s.G = (int)(U < sms ? U : sms);
+    s.c = I_max;
+    s.nfull = U / ((int64_t)s.G * s.c);
+    s.S = s.nfull * s.G * s.c;
+    s.L = U - s.S;
+    return s;
+}
+
+template <int W, int G>
+cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) {
+    int64_t i_max = 1;
+    for (int j = 0; j < tg.count; ++j) i_max = tg.p[j].I > i_max ? tg.p[j].I : i_max;
+    tg.sched = pg.sched = make_sched(tg.u_off[tg.count], i_max, sm_count());
+    prologue_kernel<W, G><<<(unsigned)pg.b_off[pg.count], 256, 0, st>>>(pg);
+    cudaError_t e = ensure_smem_attr<W, G>();
+    if (e != cudaSuccess) return e;
+    ring_gemm_tc_kernel<W, G><<<(unsigned)tg.sched.G, NTHREADS, Layout<W>::SMEM, st>>>(tg);
     return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t st) {
+    TcGroup<1> tg{};
+    PrologueGroup<1> pg{};
+    tg.count = pg.count = 1;
+    if (!fill<W, 1>(tg, pg, 0, a, Ap, pl)) return cudaErrorInvalidValue;
+    return launch_group<W, 1>(tg, pg, st);
+}
+
+// Layers [0, n) in launches of up to GMAX layers; layer i's digit planes at
+// Ap[i].  Every layer is eligible and has the ring width W.
+template <int W>
+cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st) {
+    static_assert(alignof(TcGroup<GMAX>) >= 64, "tensor map alignment");
+    auto* tg = new (std::nothrow) TcGroup<GMAX>;
+    auto* pg = new (std::nothrow) PrologueGroup<GMAX>;
+    if (!tg || !pg) {
+        delete tg;
+        delete pg;
+        return cudaErrorMemoryAllocation;
+    }
+    // layers with more K intervals first, so that whole tiles of the long
+    // layers line up with the CTAs' ranges (the order changes no result)
+    std::vector<int> order(n);
+    std::vector<int> iv(n);
+    for (int i = 0; i < n; ++i) {
+        order[i] = i;
+        iv[i] = make_plan(a[i].M, a[i].K, a[i].N, W, a[i].one_half).I;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return iv[x] > iv[y]; });
+    cudaError_t e = cudaSuccess;
+    for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += GMAX) {
+        const int cnt = n - i0 < GMAX ? n - i0 : GMAX;
+        tg->count = pg->count = cnt;
+        tg->u_off[0] = 0;
+        pg->b_off[0] = 0;
+        for (int j = 0; j < cnt && e == cudaSuccess; ++j) {
+            const int li = order[i0 + j];
+            const GemmArgs& x = a[li];
+            if (!fill<W, GMAX>(*tg, *pg, j, x, Ap[li], make_plan(x.M, x.K, x.N, W, x.one_half)))
+                e = cudaErrorInvalidValue;
+        }
+        if (e == cudaSuccess) e = launch_group<W, GMAX>(*tg, *pg, st);
+    }
+    delete tg;
+    delete pg;
+    return e;
 }
 
 }  // namespace
 
-bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
+bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words) {
     if (words != 1 && words != 2) return false;
     if (M <= 8 || N < 1 || K < 1) return false;        // skinny layers stream better on the SIMT GEMV
     if (words == 1 && N % 2 != 0) return false;       // TMA row stride: 16-byte multiple
     if (K > (int64_t(1) << 30) || N > (int64_t(1) << 28)) return false;
     if ((M + BM - 1) / BM > 65535) return false;
+    return true;
+}
+
+bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
+    if (!gemm_tc_feasible(M, K, N, words)) return false;
     // smaller products run faster on the integer-pipe kernel
     const double macs = 2.0 * (double)M * (double)K * (double)N;
     return macs >= (words == 1 ? (double)(1 << 22) : (double)(1 << 20));
 }
 
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half) {
-    if (!gemm_tc_eligible(M, K, N, words)) return 0;
+    if (!gemm_tc_feasible(M, K, N, words)) return 0;
     return align256(make_plan(M, K, N, words, one_half).ap_bytes);
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
-    if (!gemm_tc_eligible(a.M, a.K, a.N, a.words)) return cudaErrorNotSupported;
+    if (!gemm_tc_feasible(a.M, a.K, a.N, a.words)) return cudaErrorNotSupported;
     Plan pl = make_plan(a.M, a.K, a.N, a.words, a.one_half);
     if (ws_bytes < align256(pl.ap_bytes) || ws == nullptr) return cudaErrorInvalidValue;
     uint8_t* Ap = static_cast<uint8_t*>(ws);
@@ -664,8 +964,20 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStr
 }
 
 int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words) {
-    return gemm_tc_eligible(M, K, N, words) ? 2 : 0;
+    return gemm_tc_feasible(M, K, N, words) ? 2 : 0;
 }
+
+cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int w = a[0].words;
+    for (int i = 0; i < n; ++i)
+        if (a[i].words != w || !gemm_tc_feasible(a[i].M, a[i].K, a[i].N, w) || !Ap[i] ||
+            reinterpret_cast<uintptr_t>(Ap[i]) % 256 != 0)
+            return cudaErrorInvalidValue;
+    return w == 1 ? launch_many<1>(a, n, Ap, st) : launch_many<2>(a, n, Ap, st);
+}
+
+int gemm_tc_grouped_launches(int n) { return n <= 0 ? 0 : 2 * ((n + GMAX - 1) / GMAX); }
 
 // Reads and clears the device flag that a bounded wait sets when it gives up.
 int tc_timeout_flag(bool* set) {

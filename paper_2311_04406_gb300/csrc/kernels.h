@@ -28,15 +28,34 @@ struct GemmArgs {
     int coef;          // CoefMode
     const u64* alpha;  // one element (COEF_ALPHA)
     int one_half;      // 1: Z = C + (X + cE) . F over K only (the public product E.F)
+    int gm;            // tensor cores: row tiles per swizzle group (0: default)
+    int simt_waves;    // integer pipes: K-split target in waves of 152 blocks (0: default)
 };
+
+// The launch choice of one GEMM shape: path 1 = tensor cores (gm = swizzle
+// width), path 0 = integer pipes (waves = K-split target).  From the autotune
+// table when the shape was tuned (tuned = 1), else the built-in heuristic.
+struct Choice {
+    int path;
+    int gm;
+    int waves;
+    int tuned;
+};
+Choice gemm_choice(int64_t M, int64_t K, int64_t N, int words);
 
 cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t st);
 
 // tensor-core ring GEMM (fp16 digit products, exact); returns
 // cudaErrorNotSupported when the shape is not handled by it.
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
+// several eligible layers of one ring width in grouped persistent launches
+// (up to 64 layers per prologue + GEMM pair); layer i's digit planes at Ap[i]
+// (gemm_tc_workspace bytes, 256-byte aligned)
+cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st);
+int gemm_tc_grouped_launches(int n);
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half = 0);
-bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words);
+bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words);   // heuristic preference
+bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words);   // the kernel can run the shape
 int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words);
 int tc_timeout_flag(bool* set);   // synchronous; 0 on success
 
@@ -66,6 +85,10 @@ cudaError_t launch_compact(const CompactArgs& a, void* ws, size_t ws_bytes, cuda
 cudaError_t launch_optmac_trunc(int64_t MN, int words, int k, int f, int party0, const u64* alpha,
                                 const u64* Rf, const u64* mRf, const u64* Dt, const u64* P, u64* Zf,
                                 u64* mZf, cudaStream_t st);
+
+// local transpose of a ring matrix (training's backward layers)
+cudaError_t launch_transpose(int64_t rows, int64_t cols, int words, const u64* in, u64* out,
+                             cudaStream_t st);
 
 // checks (a6)
 cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u64* chi_hat,

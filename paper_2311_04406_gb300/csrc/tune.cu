@@ -1,0 +1,247 @@
+// tune.cu -- the per-shape launch table (autotuner) of the ring GEMM.
+//
+// Every GEMM path computes the same exact sums, so the choice of path and
+// tiling changes only the time a layer takes.  For each layer shape
+// (ring width, M, K, N) the table holds a Choice: the tensor-core kernel with
+// a row-tile swizzle width, or the integer-pipe kernels with a K-split
+// target.  Shapes not in the table use the built-in heuristic
+// (gemm_tc_eligible).  mpc_autotune times the candidates of each distinct
+// shape on the caller's stream and stores the fastest; the table can be saved
+// to and loaded from a text file:
+//     mpclinear-autotune 1
+//     <words> <M> <K> <N> <path> <swizzle> <waves>      (one line per shape)
+// The table is process-wide and guarded by a mutex.
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+#include "mpclinear.h"
+
+namespace mpcl {
+
+namespace {
+
+using Key = std::tuple<int, int64_t, int64_t, int64_t>;
+
+std::mutex g_mu;
+std::map<Key, Choice>& table() {
+    static std::map<Key, Choice> t;
+    return t;
+}
+
+bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
+    if (c.path == 1) return gemm_tc_feasible(M, K, N, words) && c.gm >= 1 && c.gm <= 64;
+    return c.path == 0 && c.waves >= 0 && c.waves <= 64;
+}
+
+}  // namespace
+
+Choice gemm_choice(int64_t M, int64_t K, int64_t N, int words) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = table().find(Key{words, M, K, N});
+        if (it != table().end()) return it->second;
+    }
+    Choice c;
+    c.path = gemm_tc_eligible(M, K, N, words) ? 1 : 0;
+    c.gm = 0;
+    c.waves = 0;
+    c.tuned = 0;
+    return c;
+}
+
+}  // namespace mpcl
+
+namespace {
+
+int check_shape(const mpc_layer* L) {
+    if (!L) return MPC_E_NULL;
+    const mpc_ring& r = L->ring;
+    if (!((r.words == 1 || r.words == 2) && r.k >= 1 && r.s >= 1 && r.k + r.s == 64 * r.words)) return MPC_E_RING;
+    if (L->M < 0 || L->K < 0 || L->N < 0) return MPC_E_SHAPE;
+    return MPC_OK;
+}
+
+// one timed candidate: the best of `reps` runs after a warm-up run, in ms
+float time_candidate(const mpcl::GemmArgs& a, const mpcl::Choice& c, void* ws, size_t ws_bytes, cudaStream_t st,
+                     cudaEvent_t e0, cudaEvent_t e1, int reps, bool* ok) {
+    mpcl::GemmArgs g = a;
+    g.gm = c.gm;
+    g.simt_waves = c.waves;
+    auto run = [&]() -> cudaError_t {
+        return c.path == 1 ? mpcl::launch_gemm_tc(g, ws, ws_bytes, st) : mpcl::launch_gemm_simt(g, st);
+    };
+    *ok = false;
+    if (run() != cudaSuccess) return 0.f;
+    float best = -1.f;
+    for (int r = 0; r < reps; ++r) {
+        if (cudaEventRecord(e0, st) != cudaSuccess) return 0.f;
+        if (run() != cudaSuccess) return 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess) return 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return 0.f;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return 0.f;
+        if (best < 0.f || ms < best) best = ms;
+    }
+    *ok = true;
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpc_autotune(const mpc_layer* layers, int count, void* stream) {
+    if (count < 0) return MPC_E_SHAPE;
+    if (count == 0) return 0;
+    if (!layers) return MPC_E_NULL;
+    for (int i = 0; i < count; ++i) {
+        int s = check_shape(&layers[i]);
+        if (s != MPC_OK) return s;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MPC_E_CUDA;
+    int tuned = 0, status = MPC_OK;
+    std::map<std::tuple<int, int64_t, int64_t, int64_t>, bool> seen;
+    for (int i = 0; i < count && status == MPC_OK; ++i) {
+        const mpc_layer& L = layers[i];
+        const int64_t M = L.M, K = L.K, N = L.N;
+        const int w = L.ring.words;
+        if (M == 0 || N == 0) continue;
+        auto key = std::make_tuple(w, M, K, N);
+        if (seen.count(key)) continue;
+        seen[key] = true;
+        std::vector<mpcl::Choice> cands;
+        const bool tc = mpcl::gemm_tc_feasible(M, K, N, w);
+        const double macs = 2.0 * (double)M * (double)K * (double)N;
+        if (tc)
+            for (int gm : {1, 4, 8, 16}) cands.push_back(mpcl::Choice{1, gm, 0, 1});
+        // the integer pipes are far slower on large products: not timed there
+        if (!tc || macs < 2147483648.0)
+            for (int wv : {1, 2, 4, 8}) cands.push_back(mpcl::Choice{0, 0, wv, 1});
+        // operands (contents do not matter for the time: every path is exact)
+        const size_t e = 8 * (size_t)w;
+        const size_t b_mk = e * (size_t)(M * K), b_kn = e * (size_t)(K * N), b_mn = e * (size_t)(M * N);
+        const size_t ws_bytes = tc ? mpcl::gemm_tc_workspace(M, K, N, w) : 0;
+        void *E = nullptr, *X = nullptr, *B = nullptr, *F = nullptr, *C = nullptr, *Z = nullptr, *ws = nullptr;
+        bool alloc = cudaMalloc(&E, b_mk > 0 ? b_mk : 16) == cudaSuccess &&
+                     cudaMalloc(&X, b_mk > 0 ? b_mk : 16) == cudaSuccess &&
+                     cudaMalloc(&B, b_kn > 0 ? b_kn : 16) == cudaSuccess &&
+                     cudaMalloc(&F, b_kn > 0 ? b_kn : 16) == cudaSuccess &&
+                     cudaMalloc(&C, b_mn) == cudaSuccess && cudaMalloc(&Z, b_mn) == cudaSuccess &&
+                     (ws_bytes == 0 || cudaMalloc(&ws, ws_bytes) == cudaSuccess);
+        if (alloc) {
+            cudaMemsetAsync(E, 0, b_mk, st);
+            cudaMemsetAsync(X, 0, b_mk, st);
+            cudaMemsetAsync(B, 0, b_kn, st);
+            cudaMemsetAsync(F, 0, b_kn, st);
+            cudaMemsetAsync(C, 0, b_mn, st);
+            mpcl::GemmArgs a{M, K, N, w, (const mpcl::u64*)E, (const mpcl::u64*)F, (const mpcl::u64*)X,
+                             (const mpcl::u64*)B, (const mpcl::u64*)C, (mpcl::u64*)Z, mpcl::COEF_ZERO, nullptr, 0};
+            float best = -1.f;
+            mpcl::Choice pick{};
+            for (const auto& c : cands) {
+                bool ok = false;
+                const float ms = time_candidate(a, c, ws, ws_bytes, st, e0, e1, 3, &ok);
+                if (!ok) {
+                    status = MPC_E_CUDA;
+                    break;
+                }
+                if (best < 0.f || ms < best) {
+                    best = ms;
+                    pick = c;
+                }
+            }
+            if (status == MPC_OK && best >= 0.f) {
+                std::lock_guard<std::mutex> lk(mpcl::g_mu);
+                mpcl::table()[key] = pick;
+                ++tuned;
+            }
+        } else {
+            status = MPC_E_CUDA;
+        }
+        cudaStreamSynchronize(st);
+        for (void* p : {E, X, B, F, C, Z, ws})
+            if (p) cudaFree(p);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return status == MPC_OK ? tuned : status;
+}
+
+int mpc_autotune_set(const mpc_layer* layer, int path, int swizzle, int waves) {
+    int s = check_shape(layer);
+    if (s != MPC_OK) return s;
+    mpcl::Choice c{path, swizzle, waves, 1};
+    if (!mpcl::choice_ok(c, layer->M, layer->K, layer->N, layer->ring.words)) return MPC_E_MODE;
+    std::lock_guard<std::mutex> lk(mpcl::g_mu);
+    mpcl::table()[std::make_tuple(layer->ring.words, layer->M, layer->K, layer->N)] = c;
+    return MPC_OK;
+}
+
+int mpc_autotune_choice(const mpc_layer* layer, int* path, int* swizzle, int* waves) {
+    int s = check_shape(layer);
+    if (s != MPC_OK) return s;
+    const mpcl::Choice c = mpcl::gemm_choice(layer->M, layer->K, layer->N, layer->ring.words);
+    if (path) *path = c.path;
+    if (swizzle) *swizzle = c.gm;
+    if (waves) *waves = c.waves;
+    return c.tuned ? 1 : 0;
+}
+
+int mpc_autotune_clear(void) {
+    std::lock_guard<std::mutex> lk(mpcl::g_mu);
+    const int n = (int)mpcl::table().size();
+    mpcl::table().clear();
+    return n;
+}
+
+int mpc_autotune_save(const char* path) {
+    if (!path) return MPC_E_NULL;
+    FILE* f = std::fopen(path, "w");
+    if (!f) return MPC_E_IO;
+    std::lock_guard<std::mutex> lk(mpcl::g_mu);
+    std::fprintf(f, "mpclinear-autotune 1\n");
+    for (const auto& kv : mpcl::table()) {
+        const auto& k = kv.first;
+        const auto& c = kv.second;
+        std::fprintf(f, "%d %lld %lld %lld %d %d %d\n", std::get<0>(k), (long long)std::get<1>(k),
+                     (long long)std::get<2>(k), (long long)std::get<3>(k), c.path, c.gm, c.waves);
+    }
+    const int n = (int)mpcl::table().size();
+    return std::fclose(f) == 0 ? n : MPC_E_IO;
+}
+
+int mpc_autotune_load(const char* path) {
+    if (!path) return MPC_E_NULL;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return MPC_E_IO;
+    int version = 0;
+    if (std::fscanf(f, "mpclinear-autotune %d", &version) != 1 || version != 1) {
+        std::fclose(f);
+        return MPC_E_IO;
+    }
+    std::vector<std::pair<std::tuple<int, int64_t, int64_t, int64_t>, mpcl::Choice>> rows;
+    int w, path_, gm, waves;
+    long long M, K, N;
+    while (std::fscanf(f, "%d %lld %lld %lld %d %d %d", &w, &M, &K, &N, &path_, &gm, &waves) == 7) {
+        mpcl::Choice c{path_, gm, waves, 1};
+        if ((w != 1 && w != 2) || M < 0 || K < 0 || N < 0 || !mpcl::choice_ok(c, M, K, N, w)) {
+            std::fclose(f);
+            return MPC_E_IO;
+        }
+        rows.push_back({std::make_tuple(w, (int64_t)M, (int64_t)K, (int64_t)N), c});
+    }
+    const bool at_end = std::feof(f) != 0;
+    std::fclose(f);
+    if (!at_end) return MPC_E_IO;
+    std::lock_guard<std::mutex> lk(mpcl::g_mu);
+    for (const auto& r : rows) mpcl::table()[r.first] = r.second;
+    return (int)rows.size();
+}
+
+}  // extern "C"

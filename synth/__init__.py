@@ -217,3 +217,14 @@ def uneven_layers(count: int = 256, seed: int = 0xC0FFEE03) -> list[Layer]:
         n = 64 << (int(w[3 * i + 2]) % 7)
         out.append(Layer(f"u{i}", m, k, n))
     return out
+
+
+def backward_layers(forward: list) -> list:
+    """The two gradient products of each forward layer Z (M x N) = X (M x K) . W:
+    grad X = grad Z (M x N) . W^T (N x K)  -> (M, N, K), and
+    grad W = X^T (K x M) . grad Z (M x N)  -> (K, M, N)."""
+    out = []
+    for L in forward:
+        out.append(Layer(L.name + "_dX", L.M, L.N, L.K))
+        out.append(Layer(L.name + "_dW", L.K, L.M, L.N))
+    return out

@@ -91,3 +91,87 @@ def test_empty_layers_are_noops(lib):
     assert _call_share(lib, L, [None, 0x1000, None, 0x1000, None, None]) == 0
     L = abi.make_layer(5, 4, 0)
     assert _call_share(lib, L, [0x1000, None, 0x1000, None, None, None]) == 0
+
+
+def test_grouped_host_logic(lib):
+    """Grouped calls: workspace and launch counts are the sums over the group;
+    invalid groups are rejected before any launch."""
+    layers = [abi.make_layer(128, 4096, 4096), abi.make_layer(4, 512, 300), abi.make_layer(1024, 576, 64),
+              abi.make_layer(64, 256, 256)]
+    tc = [abi.mpc_gemm_path(L) for L in layers]
+    assert tc == [1, 0, 1, 1]
+    ws = abi.mpc_workspace_size_grouped(layers, abi.MPC_WS_SHARE)
+    assert ws == sum(-(-abi.mpc_workspace_size(L, abi.MPC_WS_SHARE) // 256) * 256 for L in layers)
+    cws = abi.mpc_workspace_size_grouped(layers, abi.MPC_WS_TAG_COMPACT)
+    assert cws == sum(-(-abi.mpc_workspace_size(L, abi.MPC_WS_TAG_COMPACT) // 256) * 256 for L in layers)
+    # one prologue + GEMM pair for the three tensor-core layers, one kernel for the other
+    assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_SHARE) == 2 + 1
+    assert abi.mpc_launch_count_grouped(layers * 30, abi.MPC_WS_TAG_FULL) == 2 * 2 + 30
+    assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_TAG_COMPACT) == \
+        sum(abi.mpc_launch_count(L, abi.MPC_WS_TAG_COMPACT) for L in layers)
+    mixed = [abi.make_layer(8, 8, 8), abi.make_layer(8, 8, 8, 64, 64)]
+    assert abi.mpc_launch_count_grouped(mixed, abi.MPC_WS_SHARE) == abi.MPC_E_RING
+    assert abi.mpc_workspace_size_grouped(mixed, abi.MPC_WS_SHARE) == 0
+    arr = (abi.mpc_layer * 2)(*mixed)
+    ptrs = (abi.mpc_share_ptrs * 2)()
+    assert lib.mpc_linear_share_grouped(arr, 2, ptrs, None, 0, None) == abi.MPC_E_RING
+    assert lib.mpc_linear_share_grouped(arr, -1, ptrs, None, 0, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_linear_share_grouped(None, 0, None, None, 0, None) == 0
+    assert lib.mpc_linear_share_grouped(None, 2, ptrs, None, 0, None) == abi.MPC_E_NULL
+    tptrs = (abi.mpc_tag_ptrs * 2)()
+    same = (abi.mpc_layer * 2)(abi.make_layer(8, 8, 8), abi.make_layer(8, 8, 8))
+    assert lib.mpc_linear_tag_grouped(same, 2, 9, tptrs, None, 0, None) == abi.MPC_E_MODE
+    # NULL operands in a group are caught before any launch
+    assert lib.mpc_linear_tag_grouped(same, 2, abi.MPC_TAG_FULL, tptrs, None, 0, None) == abi.MPC_E_NULL
+    # a tensor-core group without its workspace
+    big = (abi.mpc_layer * 1)(abi.make_layer(128, 256, 256))
+    p1 = (abi.mpc_share_ptrs * 1)()
+    for f in abi.SHARE_PTR_FIELDS:
+        setattr(p1[0], f, 0x1000)
+    assert lib.mpc_linear_share_grouped(big, 1, p1, None, 0, None) == abi.MPC_E_WORKSPACE
+    assert lib.mpc_linear_share_grouped(big, 1, p1, 0x1010, 1 << 30, None) == abi.MPC_E_ALIGN
+
+
+def test_launch_table_host_logic(lib, tmp_path):
+    """The autotune table: set / query / save / load / clear, and rejection of
+    choices the kernels cannot run (no GPU needed)."""
+    abi.mpc_autotune_clear()
+    big = abi.make_layer(128, 4096, 4096)
+    small = abi.make_layer(64, 128, 64)
+    skinny = abi.make_layer(4, 512, 512)
+    assert abi.mpc_autotune_choice(big) == (1, 0, 0, False)      # built-in rule
+    assert abi.mpc_autotune_choice(small)[0] == 0
+    ws_before = abi.mpc_workspace_size(small, abi.MPC_WS_SHARE)
+    abi.mpc_autotune_set(small, 1, 4, 0)
+    assert abi.mpc_autotune_choice(small) == (1, 4, 0, True)
+    assert abi.mpc_gemm_path(small) == 1
+    assert abi.mpc_workspace_size(small, abi.MPC_WS_SHARE) == ws_before   # independent of the table
+    abi.mpc_autotune_set(big, 0, 0, 8)
+    assert abi.mpc_gemm_path(big) == 0
+    # the tensor-core kernel cannot run M <= 8 or odd N in Z_2^64
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_set(skinny, 1, 8, 0)
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_set(abi.make_layer(64, 64, 63), 1, 8, 0)
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_set(small, 1, 0, 0)
+    f = tmp_path / "table.txt"
+    assert abi.mpc_autotune_save(str(f)) == 2
+    lines = f.read_text().split("\n")
+    assert lines[0] == "mpclinear-autotune 1" and "1 64 128 64 1 4 0" in lines
+    assert abi.mpc_autotune_clear() == 2
+    assert abi.mpc_autotune_choice(small)[3] is False
+    assert abi.mpc_autotune_load(str(f)) == 2
+    assert abi.mpc_autotune_choice(small) == (1, 4, 0, True)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("mpclinear-autotune 1\n1 4 512 512 1 8 0\n")   # tensor cores on M = 4
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_load(str(bad))
+    bad.write_text("something else\n")
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_load(str(bad))
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_load(str(tmp_path / "missing.txt"))
+    assert abi.mpc_autotune([]) == 0
+    abi.mpc_autotune_clear()
+    assert abi.mpc_gemm_path(big) == 1

@@ -1,0 +1,81 @@
+"""The serving loop (continuous batching over grouped calls, memory-gated
+admission): every request's outputs are the same bit for bit whether it is
+served alone or in a mix, and they equal the oracle's."""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from paper_2311_04406_gb300 import abi, build
+from paper_2311_04406_gb300.serve import Server, make_requests, request_bytes
+
+from gpuhelp import host
+
+pytestmark = pytest.mark.gpu
+
+OUT_KEYS = ("Z", "mZ", "mDc", "Dc", "cs")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    abi.load()
+
+
+def fresh(reqs):
+    """The same requests, not yet served."""
+    from paper_2311_04406_gb300.serve import Request
+    return [Request(r.rid, r.model, r.batch, r.arrival, r.seed, r.layers) for r in reqs]
+
+
+def outputs(r):
+    return [{k: host(d[k]) for k in OUT_KEYS} for d in r.bufs]
+
+
+@pytest.mark.parametrize("budget_gb", [3, 200])
+def test_alone_equals_mixed(budget_gb):
+    reqs = make_requests(6, 1000.0, seed=3, max_batch=2)
+    srv = Server(ring=synth.Z128, mem_budget=int(budget_gb * 2**30))
+    stats = srv.run(reqs, keep_outputs=True)
+    assert stats["requests"] == 6
+    mixed = {r.rid: outputs(r) for r in reqs}
+    for r in fresh(reqs):
+        Server(ring=synth.Z128, mem_budget=int(budget_gb * 2**30)).run([r], keep_outputs=True)
+        alone = outputs(r)
+        for li, (a, b) in enumerate(zip(alone, mixed[r.rid])):
+            for k in OUT_KEYS:
+                assert np.array_equal(a[k], b[k]), f"request {r.rid} layer {li} {k}"
+    assert abi.mpc_device_status() == 0
+
+
+def test_memory_gate_limits_residency():
+    reqs = make_requests(5, 1e6, seed=4, max_batch=2)
+    biggest = max(request_bytes(r.layers, 2) for r in reqs)
+    srv = Server(ring=synth.Z128, mem_budget=biggest + 1)
+    stats = srv.run(reqs)
+    assert stats["requests"] == 5
+    assert stats["peak_resident_bytes"] <= biggest + 1
+
+
+def test_served_layers_match_oracle():
+    """One request's small layers against the oracle (full outputs)."""
+    reqs = make_requests(3, 1e6, seed=5, max_batch=1, models=("resnet18",))
+    Server(ring=synth.Z128, mem_budget=200 * 2**30).run(reqs, keep_outputs=True)
+    bits = 128
+    r = reqs[1]
+    checked = 0
+    for L, d in zip(r.layers, r.bufs):
+        if L.M * L.K * L.N > 3e7:
+            continue
+        g = {k: host(d[k]) for k in ("E", "F", "A", "B", "C", "mA", "mB", "mC", "mR", "Dt", "chi", "alpha",
+                                      "chi_hat")}
+        Z = O.linear_share(bits, 0, g["E"], g["F"], g["A"], g["B"], g["C"])
+        assert np.array_equal(host(d["Z"]), Z), L
+        mDc, Dc, _ = O.compact_tag(bits, g["alpha"], g["E"], g["F"], g["mA"], g["mB"], g["mC"], g["mR"], g["Dt"],
+                                   g["chi"])
+        assert np.array_equal(host(d["mDc"]), mDc) and np.array_equal(host(d["Dc"]), Dc), L
+        assert np.array_equal(host(d["mZ"]), O.optmac(bits, g["alpha"], g["mR"], g["Dt"])), L
+        cs = O.check_compact(bits, g["alpha"], g["chi_hat"], Dc, mDc)
+        assert np.array_equal(host(d["cs"]).reshape(-1), cs.reshape(-1)), L
+        checked += 1
+    assert checked >= 3
