@@ -425,13 +425,38 @@ class GpuRun:
                     n += 4   # two transposes before the share, one before each tag
         return n
 
+    COPY_STREAMS = 4
+
+    def _copy_streams(self):
+        if not hasattr(self, "_cs"):
+            self._cs = [self.torch.cuda.Stream() for _ in range(self.COPY_STREAMS)]
+        return self._cs
+
+    def _spread(self, pairs, fn):
+        """Issue the copies round-robin on several streams (several copy
+        engines), each ordered after the work already on the compute stream,
+        and make the compute stream wait for all of them."""
+        torch = self.torch
+        st = torch.cuda.current_stream()
+        cs = self._copy_streams()
+        # largest copies first, dealt so that the streams carry similar bytes
+        order = sorted(range(len(pairs)), key=lambda i: -pairs[i][0].numel())
+        load = [0] * len(cs)
+        for c in cs:
+            c.wait_stream(st)
+        for i in order:
+            j = min(range(len(cs)), key=lambda k: load[k])
+            load[j] += pairs[i][0].numel()
+            with torch.cuda.stream(cs[j]):
+                fn(*pairs[i])
+        for c in cs:
+            st.wait_stream(c)
+
     def h2d(self):
-        for h, d in self.h2d_pairs:
-            d.copy_(h, non_blocking=True)
+        self._spread(self.h2d_pairs, lambda h, d: d.copy_(h, non_blocking=True))
 
     def d2h(self):
-        for h, d in zip(self.h_outputs, self.outputs):
-            h.copy_(d, non_blocking=True)
+        self._spread(list(zip(self.h_outputs, self.outputs)), lambda h, d: h.copy_(d, non_blocking=True))
 
     def h2d_bytes(self):
         return sum(h.numel() * 8 for h, _ in self.h2d_pairs)
@@ -540,6 +565,15 @@ def run_ours(args):
     if PASS == "train":
         layers = layers + synth.backward_layers(layers)
     workload = wl_name.format(b=args.batch) + ("_train" if PASS == "train" else "")
+    tune = None
+    if args.autotune:
+        t0 = time.perf_counter()
+        shapes = [abi.make_layer(L.M, L.K, L.N, RING.k, RING.s) for L in layers]
+        n_tuned = abi.mpc_autotune(shapes)
+        torch.cuda.synchronize()
+        tc_after = sum(1 for L in shapes if abi.mpc_gemm_path(L) == 1)
+        tune = {"shapes": n_tuned, "seconds": time.perf_counter() - t0, "tensor_core_layers": tc_after,
+                "choices": sorted({abi.mpc_autotune_choice(L)[:3] for L in shapes})}
     run = GpuRun(layers, torch, abi, pinned_host=not args.no_e2e)
     units = step_units(layers)
     if args.grouped:
@@ -720,6 +754,7 @@ def run_ours(args):
             "per_layer": per_layer,
             "per_group_call": per_group,
             "grouped": bool(args.grouped),
+            "autotune": tune,
             "ms_per_step_per_layer_calls": per_layer_calls_ms,
             "roofline": roof,
             "compact_hbm_roofline": hbm_roof,
@@ -922,6 +957,8 @@ def main():
                          "OptMAC&Trunc, compact tag without the E.F term)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per serving run")
     ap.add_argument("--serve-budget-gb", type=float, default=96.0, help="serving memory budget (GiB)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="fill the launch table for the workload's shapes (timed candidates) before warm-up")
     ap.add_argument("--grouped", action="store_true",
                     help="one grouped call of each kind per party for all layers (persistent grouped "
                          "tensor-core launches) instead of one call per layer")

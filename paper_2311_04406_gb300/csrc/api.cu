@@ -472,13 +472,13 @@ int mpc_linear_tag_grouped(const mpc_layer* layers, int count, int mode, const m
         if (!ws || ws_bytes < need) return MPC_E_WORKSPACE;
         if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
     }
-    uint8_t* cur = static_cast<uint8_t*>(ws);
+    std::vector<char*> slices((size_t)count);
+    char* cur = static_cast<char*>(ws);
     for (int i = 0; i < count; ++i) {
-        const size_t b = (mpcl::compact_workspace(c[i].M, c[i].K, c[i].N, c[i].words) + 255) & ~size_t(255);
-        CHK(cuda_status(mpcl::launch_compact(c[i], cur, b, st)));
-        cur += b;
+        slices[i] = cur;
+        cur += (mpcl::compact_workspace(c[i].M, c[i].K, c[i].N, c[i].words) + 255) & ~size_t(255);
     }
-    return MPC_OK;
+    return cuda_status(mpcl::launch_compact_grouped(c.data(), count, slices.data(), st));
 }
 
 size_t mpc_workspace_size_grouped(const mpc_layer* layers, int count, int which) {
@@ -507,10 +507,19 @@ int mpc_launch_count_grouped(const mpc_layer* layers, int count, int which) {
             if (on_tc(L)) ++tc;
             else if (L.M > 0 && L.N > 0) n += 1;
         } else if (which == MPC_WS_TAG_COMPACT) {
-            n += mpcl::compact_launches(L.M, L.K, L.N);
+            // counted below for the whole group
         } else {
             return MPC_E_MODE;
         }
+    }
+    if (which == MPC_WS_TAG_COMPACT) {
+        std::vector<int64_t> M((size_t)count), K((size_t)count), N((size_t)count);
+        for (int i = 0; i < count; ++i) {
+            M[i] = layers[i].M;
+            K[i] = layers[i].K;
+            N[i] = layers[i].N;
+        }
+        return mpcl::compact_grouped_launches(M.data(), K.data(), N.data(), count);
     }
     return n + mpcl::gemm_tc_grouped_launches(tc);
 }

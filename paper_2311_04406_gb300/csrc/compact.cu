@@ -16,6 +16,8 @@
 //                    mA against those vectors, then mZc, mDc and Dc.
 // Every sum is a wrapping sum mod 2^(64 W), so the split into chunks does not
 // change any result bit.
+#include <new>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -95,12 +97,11 @@ struct RowsParams {
     u64 *pmr, *pd, *pmc, *qmb, *qf;
 };
 
-// VEC = 2: two Z_2^64 elements per 16-byte access (needs even N).
+// VEC = 2: two Z_2^64 elements per 16-byte access (needs even N).  Warp
+// task g of one layer.
 template <int W, int VEC>
-__global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
+__device__ __forceinline__ void rows_body(const RowsParams& p, int64_t g, int lane) {
     using T = typename Elem<W>::T;
-    const int lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
     const int64_t tasksA = p.M * p.S, tasksB = p.K * p.S;
     if (g >= tasksA + tasksB) return;
     const bool isA = g < tasksA;
@@ -175,12 +176,16 @@ __global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
     }
 }
 
+template <int W, int VEC>
+__global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
+    rows_body<W, VEC>(p, (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5), threadIdx.x & 31);
+}
+
 template <int W>
-__global__ void finalize_kernel(int64_t K, int64_t S, const u64* qmb, const u64* qf,
-                                u64* vmb, u64* vf) {
+__device__ __forceinline__ void finalize_body(int64_t K, int64_t S, const u64* qmb, const u64* qf, u64* vmb,
+                                              u64* vf, int64_t id, int64_t nthreads) {
     using T = typename Elem<W>::T;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
-         k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t k = id; k < K; k += nthreads) {
         T a = 0, b = 0;
         for (int64_t s = 0; s < S; ++s) {
             a += ld_elem<W>(qmb, k * S + s);
@@ -189,6 +194,13 @@ __global__ void finalize_kernel(int64_t K, int64_t S, const u64* qmb, const u64*
         st_elem<W>(vmb, k, a);
         st_elem<W>(vf, k, b);
     }
+}
+
+template <int W>
+__global__ void finalize_kernel(int64_t K, int64_t S, const u64* qmb, const u64* qf,
+                                u64* vmb, u64* vf) {
+    finalize_body<W>(K, S, qmb, qf, vmb, vf, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                     (int64_t)gridDim.x * blockDim.x);
 }
 
 struct VecParams {
@@ -201,12 +213,12 @@ struct VecParams {
 // `wpr` warps share one row (1, 2, 4 or 8), each taking every wpr-th chunk of
 // 32 (or 64, vectorised) K values; their partial sums meet in shared memory.
 template <int W, int VEC>
-__global__ void __launch_bounds__(NT) vec_kernel(VecParams p, int wpr) {
+__device__ __forceinline__ void vec_body(const VecParams& p, int wpr, int64_t blk) {
     using T = typename Elem<W>::T;
     __shared__ T part[3][WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rows_per_block = WARPS / wpr;
-    const int64_t r = (int64_t)blockIdx.x * rows_per_block + warp / wpr;
+    const int64_t r = blk * rows_per_block + warp / wpr;
     const int sub = warp % wpr;
     T e_mb = 0, ma_u = 0, e_u = 0;
     if (r < p.M) {
@@ -263,12 +275,17 @@ __global__ void __launch_bounds__(NT) vec_kernel(VecParams p, int wpr) {
     }
 }
 
+template <int W, int VEC>
+__global__ void __launch_bounds__(NT) vec_kernel(VecParams p, int wpr) {
+    vec_body<W, VEC>(p, wpr, blockIdx.x);
+}
+
 // K < 64: one thread per row, the two compressed K-vectors staged in shared
 // memory (a warp per row would leave most lanes idle)
 constexpr int SMALL_K = 64;
 
 template <int W>
-__global__ void __launch_bounds__(NT) vec_small_kernel(VecParams p) {
+__device__ __forceinline__ void vec_small_body(const VecParams& p, int64_t blk) {
     using T = typename Elem<W>::T;
     __shared__ T smb[SMALL_K], sf[SMALL_K];
     for (int k = threadIdx.x; k < p.K; k += NT) {
@@ -276,7 +293,7 @@ __global__ void __launch_bounds__(NT) vec_small_kernel(VecParams p) {
         sf[k] = ld_elem<W>(p.vf, k);
     }
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t r = blk * NT + threadIdx.x;
     if (r >= p.M) return;
     T e_mb = 0, ma_u = 0, e_u = 0;
     const int64_t base = r * p.K;
@@ -297,6 +314,11 @@ __global__ void __launch_bounds__(NT) vec_small_kernel(VecParams p) {
     const T mzc = mcc + e_mb + ma_u + (p.with_eu ? alpha * e_u : (T)0);
     st_elem<W>(p.mDc, r, mrc - mzc);
     st_elem<W>(p.Dc, r, dc);
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) vec_small_kernel(VecParams p) {
+    vec_small_body<W>(p, blockIdx.x);
 }
 
 int vec_warps_per_row(int64_t K) {
@@ -340,6 +362,137 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// grouped: the tags of up to CG layers in three launches (rows, finalize,
+// vec).  Per-layer parameters travel in the kernels' parameter space; a block
+// finds its layer by a binary search over the layers' first blocks.
+
+constexpr int CG = 64;
+
+struct CompactLayer {
+    RowsParams rp;
+    VecParams vp;
+    int rows_vec2;   // rows pass on 16-byte pairs
+    int vec_small;   // K < SMALL_K: one thread per row
+    int vec_vec2;    // vec pass on 16-byte pairs
+    int wpr;         // warps per row in the vec pass
+    u64 *vmb, *vf;
+};
+
+struct CompactGroup {
+    int count;
+    int64_t rb[CG + 1], fb[CG + 1], vb[CG + 1];   // first block of each layer, per kernel
+    CompactLayer L[CG];
+};
+static_assert(sizeof(CompactGroup) + 64 <= 32764, "kernel parameter space");
+
+// the last layer whose first block is at or before block b (layers with no
+// blocks in this kernel share their successor's offset and are skipped)
+__device__ __forceinline__ int layer_of(const int64_t* off, int count, int64_t b) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) rows_group_kernel(const __grid_constant__ CompactGroup g) {
+    const int li = layer_of(g.rb, g.count, blockIdx.x);
+    const CompactLayer& L = g.L[li];
+    const int64_t task = ((int64_t)blockIdx.x - g.rb[li]) * WARPS + (threadIdx.x >> 5);
+    if (W == 1 && L.rows_vec2) rows_body<W, 2>(L.rp, task, threadIdx.x & 31);
+    else rows_body<W, 1>(L.rp, task, threadIdx.x & 31);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) finalize_group_kernel(const __grid_constant__ CompactGroup g) {
+    const int li = layer_of(g.fb, g.count, blockIdx.x);
+    const CompactLayer& L = g.L[li];
+    const int64_t nb = g.fb[li + 1] - g.fb[li];
+    finalize_body<W>(L.rp.K, L.rp.S, L.rp.qmb, L.rp.qf, L.vmb, L.vf,
+                     ((int64_t)blockIdx.x - g.fb[li]) * 256 + threadIdx.x, nb * 256);
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) vec_group_kernel(const __grid_constant__ CompactGroup g) {
+    const int li = layer_of(g.vb, g.count, blockIdx.x);
+    const CompactLayer& L = g.L[li];
+    const int64_t blk = (int64_t)blockIdx.x - g.vb[li];
+    if (L.vec_small) vec_small_body<W>(L.vp, blk);
+    else if (W == 1 && L.vec_vec2) vec_body<W, 2>(L.vp, L.wpr, blk);
+    else vec_body<W, 1>(L.vp, L.wpr, blk);
+}
+
+// blocks of each kernel for one layer
+struct CompactBlocks {
+    int64_t rows, fin, vec;
+};
+
+CompactBlocks compact_blocks(int64_t M, int64_t K, int64_t N) {
+    CompactBlocks b{0, 0, 0};
+    if (M == 0) return b;
+    const Split sp = choose_split(M, K, N);
+    b.rows = ((M + K) * sp.S + WARPS - 1) / WARPS;
+    if (K > 0) {
+        b.fin = (K + 255) / 256;
+        if (b.fin > 1024) b.fin = 1024;
+    }
+    if (K < SMALL_K) {
+        b.vec = (M + NT - 1) / NT;
+    } else {
+        const int64_t rpb = WARPS / vec_warps_per_row(K);
+        b.vec = (M + rpb - 1) / rpb;
+    }
+    return b;
+}
+
+template <int W>
+cudaError_t run_group(const CompactArgs* a, int n, char* const* ws, cudaStream_t st) {
+    auto* g = new (std::nothrow) CompactGroup;
+    if (!g) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaSuccess;
+    int i = 0;
+    while (i < n && e == cudaSuccess) {
+        int cnt = 0;
+        g->rb[0] = g->fb[0] = g->vb[0] = 0;
+        for (; i < n && cnt < CG; ++i) {
+            const CompactArgs& x = a[i];
+            if (x.M == 0) continue;
+            const Split sp = choose_split(x.M, x.K, x.N);
+            const WsLayout wl = ws_layout(x.M, x.K, x.N, W);
+            char* w = ws[i];
+            CompactLayer& L = g->L[cnt];
+            L.rp = RowsParams{x.M, x.K, x.N, sp.S, sp.cw, x.alpha, x.mR, x.Dt, x.mC, x.mB, x.F, x.chi, x.mZ,
+                              (u64*)(w + wl.pmr), (u64*)(w + wl.pd), (u64*)(w + wl.pmc),
+                              (u64*)(w + wl.qmb), (u64*)(w + wl.qf)};
+            L.vmb = (u64*)(w + wl.vmb);
+            L.vf = (u64*)(w + wl.vf);
+            L.vp = VecParams{x.M, x.K, sp.S, x.with_eu, x.alpha, x.E, x.mA, L.vmb, L.vf, L.rp.pmr, L.rp.pd,
+                             L.rp.pmc, x.mDc, x.Dc};
+            L.rows_vec2 = (x.N % 2) == 0;
+            L.vec_small = x.K < SMALL_K;
+            L.vec_vec2 = (x.K % 2) == 0;
+            L.wpr = vec_warps_per_row(x.K);
+            const CompactBlocks b = compact_blocks(x.M, x.K, x.N);
+            g->rb[cnt + 1] = g->rb[cnt] + b.rows;
+            g->fb[cnt + 1] = g->fb[cnt] + b.fin;
+            g->vb[cnt + 1] = g->vb[cnt] + b.vec;
+            ++cnt;
+        }
+        if (cnt == 0) break;
+        g->count = cnt;
+        if (g->rb[cnt] > 0) rows_group_kernel<W><<<(unsigned)g->rb[cnt], NT, 0, st>>>(*g);
+        if (g->fb[cnt] > 0) finalize_group_kernel<W><<<(unsigned)g->fb[cnt], 256, 0, st>>>(*g);
+        if (g->vb[cnt] > 0) vec_group_kernel<W><<<(unsigned)g->vb[cnt], NT, 0, st>>>(*g);
+        e = cudaGetLastError();
+    }
+    delete g;
+    return e;
+}
+
 }  // namespace
 
 int compact_launches(int64_t M, int64_t K, int64_t N) {
@@ -350,6 +503,34 @@ int compact_launches(int64_t M, int64_t K, int64_t N) {
 
 size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words) {
     return ws_layout(M, K, N, words).total;
+}
+
+int compact_grouped_launches(const int64_t* M, const int64_t* K, const int64_t* N, int n) {
+    int launches = 0, cnt = 0;
+    int64_t r = 0, f = 0, v = 0;
+    for (int i = 0; i <= n; ++i) {
+        if (i == n || cnt == CG) {
+            launches += (r > 0) + (f > 0) + (v > 0);
+            r = f = v = 0;
+            cnt = 0;
+            if (i == n) break;
+        }
+        if (M[i] == 0) continue;
+        const CompactBlocks b = compact_blocks(M[i], K[i], N[i]);
+        r += b.rows;
+        f += b.fin;
+        v += b.vec;
+        ++cnt;
+    }
+    return launches;
+}
+
+cudaError_t launch_compact_grouped(const CompactArgs* a, int n, char* const* ws, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int w = a[0].words;
+    for (int i = 0; i < n; ++i)
+        if (a[i].words != w) return cudaErrorInvalidValue;
+    return w == 1 ? run_group<1>(a, n, ws, st) : run_group<2>(a, n, ws, st);
 }
 
 cudaError_t launch_compact(const CompactArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {

@@ -80,6 +80,10 @@ struct CompactArgs {
 size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words);
 int compact_launches(int64_t M, int64_t K, int64_t N);
 cudaError_t launch_compact(const CompactArgs& a, void* ws, size_t ws_bytes, cudaStream_t st);
+// the tags of many layers (one ring width) in three launches per 64 layers;
+// layer i's workspace (compact_workspace bytes) at ws[i]
+cudaError_t launch_compact_grouped(const CompactArgs* a, int n, char* const* ws, cudaStream_t st);
+int compact_grouped_launches(const int64_t* M, const int64_t* K, const int64_t* N, int n);
 
 // truncated layer: OptMAC&Trunc elementwise step
 cudaError_t launch_optmac_trunc(int64_t MN, int words, int k, int f, int party0, const u64* alpha,

@@ -8,8 +8,9 @@ completion.  The scheduler
 
   * admits arrived requests first-come first-served while their shares fit a
     device-memory budget (memory-gated admission);
-  * materialises an admitted request's shares on a side stream, so that input
-    preparation overlaps the layers already running;
+  * materialises an admitted request's shares on a side stream (device copies
+    out of a seeded pool of uniform words standing in for the offline phase's
+    output), so that input preparation overlaps the layers already running;
   * runs one "tick" at a time: the next linear layer of every admitted,
     ready request, as ONE grouped share call, ONE grouped tag call and the
     per-layer checks (continuous batching: a request joins at the next tick
@@ -92,8 +93,10 @@ def make_requests(n: int, rate: float, seed: int, max_batch: int = 32, models=("
 
 
 class Server:
+    POOL_WORDS = 1 << 28          # 2 GiB of uniform words, larger than any one share tensor
+
     def __init__(self, ring=synth.Z128, party: int = 0, nparties: int = 2, mem_budget: int = 96 << 30,
-                 tag: str = "compact", max_inflight: int = 2, max_group: int = 512):
+                 tag: str = "compact", max_inflight: int = 2, max_group: int = 512, pool_seed: int = 0x5EED):
         import torch
         if tag not in ("compact", "full"):
             raise ValueError("tag must be 'compact' or 'full'")
@@ -102,28 +105,41 @@ class Server:
         self.mem_budget, self.tag = mem_budget, tag
         self.max_inflight, self.max_group = max_inflight, max_group
         abi.load()
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(pool_seed)
+        self.pool = torch.randint(-(1 << 63), (1 << 63) - 1, (self.POOL_WORDS,), dtype=torch.int64,
+                                  device="cuda", generator=gen)
 
     # -- request shares -------------------------------------------------------
     def _materialise(self, req: Request, stream):
-        """Allocate and fill the request's shares on `stream` (seeded, so the
-        same request always gets the same shares)."""
+        """Allocate the request's shares and fill them on `stream` with copies
+        of pool windows at offsets drawn from the request's seed (so the same
+        request always gets the same shares)."""
         torch = self.torch
         w = self.ring.words
         shp = (lambda *d: d + ((2,) if w == 2 else ()))
         gen = torch.Generator(device="cuda")
         gen.manual_seed(req.seed)
-        lo, hi = -(1 << 63), (1 << 63) - 1
+        rng = np.random.default_rng(req.seed)
         bufs = []
+
+        def window(shape):
+            n = int(np.prod(shape))
+            off = int(rng.integers(0, self.POOL_WORDS - n + 1))
+            t = torch.empty(shape, dtype=torch.int64, device="cuda")
+            t.view(-1).copy_(self.pool[off:off + n], non_blocking=True)
+            return t
+
         with torch.cuda.stream(stream):
             for L in req.layers:
                 M, K, N = L.M, L.K, L.N
                 d = {}
                 for k in KEYS_MK:
-                    d[k] = torch.randint(lo, hi, shp(M, K), dtype=torch.int64, device="cuda", generator=gen)
+                    d[k] = window(shp(M, K))
                 for k in KEYS_KN:
-                    d[k] = torch.randint(lo, hi, shp(K, N), dtype=torch.int64, device="cuda", generator=gen)
+                    d[k] = window(shp(K, N))
                 for k in KEYS_MN:
-                    d[k] = torch.randint(lo, hi, shp(M, N), dtype=torch.int64, device="cuda", generator=gen)
+                    d[k] = window(shp(M, N))
                 # key share and combiners: uniform in [0, 2^s) (s <= 63 here: 2^63 - 1 bound)
                 smax = (1 << min(self.ring.s, 63)) - 1
                 d["alpha"] = torch.zeros(shp(1), dtype=torch.int64, device="cuda")

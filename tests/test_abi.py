@@ -107,8 +107,10 @@ def test_grouped_host_logic(lib):
     # one prologue + GEMM pair for the three tensor-core layers, one kernel for the other
     assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_SHARE) == 2 + 1
     assert abi.mpc_launch_count_grouped(layers * 30, abi.MPC_WS_TAG_FULL) == 2 * 2 + 30
-    assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_TAG_COMPACT) == \
-        sum(abi.mpc_launch_count(L, abi.MPC_WS_TAG_COMPACT) for L in layers)
+    # the CompactTag tags of a group: rows, finalize and vec passes, one launch each per 64 layers
+    assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_TAG_COMPACT) == 3
+    assert abi.mpc_launch_count_grouped(layers * 20, abi.MPC_WS_TAG_COMPACT) == 6
+    assert abi.mpc_launch_count_grouped([abi.make_layer(0, 4, 4)], abi.MPC_WS_TAG_COMPACT) == 0
     mixed = [abi.make_layer(8, 8, 8), abi.make_layer(8, 8, 8, 64, 64)]
     assert abi.mpc_launch_count_grouped(mixed, abi.MPC_WS_SHARE) == abi.MPC_E_RING
     assert abi.mpc_workspace_size_grouped(mixed, abi.MPC_WS_SHARE) == 0
