@@ -240,6 +240,7 @@ class GpuRun:
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64))
         self.items = []
         self.h2d_pairs = []   # (host pinned, device) for the e2e copy
+        self.h2d_by = {}      # (layer, party or "pub") -> its pairs, for the pipelined e2e step
         # backward layers: operands that are transposes of forward operands
         # (index of the forward layer, public key, share key, tag key, forward dims)
         names = {L.name: i for i, L in enumerate(layers)}
@@ -276,16 +277,26 @@ class GpuRun:
                 if pinned_host:
                     for k, v in sh.items():
                         if k not in derived:
-                            self.h2d_pairs.append((t(v).pin_memory(), d[k]))
+                            self.h2d_by.setdefault((li, p), []).append((t(v).pin_memory(), d[k]))
             if pinned_host:
                 for k, v in pub.items():
                     if k not in derived:
-                        self.h2d_pairs.append((t(v).pin_memory(), dpub[k]))
+                        self.h2d_by.setdefault((li, "pub"), []).append((t(v).pin_memory(), dpub[k]))
+                for key in [(li, "pub")] + [(li, p) for p in range(len(parties))]:
+                    self.h2d_pairs += self.h2d_by.get(key, [])
             self.items.append((L, dpub, dpar))
         out_keys = ("Z", "mZfull", "mZ", "mDc", "Dc", "cs") if PROTOCOL == "plain" else \
             ("Z", "mZfull", "Zf", "mZf_t", "mDc", "Dc", "cs")
         self.outputs = [d[k] for _, _, dpar in self.items for d in dpar for k in out_keys]
         self.h_outputs = [o.cpu().pin_memory() for o in self.outputs] if pinned_host else []
+        nk = len(out_keys)
+        self.d2h_by = {}
+        if pinned_host:
+            j = 0
+            for li, (_, _, dpar) in enumerate(self.items):
+                for p in range(len(dpar)):
+                    self.d2h_by[(li, p)] = list(zip(self.h_outputs[j:j + nk], self.outputs[j:j + nk]))
+                    j += nk
 
     def _transpose(self, src, dst, rows, cols):
         self.abi.mpc_transpose(RING.k, RING.s, rows, cols, src, dst)
@@ -452,6 +463,43 @@ class GpuRun:
         for c in cs:
             st.wait_stream(c)
 
+    def e2e_step(self):
+        """One step with its host copies pipelined: the inputs are copied in
+        the order the step consumes them (layer by layer, party by party) on a
+        copy stream, each call waits only for its own inputs, and each party's
+        outputs are copied back on a second stream as soon as they exist."""
+        torch = self.torch
+        st = torch.cuda.current_stream()
+        if not hasattr(self, "_h2d_stream"):
+            self._h2d_stream, self._d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
+        cs, ds = self._h2d_stream, self._d2h_stream
+        cs.wait_stream(st)        # the previous step is done with the buffers
+        ready = {}
+        for i in range(len(self.items)):
+            with torch.cuda.stream(cs):
+                for h, d in self.h2d_by.get((i, "pub"), []):
+                    d.copy_(h, non_blocking=True)
+                for p in range(PARTIES):
+                    for h, d in self.h2d_by.get((i, p), []):
+                        d.copy_(h, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(cs)
+                    ready[(i, p)] = ev
+        ds.wait_stream(st)
+        for i in range(len(self.items)):
+            for p in range(PARTIES):
+                st.wait_event(ready[(i, p)])
+                self.share(i, p)
+                self.full(i, p)
+                self.compact(i, p)
+                done = torch.cuda.Event()
+                done.record(st)
+                ds.wait_event(done)
+                with torch.cuda.stream(ds):
+                    for h, d in self.d2h_by[(i, p)]:
+                        h.copy_(d, non_blocking=True)
+        st.wait_stream(ds)
+
     def h2d(self):
         self._spread(self.h2d_pairs, lambda h, d: d.copy_(h, non_blocking=True))
 
@@ -465,10 +513,11 @@ class GpuRun:
         return sum(h.numel() * 8 for h in self.h_outputs)
 
 
-def time_calls(torch, fn, reps, graph=True):
+def time_calls(torch, fn, reps, graph=True, budget_s=None):
     """Per-call device durations (ms) with CUDA events on the launching stream;
     with graph=True the call is captured once and its graph replayed, so host
-    launch overhead is not counted."""
+    launch overhead is not counted.  With budget_s, `reps` is a maximum: the
+    count is cut so that the timed calls take about budget_s (at least 20)."""
     st = torch.cuda.current_stream()
     call = fn
     if graph:
@@ -484,6 +533,15 @@ def time_calls(torch, fn, reps, graph=True):
         torch.cuda.synchronize()
         call = g.replay
         call()
+    if budget_s is not None:
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(st)
+        for _ in range(3):
+            call()
+        a1.record(st)
+        torch.cuda.synchronize()
+        per = max(a0.elapsed_time(a1) / 3e3, 1e-6)
+        reps = int(min(reps, max(20, budget_s / per)))
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(reps)]
     for a, b in evs:
@@ -619,7 +677,7 @@ def run_ours(args):
         per_layer_calls_ms = timed_steps(torch, g2.replay, args.steps)
         del g2
 
-    reps = max(10, min(50, args.steps * 2))
+    reps = 200                    # at most; each call kind gets about 2 s
     graphs = not args.eager
     hbm, bf16, bf16s, src = peaks()
     digit = costmodel.digit_products(RING.bits)
@@ -629,10 +687,11 @@ def run_ours(args):
         # call of each kind in the grouped step, as one call per layer otherwise)
         if not args.grouped:
             run.setup_grouped()
-        sh = time_calls(torch, lambda: run.share_group(1), reps, graphs)
-        fu = time_calls(torch, lambda: run.full_group(1), reps, graphs)
-        co = time_calls(torch, lambda: run.compact_group(1), reps, graphs)
-        per_group = dict(layers=len(layers), share_ms_p50=pct(sh, 50), full_tag_ms_p50=pct(fu, 50),
+        sh = time_calls(torch, lambda: run.share_group(1), reps, graphs, budget_s=2.0)
+        fu = time_calls(torch, lambda: run.full_group(1), reps, graphs, budget_s=2.0)
+        co = time_calls(torch, lambda: run.compact_group(1), reps, graphs, budget_s=2.0)
+        per_group = dict(layers=len(layers), timed_calls=len(sh), share_ms_p50=pct(sh, 50),
+                         full_tag_ms_p50=pct(fu, 50),
                          compact_tag_ms_p50=pct(co, 50), compact_tag_ms_p99=pct(co, 99),
                          full_tag_ms_p99=pct(fu, 99))
         sum_co, sum_fu = pct(co, 50), pct(fu, 50)
@@ -658,14 +717,17 @@ def run_ours(args):
     else:
         gemm_ms_by_layer = []
         for i, L in enumerate(layers):
-            sh = time_calls(torch, lambda: run.share(i, 1), reps, graphs)
-            fu = time_calls(torch, lambda: run.full(i, 1), reps, graphs)
-            co = time_calls(torch, lambda: run.compact(i, 1), reps, graphs)
+            sh = time_calls(torch, lambda: run.share(i, 1), reps, graphs, budget_s=1.0)
+            fu = time_calls(torch, lambda: run.full(i, 1), reps, graphs, budget_s=1.0)
+            co = time_calls(torch, lambda: run.compact(i, 1), reps, graphs, budget_s=1.0)
             per_layer.append(dict(layer=L.name, M=L.M, K=L.K, N=L.N,
                                   share_ms_p50=pct(sh, 50), full_tag_ms_p50=pct(fu, 50),
                                   compact_tag_ms_p50=pct(co, 50), compact_tag_ms_p99=pct(co, 99),
                                   full_tag_ms_p99=pct(fu, 99),
                                   tag_overhead_ratio=pct(co, 50) / pct(fu, 50),
+                                  full_tag_over_share=pct(fu, 50) / pct(sh, 50),
+                                  compact_tag_over_share=pct(co, 50) / pct(sh, 50),
+                                  timed_calls=len(sh),
                                   share_ring_gmacs=2 * L.M * L.K * L.N / (pct(sh, 50) / 1e3) / 1e9,
                                   cost_model_tag_ratio=costmodel.tag_mult_ratio(L.M, L.K, L.N)))
             gemm_ms_by_layer.append(sh + fu)
@@ -715,17 +777,24 @@ def run_ours(args):
         t0 = time.perf_counter()
         a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
         a.record(st)
+        pipelined = not args.grouped and not run.links
         for _ in range(e2e_steps):
-            run.h2d()
-            step_eager()
-            run.d2h()
+            if pipelined:
+                run.e2e_step()
+            else:
+                run.h2d()
+                step_eager()
+                run.d2h()
         b.record(st)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         e2e_ms = max_over_ranks(max(a.elapsed_time(b), wall * 1e3), ws) / e2e_steps
         e2e = {"value": ws * units / (e2e_ms / 1e3) / 1e9, "unit": "ring-GMAC/s",
                "ms_per_step": e2e_ms, "h2d_bytes_per_step": run.h2d_bytes(),
-               "d2h_bytes_per_step": run.d2h_bytes(), "host_buffers": "pinned"}
+               "d2h_bytes_per_step": run.d2h_bytes(), "host_buffers": "pinned",
+               "copies": "pipelined with the calls (inputs layer by layer and party by party on a copy "
+                         "stream, outputs back as produced)" if pipelined else
+                         "all inputs, then the step, then all outputs"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -833,8 +902,18 @@ def cpu_baseline(layers, budget_s=15.0):
     frac = min(1.0, max(1.0 / 128, (budget_s * rate) / full_units))
     run, units = cpu_sample(layers, frac)
     t0 = time.perf_counter(); run(); t1 = time.perf_counter()
-    return {"value": units / (t1 - t0) / 1e9, "unit": "ring-GMAC/s", "cores": cpu_cores(),
+    # the same oracle on one core, on a sample a core count smaller
+    import oracle as O
+    cores = cpu_cores()
+    old = O.set_threads(1)
+    try:
+        run1, units1 = cpu_sample(layers, max(1.0 / 4096, frac / max(1, cores)))
+        s0 = time.perf_counter(); run1(); s1 = time.perf_counter()
+    finally:
+        O.set_threads(old)
+    return {"value": units / (t1 - t0) / 1e9, "unit": "ring-GMAC/s", "cores": cores,
             "kind": "oracle", "seconds": t1 - t0,
+            "single_thread": {"value": units1 / (s1 - s0) / 1e9, "seconds": s1 - s0, "cores": 1},
             "sample": (f"share + full tag at the first {frac:.4f} of output rows of both layers and "
                        f"both parties, plus the whole CompactTag tag and check of both layers and "
                        f"parties ({units:.3e} ring MACs)")}
@@ -918,7 +997,7 @@ def run_serve(args):
         st = srv.run(reqs)
         st.update(offered_fraction=frac, offered_rate_per_s=rate)
         runs.append(st)
-    full = Server(ring=ring, mem_budget=budget, tag="full").run(make_requests(n, 1e9, seed=SEED, all_at_once=True))
+    full = srv.run(make_requests(n, 1e9, seed=SEED, all_at_once=True), tag="full")
     line = {
         "metric": METRIC, "value": value, "unit": "ring-GMAC/s", "n_gpus": 1,
         "steps": n, "warmup": args.warmup, "ms_per_step": cap["makespan_ms"] / n,

@@ -329,3 +329,8 @@ def chi_seeded(bits, s, seed, shape):
     n = int(np.prod(shape, dtype=np.int64)) if shape else 1
     _load().orc_chi_seeded(bits, s, int(seed) & 0xFFFFFFFFFFFFFFFF, n, _p(out))
     return out
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of the oracle's loops; returns the previous maximum."""
+    return int(_load().orc_set_threads(int(n)))

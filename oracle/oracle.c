@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <stddef.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef unsigned __int128 u128;
 typedef uint64_t u64;
@@ -383,4 +386,18 @@ void orc_chi_seeded(int b, int s, u64 seed, i64 n, u64 *out) {
     u128 ms = mask_of(s);
     for (i64 i = 0; i < n; ++i)
         st(out, i, w, (u128)splitmix_mix(seed + (u64)(i + 1) * g) & ms);
+}
+
+
+/* Threads of the OpenMP loops (for timing the oracle on one core or on all of
+ * them); n <= 0 leaves the setting alone.  Returns the previous maximum. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    const int old = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return old;
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -55,6 +55,8 @@ class Request:
     seed: int
     layers: list = field(default_factory=list)
     bufs: list = None              # per layer: dict of device tensors
+    region: tuple = None           # (offset, bytes) in the server's arena
+    plan: list = None              # per layer: key -> (shape, byte offset in the region)
     nxt: int = 0                   # next layer to run
     ready: object = None           # event: shares materialised
     done_ms: float = None          # device time of completion
@@ -66,14 +68,91 @@ class Request:
         return sum(2 * L.M * L.K * L.N for L in self.layers)
 
 
+OUT_MN = ("Z", "mZ")
+OUT_M = ("mDc", "Dc")
+
+
+def _carve(layers, words: int):
+    """The byte layout of a request's resident tensors, in three sections:
+    the pool-filled inputs (256-byte aligned tensors), the keys and combiners
+    (alpha, chi, chi^: 16-byte aligned, filled by one generator call) and the
+    outputs.  Returns (plan, inputs_end, keys_end, total), plan[layer][key] =
+    (shape, byte offset)."""
+    shp = (lambda *d: d + ((2,) if words == 2 else ()))
+    plan = [dict() for _ in layers]
+
+    def put(li, k, shape, off, align):
+        plan[li][k] = (shape, off)
+        return off + (8 * int(np.prod(shape)) + align - 1) // align * align
+
+    off = 0
+    for li, L in enumerate(layers):
+        for k in KEYS_MK:
+            off = put(li, k, shp(L.M, L.K), off, 256)
+        for k in KEYS_KN:
+            off = put(li, k, shp(L.K, L.N), off, 256)
+        for k in KEYS_MN:
+            off = put(li, k, shp(L.M, L.N), off, 256)
+    inputs_end = off
+    for li, L in enumerate(layers):
+        off = put(li, "alpha", shp(1), off, 16)
+        off = put(li, "chi", shp(L.N), off, 16)
+        off = put(li, "chi_hat", shp(L.M), off, 16)
+    keys_end = off = (off + 255) // 256 * 256
+    for li, L in enumerate(layers):
+        for k in OUT_MN:
+            off = put(li, k, shp(L.M, L.N), off, 256)
+        for k in OUT_M:
+            off = put(li, k, shp(L.M), off, 256)
+        off = put(li, "cs", shp(1), off, 256)
+    return plan, inputs_end, keys_end, off
+
+
 def request_bytes(layers, words: int) -> int:
-    e = 8 * words
-    tot = 0
-    for L in layers:
-        M, K, N = L.M, L.K, L.N
-        tot += e * (3 * M * K + 3 * K * N + 4 * M * N + N)      # inputs
-        tot += e * (2 * M * N + 2 * M + 1)                       # Z, mZ, mDc, Dc, cs
-    return tot
+    """Device bytes a request holds from admission to completion."""
+    return _carve(layers, words)[3]
+
+
+class Arena:
+    """First-fit allocator of byte ranges (256-byte granules) over one device
+    buffer, so that admitting and retiring requests never calls the CUDA
+    allocator.  Free ranges are kept sorted and coalesced."""
+
+    def __init__(self, torch, nbytes: int):
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.free = [(0, nbytes)]
+        self.used = 0
+
+    def alloc(self, n: int):
+        n = (n + 255) // 256 * 256
+        for i, (o, sz) in enumerate(self.free):
+            if sz >= n:
+                if sz == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (o + n, sz - n)
+                self.used += n
+                return o
+        return None
+
+    def release(self, off: int, n: int):
+        n = (n + 255) // 256 * 256
+        self.used -= n
+        import bisect
+        i = bisect.bisect_left(self.free, (off, 0))
+        self.free.insert(i, (off, n))
+        # coalesce with the neighbours
+        if i + 1 < len(self.free) and self.free[i][0] + self.free[i][1] == self.free[i + 1][0]:
+            self.free[i] = (self.free[i][0], self.free[i][1] + self.free[i + 1][1])
+            self.free.pop(i + 1)
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            self.free.pop(i)
+
+    def view(self, off: int, shape):
+        import torch
+        n = int(np.prod(shape))
+        return self.buf[off:off + 8 * n].view(torch.int64).view(shape)
 
 
 def make_requests(n: int, rate: float, seed: int, max_batch: int = 32, models=("resnet18", "vgg16"),
@@ -96,7 +175,8 @@ class Server:
     POOL_WORDS = 1 << 28          # 2 GiB of uniform words, larger than any one share tensor
 
     def __init__(self, ring=synth.Z128, party: int = 0, nparties: int = 2, mem_budget: int = 96 << 30,
-                 tag: str = "compact", max_inflight: int = 2, max_group: int = 512, pool_seed: int = 0x5EED):
+                 tag: str = "compact", max_inflight: int = 2, max_group: int = 512, pool_seed: int = 0x5EED,
+                 ws_bytes: int = 8 << 30):
         import torch
         if tag not in ("compact", "full"):
             raise ValueError("tag must be 'compact' or 'full'")
@@ -105,6 +185,12 @@ class Server:
         self.mem_budget, self.tag = mem_budget, tag
         self.max_inflight, self.max_group = max_inflight, max_group
         abi.load()
+        # every admitted request's shares live in this arena: its size is the
+        # memory budget that gates admission
+        self.arena = Arena(torch, mem_budget)
+        # one workspace for every tick, allocated up front: a tick whose layers
+        # need more runs as several grouped calls in turn
+        self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
         gen = torch.Generator(device="cuda")
         gen.manual_seed(pool_seed)
         self.pool = torch.randint(-(1 << 63), (1 << 63) - 1, (self.POOL_WORDS,), dtype=torch.int64,
@@ -112,62 +198,77 @@ class Server:
 
     # -- request shares -------------------------------------------------------
     def _materialise(self, req: Request, stream):
-        """Allocate the request's shares and fill them on `stream` with copies
-        of pool windows at offsets drawn from the request's seed (so the same
-        request always gets the same shares)."""
+        """Fill the request's arena range on `stream`: the inputs with copies
+        of pool windows (chunks of at most the pool's size, at offsets drawn
+        from the request's seed, so the same request always gets the same
+        shares) and the keys and combiners with one generator call; tensor
+        views are made when a layer runs."""
         torch = self.torch
         w = self.ring.words
-        shp = (lambda *d: d + ((2,) if w == 2 else ()))
+        base = req.region[0]
+        plan, inputs_end, keys_end, _ = _carve(req.layers, w)
+        rng = np.random.default_rng(req.seed)
         gen = torch.Generator(device="cuda")
         gen.manual_seed(req.seed)
-        rng = np.random.default_rng(req.seed)
-        bufs = []
-
-        def window(shape):
-            n = int(np.prod(shape))
-            off = int(rng.integers(0, self.POOL_WORDS - n + 1))
-            t = torch.empty(shape, dtype=torch.int64, device="cuda")
-            t.view(-1).copy_(self.pool[off:off + n], non_blocking=True)
-            return t
-
+        smax = (1 << min(self.ring.s, 63)) - 1      # keys and combiners: uniform in [0, 2^s)
         with torch.cuda.stream(stream):
-            for L in req.layers:
-                M, K, N = L.M, L.K, L.N
-                d = {}
-                for k in KEYS_MK:
-                    d[k] = window(shp(M, K))
-                for k in KEYS_KN:
-                    d[k] = window(shp(K, N))
-                for k in KEYS_MN:
-                    d[k] = window(shp(M, N))
-                # key share and combiners: uniform in [0, 2^s) (s <= 63 here: 2^63 - 1 bound)
-                smax = (1 << min(self.ring.s, 63)) - 1
-                d["alpha"] = torch.zeros(shp(1), dtype=torch.int64, device="cuda")
-                d["chi"] = torch.zeros(shp(N), dtype=torch.int64, device="cuda")
-                d["chi_hat"] = torch.zeros(shp(M), dtype=torch.int64, device="cuda")
-                for k, n_ in (("alpha", 1), ("chi", N), ("chi_hat", M)):
-                    v = torch.randint(0, smax, (n_,), dtype=torch.int64, device="cuda", generator=gen)
-                    if w == 2:
-                        d[k][:, 0] = v
-                    else:
-                        d[k].copy_(v)
-                d["Z"] = torch.empty(shp(M, N), dtype=torch.int64, device="cuda")
-                d["mZ"] = torch.empty(shp(M, N), dtype=torch.int64, device="cuda")
-                d["mDc"] = torch.empty(shp(M), dtype=torch.int64, device="cuda")
-                d["Dc"] = torch.empty(shp(M), dtype=torch.int64, device="cuda")
-                d["cs"] = torch.empty(shp(1), dtype=torch.int64, device="cuda")
-                d["layer"] = abi.make_layer(M, K, N, self.ring.k, self.ring.s, self.party, self.nparties)
-                bufs.append(d)
+            words = self.arena.buf[base:base + inputs_end].view(torch.int64)
+            pos = 0
+            while pos < words.numel():
+                n = min(self.POOL_WORDS, words.numel() - pos)
+                o = int(rng.integers(0, self.POOL_WORDS - n + 1))
+                words[pos:pos + n].copy_(self.pool[o:o + n], non_blocking=True)
+                pos += n
+            keys = self.arena.buf[base + inputs_end:base + keys_end].view(torch.int64)
+            if w == 2:
+                kv = keys.view(-1, 2)
+                kv[:, 0].copy_(torch.randint(0, smax, (kv.shape[0],), dtype=torch.int64, device="cuda",
+                                             generator=gen))
+                kv[:, 1].zero_()
+            else:
+                keys.copy_(torch.randint(0, smax, (keys.numel(),), dtype=torch.int64, device="cuda", generator=gen))
             ev = torch.cuda.Event()
             ev.record(stream)
-        req.bufs = bufs
+        req.plan = plan
+        req.bufs = [None] * len(req.layers)
         req.ready = ev
 
-    # -- one tick -------------------------------------------------------------
-    def _tick(self, group, ws):
+    def _bufs(self, req: Request, li: int) -> dict:
+        """The tensors of layer li of a request (views into its arena range)."""
+        d = req.bufs[li]
+        if d is None:
+            base = req.region[0]
+            d = {k: self.arena.view(base + off, shape) for k, (shape, off) in req.plan[li].items()}
+            L = req.layers[li]
+            d["layer"] = abi.make_layer(L.M, L.K, L.N, self.ring.k, self.ring.s, self.party, self.nparties)
+            d["ws_need"] = (self._layer_ws(d["layer"]) + 255) // 256 * 256
+            req.bufs[li] = d
+        return d
+
+    def _layer_ws(self, L) -> int:
+        which = (abi.MPC_WS_SHARE, abi.MPC_WS_TAG_COMPACT if self.tag == "compact" else abi.MPC_WS_TAG_FULL)
+        return max(abi.mpc_workspace_size_grouped([L], w) for w in which)
+
+    def _tick(self, group):
+        """The next layer of every request in `group`, in as few grouped calls
+        as the workspace allows."""
+        part, used = [], 0
+        for r in group:
+            need = self._bufs(r, r.nxt)["ws_need"]
+            if part and used + need > self.ws.numel():
+                self._tick_part(part, self.ws)
+                part, used = [], 0
+            part.append(r)
+            used += need
+        if part:
+            ws = self.ws if used <= self.ws.numel() else self.torch.empty(used, dtype=self.torch.uint8,
+                                                                          device="cuda")
+            self._tick_part(part, ws)
+
+    def _tick_part(self, group, ws):
         a = abi
-        layers = [r.bufs[r.nxt]["layer"] for r in group]
-        bufs = [r.bufs[r.nxt] for r in group]
+        bufs = [self._bufs(r, r.nxt) for r in group]
+        layers = [d["layer"] for d in bufs]
         a.mpc_linear_share_grouped(layers, [dict(E=d["E"], F=d["F"], A_i=d["A"], B_i=d["B"], C_i=d["C"],
                                                  Z_i=d["Z"]) for d in bufs], ws=ws)
         tp = [dict(alpha_i=d["alpha"], E=d["E"], F=d["F"], mA_i=d["mA"], mB_i=d["mB"], mC_i=d["mC"],
@@ -181,30 +282,27 @@ class Server:
         else:
             a.mpc_linear_tag_grouped(layers, a.MPC_TAG_FULL, tp, ws=ws)
 
-    def _workspace(self, group):
-        torch = self.torch
-        layers = [r.bufs[r.nxt]["layer"] for r in group]
-        which = (abi.MPC_WS_SHARE, abi.MPC_WS_TAG_COMPACT if self.tag == "compact" else abi.MPC_WS_TAG_FULL)
-        need = max(abi.mpc_workspace_size_grouped(layers, w) for w in which)
-        check = max(abi.mpc_workspace_size(L, abi.MPC_WS_CHECK_COMPACT) for L in layers)
-        need = max(need, check, 256)
-        if self._ws is None or self._ws.numel() < need:
-            self._ws = torch.empty(int(need * 1.25), dtype=torch.uint8, device="cuda")
-        return self._ws
-
     # -- the loop -------------------------------------------------------------
-    def run(self, requests, keep_outputs: bool = False) -> dict:
+    def run(self, requests, keep_outputs: bool = False, tag: str = None) -> dict:
+        """Serve `requests` to completion; `tag` overrides the server's tag path
+        for this run."""
+        if tag is not None:
+            if tag not in ("compact", "full"):
+                raise ValueError("tag must be 'compact' or 'full'")
+            saved, self.tag = self.tag, tag
+            try:
+                return self.run(requests, keep_outputs)
+            finally:
+                self.tag = saved
         torch = self.torch
         st = torch.cuda.current_stream()
         side = torch.cuda.Stream()
-        self._ws = None
         words = self.ring.words
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         waiting = collections.deque()
         active = []
         inflight = collections.deque()      # (event, finished requests)
         tick_ms = []
-        mem_used = 0
         peak_mem = 0
         start = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -213,17 +311,26 @@ class Server:
         prev_ev = start
         finished_all = []
 
+        kept = []
+
         def retire(block: bool):
-            nonlocal mem_used
             while inflight and (block or inflight[0][0].query()):
                 ev, fin = inflight.popleft()
                 ev.synchronize()
                 t = start.elapsed_time(ev)
                 for r in fin:
                     r.done_ms = t
-                    mem_used -= request_bytes(r.layers, words)
-                    if not keep_outputs:
+                    if keep_outputs:
+                        # outputs stay readable: copy them out of the arena before
+                        # the range is handed to the next request (whose shares
+                        # are written on the side stream)
+                        r.bufs = [{k: (v.clone() if hasattr(v, "clone") else v)
+                                   for k, v in self._bufs(r, li).items()} for li in range(len(r.layers))]
+                        st.synchronize()
+                    else:
                         r.bufs = None
+                    self.arena.release(*r.region)
+                    r.region = None
                     finished_all.append(r)
                 block = False
 
@@ -233,11 +340,15 @@ class Server:
                 waiting.append(pending.popleft())
             while waiting:
                 need = request_bytes(waiting[0].layers, words)
-                if mem_used + need > self.mem_budget and (active or inflight):
+                off = self.arena.alloc(need)
+                if off is None:
+                    if not (active or inflight):
+                        raise MemoryError(f"request {waiting[0].rid} needs {need} bytes, more than the "
+                                          f"{self.mem_budget}-byte budget")
                     break
                 r = waiting.popleft()
-                mem_used += need
-                peak_mem = max(peak_mem, mem_used)
+                r.region = (off, need)
+                peak_mem = max(peak_mem, self.arena.used)
                 r.admit_s = time.perf_counter() - t0
                 self._materialise(r, side)
                 active.append(r)
@@ -248,7 +359,7 @@ class Server:
                     if r.ready is not None:
                         st.wait_event(r.ready)
                         r.ready = None
-                self._tick(group, self._workspace(group))
+                self._tick(group)
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(st)
                 tick_ms.append((prev_ev, ev))
