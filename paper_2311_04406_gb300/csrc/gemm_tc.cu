@@ -59,14 +59,21 @@ __device__ unsigned int g_tc_timeout = 0;
 namespace {
 
 // ---------------------------------------------------------------------------
-// configuration per ring width
+// configuration per ring width (pipeline depths: defaults measured best)
+
+#ifndef MPCL_TC_STAGES_W1
+#define MPCL_TC_STAGES_W1 4
+#endif
+#ifndef MPCL_TC_RAW
+#define MPCL_TC_RAW 4
+#endif
 
 template <int W> struct Cfg;
 template <> struct Cfg<1> {
     static constexpr int NDIG = 8;     // digits per element
     static constexpr int ND = 32;      // output columns per tile
     static constexpr int KD = 8;       // stages per drain interval (Kd = 128)
-    static constexpr int STAGES = 4;   // operand stages in shared memory
+    static constexpr int STAGES = MPCL_TC_STAGES_W1;   // operand stages in shared memory
 };
 template <> struct Cfg<2> {
     static constexpr int NDIG = 16;
@@ -78,7 +85,7 @@ template <> struct Cfg<2> {
 constexpr int BM = 128;                  // rows per tile (TMEM lanes)
 constexpr int KS = 16;                   // K per stage (one MMA K step)
 constexpr int NSTACK = 256;              // rows of the stacked B operand (NDIG * ND)
-constexpr int RAW = 8;                   // raw R tiles in flight
+constexpr int RAW = MPCL_TC_RAW;         // raw R tiles in flight
 constexpr uint32_t A_PLANE_BYTES = BM * KS * 2;            // 4 KB
 constexpr uint32_t B_STAGE_BYTES = NSTACK * KS * 2;        // 8 KB
 constexpr uint32_t RAW_BYTES = 4096;                       // 16 K x (ND * W) words
@@ -91,17 +98,24 @@ constexpr int W_APROD = 0, W_CONV0 = 1, W_MMA = 5, W_BPROD = 10;   // warps 6-9 
 constexpr int NCONV = 128;               // converter threads
 constexpr int NDRAIN = 128;              // drain threads
 constexpr long long WAIT_LIMIT = 4000000000LL;   // clock cycles (about 2 s)
-constexpr int NBARS = 2 * 4 + 2 * RAW + 2 + 2 + 1;
+constexpr int MAX_STAGES = 8;
+constexpr int NBARS = 2 * MAX_STAGES + 2 * RAW + 2 + 2 + 1;
 
 template <int W> struct Layout {
     static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE_BYTES;
     static constexpr uint32_t OFF_B = Cfg<W>::STAGES * A_STAGE;
     static constexpr uint32_t OFF_RAW = OFF_B + Cfg<W>::STAGES * B_STAGE_BYTES;
-    static constexpr uint32_t OFF_BAR = OFF_RAW + RAW * RAW_BYTES;
+    // epilogue staging: per drain warp 32 rows x (ND + 1) sums (one element
+    // of padding per row keeps the row-wise writes and column-wise reads free
+    // of bank conflicts)
+    static constexpr uint32_t OFF_STG = OFF_RAW + RAW * RAW_BYTES;
+    static constexpr uint32_t STG_BYTES = 4 * 32 * (Cfg<W>::ND + 1) * 8 * W;
+    static constexpr uint32_t OFF_BAR = OFF_STG + STG_BYTES;
     static constexpr uint32_t SMEM = OFF_BAR + NBARS * 8 + 16;
 };
 static_assert(Cfg<1>::NDIG * Cfg<1>::ND == NSTACK && Cfg<2>::NDIG * Cfg<2>::ND == NSTACK, "stack");
 static_assert(Layout<1>::SMEM <= 227 * 1024 && Layout<2>::SMEM <= 227 * 1024, "smem");
+static_assert(Cfg<1>::STAGES <= MAX_STAGES && Cfg<2>::STAGES <= MAX_STAGES, "barrier slots");
 
 constexpr unsigned long long DIGIT_BIAS = 0x8080808080808080ULL;
 constexpr uint32_t F16_1152X2 = 0x64806480u;   // fp16 (1152, 1152)
@@ -472,10 +486,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     uint8_t* sA = smem;
     uint8_t* sB = smem + Layout<W>::OFF_B;
     uint8_t* sRaw = smem + Layout<W>::OFF_RAW;
+    uint8_t* sStg = smem + Layout<W>::OFF_STG;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Layout<W>::OFF_BAR);
     uint64_t* full = bars;
-    uint64_t* empty = full + 4;
-    uint64_t* rawFull = empty + 4;
+    uint64_t* empty = full + MAX_STAGES;
+    uint64_t* rawFull = empty + MAX_STAGES;
     uint64_t* rawEmpty = rawFull + RAW;
     uint64_t* accFull = rawEmpty + RAW;
     uint64_t* accEmpty = accFull + 2;
@@ -687,7 +702,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     } else {
         // drain warps: TMEM lane quadrant = warp % 4
         const int quad = warp & 3;
-        const int row = quad * 32 + lane;
         constexpr int DPL = 32 / ND;   // diagonals per 32-column TMEM load
         Sum sum[ND];
 #pragma unroll
@@ -729,24 +743,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 // pieces of a split tile are added to Z (set to C by the prologue)
                 const bool whole = seg_ii == 0 && x.ii == p.I - 1;
                 seg_ii = -1;
-                const int64_t m = x.mt * BM + row;
-                const int64_t n0 = x.nt * ND;
-                if (m < p.M) {
-                    u64* zrow = p.Z + (m * p.N + n0) * W;
-                    const u64* crow = p.C ? p.C + (m * p.N + n0) * W : nullptr;
-                    const int64_t rem = p.N - n0;
-                    const int ncols = rem < ND ? (int)rem : ND;
-                    if (whole) {
+                // The warp's 32 rows x ND sums go through shared memory so that
+                // the global accesses run along rows: lane = column (W = 1), or
+                // two rows of 16 columns per instruction (W = 2).
+                Sum* stg = reinterpret_cast<Sum*>(sStg) + quad * 32 * (ND + 1);
+                __syncwarp();
 #pragma unroll
-                        for (int c = 0; c < ND; ++c)
-                            if (c < ncols) st_elem<W>(zrow, c, (crow ? ldg_elem<W>(crow, c) : (Sum)0) + sum[c]);
-                    } else {
+                for (int c = 0; c < ND; ++c) stg[lane * (ND + 1) + c] = sum[c];
+                __syncwarp();
+                constexpr int RPI = 32 / ND;     // rows per instruction
+                constexpr int NIT = 32 / RPI;
+                const int rr = lane / ND, cc = lane % ND;
+                const int64_t n = x.nt * ND + cc;
+                const int64_t mb = x.mt * BM + quad * 32;
+                // all addend loads first (independent, in flight together),
+                // then the stores or atomic adds
+                Sum cv[NIT];
 #pragma unroll
-                        for (int c = 0; c < ND; ++c) {
-                            if (c < ncols) {
-                                if constexpr (W == 1) red_add_u64(zrow + c, sum[c]);
-                                else atomic_add_u128(zrow + 2 * c, sum[c]);
-                            }
+                for (int i = 0; i < NIT; ++i) {
+                    const int64_t m = mb + i * RPI + rr;
+                    cv[i] = (whole && p.C && m < p.M && n < p.N) ? ldg_elem<W>(p.C, m * p.N + n) : (Sum)0;
+                }
+#pragma unroll
+                for (int i = 0; i < NIT; ++i) {
+                    const int r = i * RPI + rr;
+                    const int64_t m = mb + r;
+                    if (m < p.M && n < p.N) {
+                        const Sum v = stg[r * (ND + 1) + cc];
+                        const int64_t e = m * p.N + n;
+                        if (whole) {
+                            st_elem<W>(p.Z, e, cv[i] + v);
+                        } else {
+                            if constexpr (W == 1) red_add_u64(p.Z + e, v);
+                            else atomic_add_u128(p.Z + 2 * e, v);
                         }
                     }
                 }
@@ -760,6 +789,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     ptx::tc_fence_after();
     if (warp == W_APROD) ptx::tmem_dealloc(tmem, TMEM_COLS);
 }
+static_assert(Layout<1>::SMEM <= 227 * 1024 && Layout<2>::SMEM <= 227 * 1024, "smem with staging");
 
 // ---------------------------------------------------------------------------
 // host side
