@@ -47,6 +47,7 @@ WORKLOADS = {
     "vgg16": ("vgg16_32x32x3_b{b}", lambda b: synth.vgg16_layers(b)),
     "resnet18": ("resnet18_32x32x3_b{b}", lambda b: synth.resnet18_layers(b)),
     "transformer": ("transformer_h1024_t2048", lambda b: synth.transformer_layers()),
+    "transformer_block": ("transformer_block_h1024_a16_t2048", lambda b: synth.transformer_block()),
     "uneven": ("uneven256_seeded", lambda b: synth.uneven_layers(256)),
     "serve": ("serve_resnet18_vgg16_b1-32_z128_poisson", None),
 }

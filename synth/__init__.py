@@ -204,6 +204,21 @@ def transformer_layers(rows: int = 2048, hidden: int = 1024) -> list[Layer]:
             Layer("ffn_down", rows, 4 * hidden, hidden)]
 
 
+def transformer_block(rows: int = 2048, hidden: int = 1024, heads: int = 16) -> list[Layer]:
+    """One encoder block at H = 1024, A = 16 heads, T1 = 2048 rows (§4.1):
+    the Q, K, V and output projections, the two FFN products, and per head the
+    attention-score product Q_h K_h^T (rows x d x rows) and the value product
+    S_h V_h (rows x rows x d), d = H / A.  Softmax and the other nonlinear
+    steps are not linear-layer work and are skipped."""
+    d = hidden // heads
+    out = [Layer(n, rows, hidden, hidden) for n in ("q_proj", "k_proj", "v_proj", "o_proj")]
+    out += [Layer("ffn_up", rows, hidden, 4 * hidden), Layer("ffn_down", rows, 4 * hidden, hidden)]
+    for h in range(heads):
+        out.append(Layer(f"scores_h{h}", rows, d, rows))
+        out.append(Layer(f"values_h{h}", rows, rows, d))
+    return out
+
+
 def uneven_layers(count: int = 256, seed: int = 0xC0FFEE03) -> list[Layer]:
     """`count` layers with M log-uniform in [1, 4096] and K, N drawn from
     {64, 128, ..., 4096} with a uniform exponent."""
