@@ -778,7 +778,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
         a.record(st)
-        pipelined = not args.grouped and not run.links
+        pipelined = not args.grouped
         for _ in range(e2e_steps):
             if pipelined:
                 run.e2e_step()
