@@ -337,6 +337,16 @@ int mpc_launch_count(const mpc_layer *layer, int which);
  * MPC_E_CUDA if the flag could not be read.  Uses the current device. */
 int mpc_device_status(void);
 
+/* Self-test of the bounded device-side wait (no counterpart in the paper):
+ * one thread waits on a barrier that nothing arrives at, for at most
+ * limit_cycles clock cycles (1e3 .. 1e10; about 1e9 per 0.5 s at 2 GHz), then
+ * gives up and records the timeout as the GEMM's roles do.  Synchronous on
+ * `stream`.  Returns MPC_E_TIMEOUT when the wait gave up (the expected
+ * outcome; the flag that mpc_device_status reads is then set), MPC_OK if it did
+ * not, MPC_E_SHAPE for a limit out of range, MPC_E_CUDA on a CUDA error.  The
+ * context stays usable afterwards. */
+int mpc_selftest_wait(long long limit_cycles, void *stream);
+
 /* Static string for a status code. */
 const char *mpc_status_str(int status);
 

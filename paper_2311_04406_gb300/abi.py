@@ -33,7 +33,7 @@ ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_wor
                  "mpc_optmac_trunc", "mpc_batchrec_mask", "mpc_transpose",
                  "mpc_linear_share_grouped", "mpc_linear_tag_grouped", "mpc_workspace_size_grouped",
                  "mpc_launch_count_grouped", "mpc_autotune", "mpc_autotune_set", "mpc_autotune_choice",
-                 "mpc_autotune_save", "mpc_autotune_load", "mpc_autotune_clear")
+                 "mpc_autotune_save", "mpc_autotune_load", "mpc_autotune_clear", "mpc_selftest_wait")
 (MPC_E_NULL, MPC_E_SHAPE, MPC_E_RING, MPC_E_ALIGN, MPC_E_WORKSPACE, MPC_E_CUDA, MPC_E_MODE, MPC_E_PARTY,
  MPC_E_TIMEOUT, MPC_E_SCRATCH_LIMIT, MPC_E_IO) = range(-1, -12, -1)
 MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -134,6 +134,8 @@ def load(build_if_missing: bool = False):
         lib.mpc_autotune_clear.restype = ctypes.c_int
         lib.mpc_launch_count.argtypes = [L, ctypes.c_int]
         lib.mpc_launch_count.restype = ctypes.c_int
+        lib.mpc_selftest_wait.argtypes = [ctypes.c_longlong, P]
+        lib.mpc_selftest_wait.restype = ctypes.c_int
         lib.mpc_device_status.argtypes = []
         lib.mpc_device_status.restype = ctypes.c_int
         lib.mpc_gemm_path.argtypes = [L]
@@ -187,6 +189,11 @@ def mpc_gemm_path(layer: mpc_layer) -> int:
 
 def mpc_launch_count(layer: mpc_layer, which: int) -> int:
     return int(load().mpc_launch_count(ctypes.byref(layer), int(which)))
+
+
+def mpc_selftest_wait(limit_cycles: int, stream=None) -> int:
+    """Status of the bounded-wait self-test: MPC_E_TIMEOUT when the wait gave up as designed."""
+    return int(load().mpc_selftest_wait(int(limit_cycles), _stream(stream)))
 
 
 def mpc_device_status() -> int:

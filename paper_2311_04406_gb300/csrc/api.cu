@@ -104,6 +104,13 @@ int mpc_launch_count(const mpc_layer* L, int which) {
     }
 }
 
+int mpc_selftest_wait(long long limit_cycles, void* stream) {
+    if (limit_cycles < 1000 || limit_cycles > 10000000000LL) return MPC_E_SHAPE;
+    const int r = mpcl::wait_selftest(limit_cycles, (cudaStream_t)stream);
+    if (r < 0) return MPC_E_CUDA;
+    return r == 1 ? MPC_E_TIMEOUT : MPC_OK;
+}
+
 int mpc_device_status(void) {
     bool set = false;
     if (mpcl::tc_timeout_flag(&set) != 0) return MPC_E_CUDA;

@@ -1009,6 +1009,47 @@ cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap,
 
 int gemm_tc_grouped_launches(int n) { return n <= 0 ? 0 : 2 * ((n + GMAX - 1) / GMAX); }
 
+// ---------------------------------------------------------------------------
+// self-test of the bounded wait: one thread waits on a barrier that nothing
+// arrives at; the wait must give up after `limit` cycles and record the
+// timeout exactly as the GEMM's roles do.
+
+namespace {
+__device__ int g_selftest_gave_up = 0;
+
+__global__ void wait_selftest_kernel(long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        abort_flag = 0;
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool ok = ptx::mbar_wait(&bar, 0, &abort_flag, limit);
+        if (!ok) {
+            record_timeout(&abort_flag);
+            g_selftest_gave_up = 1;
+        }
+    }
+}
+}  // namespace
+
+int wait_selftest(long long limit, cudaStream_t st) {
+    int zero = 0, v = 0;
+    if (cudaMemcpyToSymbolAsync(g_selftest_gave_up, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return -1;
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbolAsync(&v, g_selftest_gave_up, sizeof(v), 0, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return -1;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    return v;
+}
+
 // Reads and clears the device flag that a bounded wait sets when it gives up.
 int tc_timeout_flag(bool* set) {
     unsigned int v = 0;

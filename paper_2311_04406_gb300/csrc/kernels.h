@@ -53,6 +53,9 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStr
 // (gemm_tc_workspace bytes, 256-byte aligned)
 cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st);
 int gemm_tc_grouped_launches(int n);
+// 1 when a bounded wait on a barrier nothing arrives at gave up (as it must),
+// 0 if it did not, -1 on a CUDA error; synchronous
+int wait_selftest(long long limit, cudaStream_t st);
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half = 0);
 bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words);   // heuristic preference
 bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words);   // the kernel can run the shape

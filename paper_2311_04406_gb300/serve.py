@@ -113,13 +113,12 @@ def request_bytes(layers, words: int) -> int:
     return _carve(layers, words)[3]
 
 
-class Arena:
-    """First-fit allocator of byte ranges (256-byte granules) over one device
-    buffer, so that admitting and retiring requests never calls the CUDA
-    allocator.  Free ranges are kept sorted and coalesced."""
+class RangeAllocator:
+    """First-fit allocator of byte ranges (256-byte granules) in [0, nbytes).
+    Free ranges are kept sorted and coalesced."""
 
-    def __init__(self, torch, nbytes: int):
-        self.buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    def __init__(self, nbytes: int):
+        self.size = nbytes
         self.free = [(0, nbytes)]
         self.used = 0
 
@@ -148,6 +147,16 @@ class Arena:
         if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:
             self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
             self.free.pop(i)
+
+
+
+class Arena(RangeAllocator):
+    """A RangeAllocator over one device buffer, so that admitting and retiring
+    requests never calls the CUDA allocator."""
+
+    def __init__(self, torch, nbytes: int):
+        super().__init__(nbytes)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
 
     def view(self, off: int, shape):
         import torch
