@@ -274,6 +274,34 @@ int mpc_batchrec_mask(const mpc_ring *ring, int64_t rows, int64_t cols,
                       uint64_t *W_i, uint64_t *mW_i, void *stream);
 
 /*
+ * Linear combination of ring arrays, out = sum_j coef[j] * in[j] mod 2^(k+s),
+ * elementwise over n elements, 1 <= count <= 16, coef[] small signed integers
+ * (host array), in[] a host array of device pointers.  Authenticated shares are
+ * linear under public constants (§2.4), so this is the local part of an
+ * opening when several parties are simulated on one device (E = sum_i
+ * (X_i - A_i), Fig. Pi_MatMul step 1; D~ = sum_i (R_i - Z_i), Fig. Pi_OptMAC)
+ * and of the mask arithmetic around it.  out may alias an input (each element
+ * is read before it is written by the same thread).  No workspace.
+ */
+int mpc_lincomb(const mpc_ring *ring, int64_t n, int count, const int64_t *coef,
+                const uint64_t *const *in, uint64_t *out, void *stream);
+
+/*
+ * im2col view of a convolution (§2.6): for a batch of `channels` x height x
+ * width images in NCHW layout and an f x f filter with zero padding `pad`
+ * (< f) and stride `stride`, out is the (batch H' W') x (channels f f) matrix
+ * with H' = (height - f + 2 pad) / stride + 1 (floor; the textbook size, see
+ * the "+1" reading of §2.6), W' likewise: row (b, oy, ox), column (c, ky, kx)
+ * holds in[b][c][oy stride + ky - pad][ox stride + kx - pad], or 0 in the
+ * padding.  The convolution with a (channels f f) x out_channels weight is
+ * then the ring GEMM of mpc_linear_share.  Local and linear: each party applies
+ * it to its shares and tags.  MPC_E_SHAPE for f < 1, pad >= f, stride < 1 or
+ * an image smaller than the filter.  No workspace.
+ */
+int mpc_im2col(const mpc_ring *ring, int64_t batch, int64_t channels, int64_t height, int64_t width,
+               int f, int pad, int stride, const uint64_t *in, uint64_t *out, void *stream);
+
+/*
  * Local transpose, out (cols x rows) = in (rows x cols)^T.  Training's
  * backward linear layers (§4: grad X = grad Z . W^T, grad W = X^T . grad Z) are
  * the same per-party Beaver products on transposed operands; shares and tags

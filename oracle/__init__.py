@@ -76,6 +76,8 @@ def _load():
                 "orc_compact_tag_trunc": (_int, [_int, _i64, _i64, _i64] + [_u64p] * 12),
                 "orc_check_compact_literal": (_int, [_int, _int, _i64] + [_u64p] * 5),
                 "orc_check_batchrec": (None, [_int, _i64, _i64] + [_u64p] * 5),
+                "orc_im2col": (None, [_int, _i64, _i64, _i64, _i64, _int, _int, _int, _u64p, _u64p]),
+                "orc_set_threads": (_int, [_int]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -334,3 +336,14 @@ def chi_seeded(bits, s, seed, shape):
 def set_threads(n: int) -> int:
     """OpenMP threads of the oracle's loops; returns the previous maximum."""
     return int(_load().orc_set_threads(int(n)))
+
+
+def im2col(x: np.ndarray, f: int, pad: int, stride: int, bits: int) -> np.ndarray:
+    """im2col view of NCHW ring-element images x for an f x f convolution (§2.6)."""
+    w = words(bits)
+    B, C, H, W = x.shape[:4]
+    Ho, Wo = (H - f + 2 * pad) // stride + 1, (W - f + 2 * pad) // stride + 1
+    out = _new(bits, B * Ho * Wo, C * f * f)
+    xc = np.ascontiguousarray(x)
+    _load().orc_im2col(w, B, C, H, W, f, pad, stride, _p(xc), _p(out))
+    return out

@@ -401,3 +401,31 @@ int orc_set_threads(int n) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* im2col view of a convolution (§2.6): row (b, oy, ox), column (c, ky, kx)  */
+/* of the output is in[b][c][oy*stride + ky - pad][ox*stride + kx - pad]    */
+/* (NCHW input), or 0 in the zero padding.  Output rows B*Ho*Wo, columns     */
+/* C*f*f, with Ho = (H - f + 2 pad) / stride + 1 and Wo likewise.            */
+void orc_im2col(int words, int64_t B, int64_t C, int64_t H, int64_t W, int f, int pad, int stride,
+                const uint64_t *in, uint64_t *out) {
+    const int64_t Ho = (H - f + 2 * pad) / stride + 1, Wo = (W - f + 2 * pad) / stride + 1;
+    const int64_t cols = C * f * f;
+    for (int64_t b = 0; b < B; ++b)
+        for (int64_t oy = 0; oy < Ho; ++oy)
+            for (int64_t ox = 0; ox < Wo; ++ox) {
+                const int64_t row = (b * Ho + oy) * Wo + ox;
+                for (int64_t c = 0; c < C; ++c)
+                    for (int ky = 0; ky < f; ++ky)
+                        for (int kx = 0; kx < f; ++kx) {
+                            const int64_t col = (c * f + ky) * f + kx;
+                            const int64_t y = oy * stride + ky - pad, x = ox * stride + kx - pad;
+                            for (int h = 0; h < words; ++h) {
+                                uint64_t v = 0;
+                                if (y >= 0 && y < H && x >= 0 && x < W)
+                                    v = in[(((b * C + c) * H + y) * W + x) * words + h];
+                                out[(row * cols + col) * words + h] = v;
+                            }
+                        }
+            }
+}

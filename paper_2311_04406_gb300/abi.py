@@ -33,7 +33,7 @@ ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_wor
                  "mpc_optmac_trunc", "mpc_batchrec_mask", "mpc_transpose",
                  "mpc_linear_share_grouped", "mpc_linear_tag_grouped", "mpc_workspace_size_grouped",
                  "mpc_launch_count_grouped", "mpc_autotune", "mpc_autotune_set", "mpc_autotune_choice",
-                 "mpc_autotune_save", "mpc_autotune_load", "mpc_autotune_clear", "mpc_selftest_wait")
+                 "mpc_autotune_save", "mpc_autotune_load", "mpc_autotune_clear", "mpc_selftest_wait", "mpc_lincomb", "mpc_im2col")
 (MPC_E_NULL, MPC_E_SHAPE, MPC_E_RING, MPC_E_ALIGN, MPC_E_WORKSPACE, MPC_E_CUDA, MPC_E_MODE, MPC_E_PARTY,
  MPC_E_TIMEOUT, MPC_E_SCRATCH_LIMIT, MPC_E_IO) = range(-1, -12, -1)
 MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -107,6 +107,11 @@ def load(build_if_missing: bool = False):
         lib.mpc_batchrec_mask.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int64] + \
             [P] * 8 + [P]
         lib.mpc_batchrec_mask.restype = ctypes.c_int
+        lib.mpc_lincomb.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_void_p), P, P]
+        lib.mpc_lincomb.restype = ctypes.c_int
+        lib.mpc_im2col.argtypes = [ctypes.POINTER(mpc_ring)] + [ctypes.c_int64] * 4 + [ctypes.c_int] * 3 + [P, P, P]
+        lib.mpc_im2col.restype = ctypes.c_int
         lib.mpc_transpose.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int64, P, P, P]
         lib.mpc_transpose.restype = ctypes.c_int
         lib.mpc_linear_share_grouped.argtypes = [L, ctypes.c_int, ctypes.POINTER(mpc_share_ptrs), P,
@@ -287,6 +292,25 @@ def mpc_batchrec_mask(k, s, rows, cols, X_i, A_i, R_i, mX_i, mA_i, mR_i, W_i, mW
         ctypes.byref(ring), int(rows), int(cols), _ptr(X_i), _ptr(A_i), _ptr(R_i), _ptr(mX_i),
         _ptr(mA_i), _ptr(mR_i), _ptr(W_i), _ptr(mW_i), _stream(stream)))
     return W_i, mW_i
+
+
+def mpc_lincomb(k, s, coefs, ins, out, stream=None):
+    """out = sum_j coefs[j] * ins[j] (elementwise, mod 2^(k+s)); ins are tensors of out's shape."""
+    ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
+    n = out.numel() // ring.words if out is not None and hasattr(out, "numel") else 0
+    c = (ctypes.c_int64 * len(coefs))(*[int(x) for x in coefs])
+    p = (ctypes.c_void_p * len(ins))(*[_ptr(t) for t in ins])
+    _check("mpc_lincomb", load().mpc_lincomb(ctypes.byref(ring), int(n), len(coefs), c, p, _ptr(out),
+                                             _stream(stream)))
+    return out
+
+
+def mpc_im2col(k, s, batch, channels, height, width, f, pad, stride, src, dst, stream=None):
+    """dst = the im2col matrix of NCHW images src for an f x f filter (zero padding, stride)."""
+    ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
+    _check("mpc_im2col", load().mpc_im2col(ctypes.byref(ring), int(batch), int(channels), int(height), int(width),
+                                           int(f), int(pad), int(stride), _ptr(src), _ptr(dst), _stream(stream)))
+    return dst
 
 
 def mpc_transpose(k, s, rows, cols, src, dst, stream=None):

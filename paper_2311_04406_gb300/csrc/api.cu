@@ -170,6 +170,35 @@ int mpc_linear_share(const mpc_layer* L, const uint64_t* E, const uint64_t* F,
     return run_gemm(g, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+int mpc_lincomb(const mpc_ring* ring, int64_t n, int count, const int64_t* coef, const uint64_t* const* in,
+                uint64_t* out, void* stream) {
+    if (!ring || !coef || !in) return MPC_E_NULL;
+    if (!ring_ok(*ring)) return MPC_E_RING;
+    if (n < 0 || n > kMaxElems || count < 1 || count > mpcl::LINCOMB_MAX) return MPC_E_SHAPE;
+    for (int j = 0; j < count; ++j) CHK(check_ptr(in[j], n));
+    CHK(check_ptr(out, n));
+    return cuda_status(mpcl::launch_lincomb(n, ring->words, count, coef, (const u64* const*)in, (u64*)out,
+                                            (cudaStream_t)stream));
+}
+
+int mpc_im2col(const mpc_ring* ring, int64_t batch, int64_t channels, int64_t height, int64_t width, int f,
+               int pad, int stride, const uint64_t* in, uint64_t* out, void* stream) {
+    if (!ring) return MPC_E_NULL;
+    if (!ring_ok(*ring)) return MPC_E_RING;
+    if (batch < 0 || channels < 0 || height < 0 || width < 0 || f < 1 || pad < 0 || stride < 1 ||
+        f > 64 || pad >= f || height > kMaxDim || width > kMaxDim || channels > kMaxDim || batch > kMaxDim)
+        return MPC_E_SHAPE;
+    if (height + 2 * pad < f || width + 2 * pad < f) return MPC_E_SHAPE;
+    const int64_t Ho = (height - f + 2 * pad) / stride + 1, Wo = (width - f + 2 * pad) / stride + 1;
+    const int64_t nin = batch * channels * height * width;
+    const int64_t rows = batch * Ho * Wo, cols = channels * f * f;
+    if (nin > kMaxElems || rows > kMaxDim || cols > kMaxDim || rows * cols > kMaxElems) return MPC_E_SHAPE;
+    CHK(check_ptr(in, nin));
+    CHK(check_ptr(out, rows * cols));
+    return cuda_status(mpcl::launch_im2col(batch, channels, height, width, f, pad, stride, ring->words,
+                                           (const u64*)in, (u64*)out, (cudaStream_t)stream));
+}
+
 int mpc_transpose(const mpc_ring* ring, int64_t rows, int64_t cols, const uint64_t* in, uint64_t* out,
                   void* stream) {
     if (!ring) return MPC_E_NULL;

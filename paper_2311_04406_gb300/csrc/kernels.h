@@ -93,6 +93,16 @@ cudaError_t launch_optmac_trunc(int64_t MN, int words, int k, int f, int party0,
                                 const u64* Rf, const u64* mRf, const u64* Dt, const u64* P, u64* Zf,
                                 u64* mZf, cudaStream_t st);
 
+// out = sum_j coef[j] in[j] (elementwise, count <= LINCOMB_MAX); out may be one
+// of the inputs (each element is read before it is written, by one thread)
+constexpr int LINCOMB_MAX = 16;
+cudaError_t launch_lincomb(int64_t n, int words, int count, const int64_t* coef, const u64* const* in, u64* out,
+                           cudaStream_t st);
+
+// im2col of NCHW ring-element images for an f x f convolution (stride, zero padding)
+cudaError_t launch_im2col(int64_t B, int64_t C, int64_t H, int64_t W, int f, int pad, int stride, int words,
+                          const u64* in, u64* out, cudaStream_t st);
+
 // local transpose of a ring matrix (training's backward layers)
 cudaError_t launch_transpose(int64_t rows, int64_t cols, int words, const u64* in, u64* out,
                              cudaStream_t st);

@@ -12,10 +12,11 @@ completion.  The scheduler
     out of a seeded pool of uniform words standing in for the offline phase's
     output), so that input preparation overlaps the layers already running;
   * runs one "tick" at a time: the next linear layer of every admitted,
-    ready request, as ONE grouped share call, ONE grouped tag call and the
-    per-layer checks (continuous batching: a request joins at the next tick
-    after admission and leaves after its last layer, whatever the others are
-    doing);
+    ready request, as ONE grouped share call, the opening of D~ on the device
+    (this party's R - Z plus the other parties' part, a resident input standing
+    in for the network exchange), ONE grouped tag call and the per-layer
+    checks (continuous batching: a request joins at the next tick after
+    admission and leaves after its last layer, whatever the others are doing);
   * keeps at most `max_inflight` ticks queued on the device, and releases a
     finished request's memory once its last tick has completed.
 
@@ -43,7 +44,7 @@ from . import abi
 MODELS = {"resnet18": synth.resnet18_layers, "vgg16": synth.vgg16_layers}
 KEYS_MK = ("E", "A", "mA")
 KEYS_KN = ("F", "B", "mB")
-KEYS_MN = ("C", "mC", "mR", "Dt")
+KEYS_MN = ("C", "mC", "R", "mR", "Drest")     # Drest: the other parties' part of the opening of D
 
 
 @dataclass
@@ -68,7 +69,7 @@ class Request:
         return sum(2 * L.M * L.K * L.N for L in self.layers)
 
 
-OUT_MN = ("Z", "mZ")
+OUT_MN = ("Z", "mZ", "Dt")
 OUT_M = ("mDc", "Dc")
 
 
@@ -280,6 +281,12 @@ class Server:
         layers = [d["layer"] for d in bufs]
         a.mpc_linear_share_grouped(layers, [dict(E=d["E"], F=d["F"], A_i=d["A"], B_i=d["B"], C_i=d["C"],
                                                  Z_i=d["Z"]) for d in bufs], ws=ws)
+        if self.tag == "compact":
+            # the opening between the share and the tag (Fig. Pi_OptMAC): this
+            # party's [D]_i = [R]_i - [Z]_i plus the other parties' part
+            k, s = self.ring.k, self.ring.s
+            for d in bufs:
+                a.mpc_lincomb(k, s, [1, -1, 1], [d["R"], d["Z"], d["Drest"]], d["Dt"])
         tp = [dict(alpha_i=d["alpha"], E=d["E"], F=d["F"], mA_i=d["mA"], mB_i=d["mB"], mC_i=d["mC"],
                    mR_i=d["mR"], Dtilde=d["Dt"], chi=d["chi"], mZ_i=d["mZ"], mDc_i=d["mDc"], Dc=d["Dc"])
               for d in bufs]

@@ -20,7 +20,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "mpclinear.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mpc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mpc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_abi():
@@ -177,3 +177,30 @@ def test_launch_table_host_logic(lib, tmp_path):
     assert abi.mpc_autotune([]) == 0
     abi.mpc_autotune_clear()
     assert abi.mpc_gemm_path(big) == 1
+
+
+def test_lincomb_validation(lib):
+    import ctypes
+    ring = abi.mpc_ring(32, 32, 1)
+    c = (ctypes.c_int64 * 17)(*([1] * 17))
+    p = (ctypes.c_void_p * 17)(*([0x1000] * 17))
+    R = ctypes.byref(ring)
+    assert lib.mpc_lincomb(R, 8, 0, c, p, 0x2000, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_lincomb(R, 8, 17, c, p, 0x2000, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_lincomb(R, -1, 2, c, p, 0x2000, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_lincomb(None, 8, 2, c, p, 0x2000, None) == abi.MPC_E_NULL
+    assert lib.mpc_lincomb(R, 8, 2, c, p, 0x2008, None) == abi.MPC_E_ALIGN
+    q = (ctypes.c_void_p * 2)(0x1000, None)
+    assert lib.mpc_lincomb(R, 8, 2, c, q, 0x2000, None) == abi.MPC_E_NULL
+    assert lib.mpc_lincomb(R, 0, 2, c, p, None, None) == 0          # nothing to do, nothing launched
+
+
+def test_im2col_validation(lib):
+    import ctypes
+    ring = abi.mpc_ring(32, 32, 1)
+    R = ctypes.byref(ring)
+    assert lib.mpc_im2col(R, 1, 1, 4, 4, 3, 3, 1, 0x1000, 0x2000, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_im2col(R, 1, 1, 4, 4, 3, 1, 0, 0x1000, 0x2000, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_im2col(R, 1, 1, 1, 1, 5, 1, 1, 0x1000, 0x2000, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_im2col(R, 1, 1, 4, 4, 3, 1, 1, 0x1008, 0x2000, None) == abi.MPC_E_ALIGN
+    assert lib.mpc_im2col(R, 0, 3, 4, 4, 3, 1, 1, None, None, None) == 0        # empty batch
