@@ -48,8 +48,8 @@ def test_request_layout():
             assert total == request_bytes(r.layers, words)
             spans = []
             for li, L in enumerate(r.layers):
-                assert set(plan[li]) == {"E", "A", "mA", "F", "B", "mB", "C", "mC", "mR", "Dt", "alpha", "chi",
-                                         "chi_hat", "Z", "mZ", "mDc", "Dc", "cs"}
+                assert set(plan[li]) == {"E", "A", "mA", "F", "B", "mB", "C", "mC", "R", "mR", "Drest", "alpha",
+                                         "chi", "chi_hat", "Z", "mZ", "Dt", "mDc", "Dc", "cs"}
                 for k, (shape, off) in plan[li].items():
                     n = 8 * int(np.prod(shape))
                     assert off % 16 == 0 and off + n <= total
@@ -57,7 +57,7 @@ def test_request_layout():
                     spans.append((off, n))
                     if k in ("alpha", "chi", "chi_hat"):
                         assert inputs_end <= off and off + n <= keys_end
-                    elif k in ("Z", "mZ", "mDc", "Dc", "cs"):
+                    elif k in ("Z", "mZ", "Dt", "mDc", "Dc", "cs"):
                         assert keys_end <= off and off % 256 == 0
                     else:
                         assert off + n <= inputs_end and off % 256 == 0
