@@ -210,20 +210,31 @@ def mpc_workspace_size(layer: mpc_layer, which: int) -> int:
     return int(load().mpc_workspace_size(ctypes.byref(layer), int(which)))
 
 
-def _ws(layer, which, ws):
+def _ws(layer, which, ws, stream=None):
     if ws is not None:
         return _ptr(ws), ws.numel() * ws.element_size()
     need = mpc_workspace_size(layer, which)
     if need == 0:
         return None, 0
+    return _alloc_ws(need, stream)
+
+
+def _alloc_ws(need, stream):
+    """A workspace allocated on the call's stream, so that the caching
+    allocator orders its reuse after the call; it lives until the next call
+    that allocates one."""
     import torch
-    buf = torch.empty(need, dtype=torch.uint8, device="cuda")
-    _ws.keep = buf  # lives until the next call that allocates; the stream orders reuse
+    if stream is None or isinstance(stream, int):
+        buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+    else:
+        with torch.cuda.stream(stream):
+            buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+    _alloc_ws.keep = buf
     return buf.data_ptr(), need
 
 
 def mpc_linear_share(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None):
-    wp, wb = _ws(layer, MPC_WS_SHARE, ws)
+    wp, wb = _ws(layer, MPC_WS_SHARE, ws, stream)
     _check("mpc_linear_share", load().mpc_linear_share(
         ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(A_i), _ptr(B_i), _ptr(C_i), _ptr(Z_i),
         wp, wb, _stream(stream)))
@@ -233,7 +244,7 @@ def mpc_linear_share(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None):
 def mpc_linear_tag(layer, mode, alpha_i, E, F, mA_i, mB_i, mC_i, mZ_i, mR_i=None, Dtilde=None,
                    chi=None, mDc_i=None, Dc=None, ws=None, stream=None):
     which = MPC_WS_TAG_FULL if mode == MPC_TAG_FULL else MPC_WS_TAG_COMPACT
-    wp, wb = _ws(layer, which, ws)
+    wp, wb = _ws(layer, which, ws, stream)
     _check("mpc_linear_tag", load().mpc_linear_tag(
         ctypes.byref(layer), int(mode), _ptr(alpha_i), _ptr(E), _ptr(F), _ptr(mA_i), _ptr(mB_i),
         _ptr(mC_i), _ptr(mR_i), _ptr(Dtilde), _ptr(chi), _ptr(mZ_i), _ptr(mDc_i), _ptr(Dc),
@@ -243,7 +254,7 @@ def mpc_linear_tag(layer, mode, alpha_i, E, F, mA_i, mB_i, mC_i, mZ_i, mR_i=None
 
 def mpc_tag_check(layer, mode, alpha_i, chi_hat, opened, tag_i, cs_i, ws=None, stream=None):
     which = MPC_WS_CHECK_COMPACT if mode == MPC_CHECK_COMPACT else MPC_WS_CHECK_BATCHREC
-    wp, wb = _ws(layer, which, ws)
+    wp, wb = _ws(layer, which, ws, stream)
     _check("mpc_tag_check", load().mpc_tag_check(
         ctypes.byref(layer), int(mode), _ptr(alpha_i), _ptr(chi_hat), _ptr(opened), _ptr(tag_i),
         _ptr(cs_i), wp, wb, _stream(stream)))
@@ -262,7 +273,7 @@ def mpc_linear_tag_compact_noalloc(layer, alpha_i, E, F, mA_i, mB_i, mC_i, mR_i,
 
 def mpc_linear_share_trunc(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None):
     """Truncated layer, step 2: Z_i = C_i + E.B_i + A_i.F for every party."""
-    wp, wb = _ws(layer, MPC_WS_SHARE_TRUNC, ws)
+    wp, wb = _ws(layer, MPC_WS_SHARE_TRUNC, ws, stream)
     _check("mpc_linear_share_trunc", load().mpc_linear_share_trunc(
         ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(A_i), _ptr(B_i), _ptr(C_i), _ptr(Z_i),
         wp, wb, _stream(stream)))
@@ -271,7 +282,7 @@ def mpc_linear_share_trunc(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None
 
 def mpc_public_product(layer, E, F, P, ws=None, stream=None):
     """P = E.F (public)."""
-    wp, wb = _ws(layer, MPC_WS_PUBLIC_PRODUCT, ws)
+    wp, wb = _ws(layer, MPC_WS_PUBLIC_PRODUCT, ws, stream)
     _check("mpc_public_product", load().mpc_public_product(
         ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(P), wp, wb, _stream(stream)))
     return P
@@ -346,21 +357,18 @@ def mpc_launch_count_grouped(layers, which: int) -> int:
     return int(load().mpc_launch_count_grouped(_layer_array(layers), len(layers), int(which)))
 
 
-def _ws_grouped(layers, which, ws):
+def _ws_grouped(layers, which, ws, stream=None):
     if ws is not None:
         return _ptr(ws), ws.numel() * ws.element_size()
     need = mpc_workspace_size_grouped(layers, which)
     if need == 0:
         return None, 0
-    import torch
-    buf = torch.empty(need, dtype=torch.uint8, device="cuda")
-    _ws_grouped.keep = buf
-    return buf.data_ptr(), need
+    return _alloc_ws(need, stream)
 
 
 def mpc_linear_share_grouped(layers, ptrs, ws=None, stream=None):
     """Shares of many layers in one call (same results as one mpc_linear_share per layer)."""
-    wp, wb = _ws_grouped(layers, MPC_WS_SHARE, ws)
+    wp, wb = _ws_grouped(layers, MPC_WS_SHARE, ws, stream)
     _check("mpc_linear_share_grouped", load().mpc_linear_share_grouped(
         _layer_array(layers), len(layers), _ptr_array(mpc_share_ptrs, SHARE_PTR_FIELDS, ptrs), wp, wb,
         _stream(stream)))
@@ -369,7 +377,7 @@ def mpc_linear_share_grouped(layers, ptrs, ws=None, stream=None):
 def mpc_linear_tag_grouped(layers, mode, ptrs, ws=None, stream=None):
     """Tags of many layers in one call (same results as one mpc_linear_tag per layer)."""
     which = MPC_WS_TAG_FULL if mode == MPC_TAG_FULL else MPC_WS_TAG_COMPACT
-    wp, wb = _ws_grouped(layers, which, ws)
+    wp, wb = _ws_grouped(layers, which, ws, stream)
     _check("mpc_linear_tag_grouped", load().mpc_linear_tag_grouped(
         _layer_array(layers), len(layers), int(mode), _ptr_array(mpc_tag_ptrs, TAG_PTR_FIELDS, ptrs), wp, wb,
         _stream(stream)))

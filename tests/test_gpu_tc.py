@@ -29,8 +29,8 @@ def _lib():
     abi.load()
 
 
-def _path(M, K, N):
-    return abi.mpc_gemm_path(abi.make_layer(M, K, N))
+def _path(M, K, N, k=32, s=32):
+    return abi.mpc_gemm_path(abi.make_layer(M, K, N, k, s))
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=str)
@@ -162,4 +162,31 @@ def test_tc_ragged_k(ring, shape):
                               O.linear_share(ring.bits, i, d.E, d.F, p.A, p.B, p.C))
         assert np.array_equal(gpu_tag_full(ring, i, p.alpha, d.E, d.F, p.mA, p.mB, p.mC),
                               O.linear_tag_full(ring.bits, p.alpha, d.E, d.F, p.mA, p.mB, p.mC))
+    assert abi.mpc_device_status() == 0
+
+
+@pytest.mark.parametrize("ring,shape", [(synth.Z64, (1024, 512, 2048)), (synth.Z128, (1024, 256, 512))],
+                         ids=["z64_waves", "z128_waves"])
+def test_tc_waves_repeated_runs_stable(ring, shape):
+    """Repeated runs of a layer with more tiles than CTAs (full data-parallel
+    waves written directly through the staged epilogue, then a stream-K
+    remainder): every run is bit-identical to the first, which equals the oracle."""
+    M, K, N = shape
+    assert _path(M, K, N, ring.k, ring.s) == 1
+    g = lambda name, shape: synth.uniform(77, synth.TID[name], 0, shape, ring.bits)
+    E, F, A, B, C = g("E", (M, K)), g("F", (K, N)), g("A", (M, K)), g("B", (K, N)), g("C", (M, N))
+    import torch
+    from gpuhelp import dev, empty_like_ring, host
+    L = abi.make_layer(M, K, N, ring.k, ring.s, 1, 2)
+    d = [dev(a) for a in (E, F, A, B, C)]
+    ws = torch.empty(abi.mpc_workspace_size(L, abi.MPC_WS_SHARE), dtype=torch.uint8, device="cuda")
+    first = None
+    for rep in range(30):
+        Z = empty_like_ring((M, N), ring.words)
+        abi.mpc_linear_share(L, *d, Z, ws=ws)
+        if first is None:
+            first = Z.clone()
+            assert np.array_equal(host(Z), O.linear_share(ring.bits, 1, E, F, A, B, C))
+        else:
+            assert torch.equal(Z, first), f"run {rep}"
     assert abi.mpc_device_status() == 0
