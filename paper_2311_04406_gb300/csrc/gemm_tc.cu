@@ -156,18 +156,20 @@ __device__ __forceinline__ Biased<W> biased(const u64* e) {
 // ---------------------------------------------------------------------------
 // schedule
 //
-// The work units of a launch -- (output tile, Kd-deep K interval) pairs of all
-// its layers, numbered layer by layer, tile by tile -- are dealt to the G CTAs
-// in waves.  Each full wave gives every CTA c consecutive units (c = the
-// largest intervals-per-tile of the launch, so in a one-layer launch a CTA
-// gets exactly one whole tile per wave: the data-parallel schedule).  The
-// units left over after the full waves (fewer than G c) are split evenly over
-// the CTAs (stream-K), which balances layers with fewer tiles than CTAs.
-// Tiles are numbered in groups of GM row tiles, column-major inside a group,
-// so the G consecutive tiles of a wave form a compact block whose operand
-// tiles the CTAs share through L2 while they move through K together.
+// The work units of a layer -- (output tile, Kd-deep K interval) pairs,
+// numbered tile by tile -- are dealt to the G CTAs of the launch in waves.
+// Each full wave gives every CTA c = I consecutive units (I = intervals per
+// tile), i.e. exactly one whole tile: the data-parallel schedule.  The units
+// left after the full waves (fewer than G I) are split evenly over the CTAs
+// (stream-K), which balances layers with fewer tiles than CTAs.  A launch of
+// several layers deals every layer over all CTAs in turn (CTAs move on to the
+// next layer without waiting), so the CTAs running at any moment share that
+// layer's operands through L2; layer l's CTA index is rotated by the units of
+// the layers before it, so that small layers land on different CTAs.  Tiles
+// are numbered in groups of gm row tiles, column-major inside a group, so the
+// G consecutive tiles of a wave form a compact block of the output.
 struct Sched {
-    int64_t c;       // units per CTA in each full wave
+    int64_t c;       // units per CTA in each full wave (the layer's I)
     int64_t nfull;   // full waves
     int64_t S;       // units in the full waves (nfull G c)
     int64_t L;       // units of the last, partial wave
@@ -176,12 +178,22 @@ struct Sched {
 
 constexpr int GM_DEFAULT = 8;   // row tiles per swizzle group unless the launch table says otherwise
 
-// units of CTA b
+__host__ __device__ __forceinline__ Sched sched_of(int64_t U, int64_t I, int G) {
+    Sched s;
+    s.G = G;
+    s.c = I;
+    s.nfull = U / ((int64_t)G * I);
+    s.S = s.nfull * G * I;
+    s.L = U - s.S;
+    return s;
+}
+
+// units of (rotated) CTA b
 __host__ __device__ __forceinline__ int64_t cta_units(const Sched& s, int64_t b) {
     return s.nfull * s.c + ((b + 1) * s.L) / s.G - (b * s.L) / s.G;
 }
 
-// end of the range (of one CTA) that holds global unit u
+// end of the range (of one CTA) that holds unit u of a layer
 __host__ __device__ __forceinline__ int64_t range_end_of(const Sched& s, int64_t u) {
     if (u < s.S) return (u / s.c + 1) * s.c;
     // owner: the largest b with floor(b L / G) <= u - S
@@ -216,7 +228,6 @@ struct PrologueParams {
     uint8_t* Ap;
     const u64* C;
     u64* Z;
-    int64_t u_first;          // the layer's first global unit
     int I;                    // intervals per tile
     int64_t m_tiles, n_tiles;
     int gm;                   // row tiles per swizzle group
@@ -228,12 +239,12 @@ template <int G> struct PrologueGroup {
     int count;
     int64_t b_off[G + 1];
     PrologueParams p[G];
-    Sched sched;              // the GEMM launch's schedule
+    int grid;                 // CTAs of the GEMM launch
 };
 
 // thread `id` of `nthreads` working for one layer
 template <int W>
-__device__ __forceinline__ void prologue_body(const PrologueParams& p, const Sched& sc, int64_t id,
+__device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid, int64_t id,
                                               int64_t nthreads) {
     constexpr int NDIG = Cfg<W>::NDIG;
     constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
@@ -251,8 +262,9 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, const Sch
         const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C);
         ulonglong2* z2 = reinterpret_cast<ulonglong2*>(p.Z);
         const int64_t T = p.m_tiles * p.n_tiles;
+        const Sched sc = sched_of(T * p.I, p.I, grid);
         for (int64_t t = blk; t < T; t += nblk) {
-            const int64_t u = p.u_first + t * p.I;
+            const int64_t u = t * p.I;
             if (u + p.I <= range_end_of(sc, u)) continue;   // whole: written by its CTA
             int64_t mt, nt;
             tile_mn(t, p.m_tiles, p.n_tiles, p.gm, &mt, &nt);
@@ -350,7 +362,7 @@ __global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ P
     }
     const int64_t lb = (int64_t)blockIdx.x - g.b_off[gi];
     const int64_t nb = g.b_off[gi + 1] - g.b_off[gi];
-    prologue_body<W>(g.p[gi], g.sched, lb * 256 + threadIdx.x, nb * 256);
+    prologue_body<W>(g.p[gi], g.grid, lb * 256 + threadIdx.x, nb * 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,18 +382,18 @@ struct TcParams {
     int64_t m_tiles, n_tiles;
     int64_t U;       // work units = tiles x I
     int gm;          // row tiles per swizzle group
+    int64_t rot;     // rotation of the CTA index for this layer
 };
 
-// Up to G layers per launch.  Their work units are numbered consecutively:
-// layer g owns units [u_off[g], u_off[g + 1]).  The tensor maps live in the
-// kernel's parameter space (__grid_constant__), as for a single layer.
+// Up to G layers per launch, each dealt over all CTAs in turn (see the
+// schedule above).  The tensor maps live in the kernel's parameter space
+// (__grid_constant__), as for a single layer.
 template <int G> struct TcGroup {
     CUtensorMap tmB[G];
     CUtensorMap tmF[G];
     TcParams p[G];
-    int64_t u_off[G + 1];
-    Sched sched;
     int count;
+    int grid;        // CTAs of the launch
 };
 
 // Unit u (local to its layer) is interval u % I of tile u / I.
@@ -396,30 +408,127 @@ struct Unit {
 // the CTA's ranges of consecutive units starts; inside a range the position
 // (layer, tile in swizzled order, interval) advances incrementally.
 template <int G> struct Walker {
-    const TcGroup<G>& g;
-    const int64_t cta;
-    int64_t v = 0, left = 0, u = 0;
-    int gi = 0;
+    const TcParams* P;                 // the launch's layers (a copy in shared memory)
+    const int count, grid;
+    const int cta;
+    int gi = -1;
+    int vl = 0, nvl = 0;               // units of this CTA in layer gi: taken, total (< 2^31)
+    int left = 0, bp = 0;              // units left in the current range; rotated CTA index
+    int64_t u = 0;                     // unit index within the layer
+    int64_t nfull = 0, L = 0;          // layer gi's schedule: full waves, units of the last wave
     int ii = 0, m_in = 0, gm = 1;      // tile and swizzle counters (tile counts < 2^31)
-    int64_t mt = 0, nt = 0, grp = 0;
+    int mt = 0, nt = 0, grp = 0;
+    // the current layer's parameters, read from the parameter space only when
+    // the layer changes
+    int cI = 1, cKD = 1, cS = 1, cGM = 1;
+    int cNT = 1, cMT = 1;
 
-    __device__ __forceinline__ Walker(const TcGroup<G>& g_, int64_t cta_) : g(g_), cta(cta_) {}
+    __device__ __forceinline__ Walker(const TcParams* P_, int count_, int grid_, int cta_)
+        : P(P_), count(count_), grid(grid_), cta(cta_) {
+        advance_layer();
+    }
 
-    __device__ __forceinline__ void decode(const TcParams& p, int64_t ul) {
-        const int64_t GM = p.gm;
-        const int64_t tile = ul / p.I;
-        ii = (int)(ul - tile * p.I);
-        grp = tile / (GM * p.n_tiles);
-        const int64_t r = tile - grp * GM * p.n_tiles;
-        const int64_t lft = p.m_tiles - grp * GM;
-        gm = (int)(lft < GM ? lft : GM);
-        nt = r / gm;
-        m_in = (int)(r - nt * gm);
-        mt = grp * GM + m_in;
+    // the next layer in which this CTA has units (or past the last layer)
+    __device__ __forceinline__ void advance_layer() {
+        while (++gi < count) {
+            const TcParams& p = P[gi];
+            const Sched sc = sched_of(p.U, p.I, grid);
+            bp = (int)((cta + p.rot) % grid);
+            nvl = (int)cta_units(sc, bp);
+            vl = 0;
+            left = 0;
+            if (nvl > 0) {
+                nfull = sc.nfull;
+                L = sc.L;
+                cI = p.I;
+                cKD = p.KD;
+                cS = p.S_tot;
+                cGM = p.gm;
+                cNT = (int)p.n_tiles;
+                cMT = (int)p.m_tiles;
+                return;
+            }
+        }
     }
 
     __device__ __forceinline__ Unit next() {
-        const Sched& s = g.sched;
+        if (vl == nvl) advance_layer();
+        if (left == 0) {
+            const int64_t G_ = grid;
+            const int64_t full = nfull * cI;
+            int64_t len;
+            if (vl < full) {
+                u = ((vl / cI) * G_ + bp) * cI;
+                len = cI;
+            } else {
+                const int64_t a = (bp * L) / G_, e = ((bp + 1) * L) / G_;
+                u = nfull * G_ * cI + a;
+                len = e - a;
+            }
+            left = (int)len - 1;
+            const int64_t GM = cGM;
+            const int64_t tile = u / cI;
+            ii = (int)(u - tile * cI);
+            grp = (int)(tile / (GM * cNT));
+            const int64_t r = tile - grp * GM * cNT;
+            const int lft = cMT - grp * cGM;
+            gm = lft < cGM ? lft : cGM;
+            nt = (int)(r / gm);
+            m_in = (int)(r - (int64_t)nt * gm);
+            mt = grp * cGM + m_in;
+        } else {
+            ++u;
+            --left;
+            if (++ii == cI) {
+                ii = 0;
+                if (++m_in == gm) {
+                    m_in = 0;
+                    if (++nt == cNT) {
+                        nt = 0;
+                        ++grp;
+                        const int lft = cMT - grp * cGM;
+                        gm = lft < cGM ? lft : cGM;
+                    }
+                }
+                mt = grp * cGM + m_in;
+            }
+        }
+        ++vl;
+        Unit x;
+        x.mt = mt;
+        x.nt = nt;
+        x.ii = ii;
+        x.nst = min(cKD, cS - x.ii * cKD);
+        x.flush = (left == 0) || (x.ii == cI - 1);
+        return x;
+    }
+};
+
+// One layer per launch: the same dealing without the layer bookkeeping (the
+// layer's parameters stay in registers; measured faster on small-K layers).
+template <> struct Walker<1> {
+    const int cta;
+    static constexpr int gi = 0;
+    Sched s;
+    int64_t v = 0, left = 0, u = 0;
+    int ii = 0, m_in = 0, gm = 1;
+    int64_t mt = 0, nt = 0, grp = 0;
+    int cI = 1, cKD = 1, cS = 1, cGM = 1;
+    int64_t cNT = 1, cMT = 1;
+
+    __device__ __forceinline__ Walker(const TcParams* P, int count, int grid, int cta_) : cta(cta_) {
+        (void)count;
+        const TcParams& p = P[0];
+        s = sched_of(p.U, p.I, grid);
+        cI = p.I;
+        cKD = p.KD;
+        cS = p.S_tot;
+        cGM = p.gm;
+        cNT = p.n_tiles;
+        cMT = p.m_tiles;
+    }
+
+    __device__ __forceinline__ Unit next() {
         if (left == 0) {
             const int64_t full = s.nfull * s.c;
             int64_t len;
@@ -432,44 +541,50 @@ template <int G> struct Walker {
                 len = e - a;
             }
             left = len - 1;
-            if constexpr (G > 1)
-                while (gi + 1 < g.count && u >= g.u_off[gi + 1]) ++gi;
-            decode(g.p[gi], u - g.u_off[gi]);
+            const int64_t GM = cGM;
+            const int64_t tile = u / cI;
+            ii = (int)(u - tile * cI);
+            grp = tile / (GM * cNT);
+            const int64_t r = tile - grp * GM * cNT;
+            const int64_t lft = cMT - grp * GM;
+            gm = (int)(lft < GM ? lft : GM);
+            nt = r / gm;
+            m_in = (int)(r - nt * gm);
+            mt = grp * GM + m_in;
         } else {
             ++u;
             --left;
-            const TcParams& p = g.p[gi];
-            if (G > 1 && gi + 1 < g.count && u == g.u_off[gi + 1]) {
-                ++gi;
-                ii = m_in = 0;
-                grp = nt = mt = 0;
-                const int64_t mtl = g.p[gi].m_tiles;
-                gm = (int)(mtl < g.p[gi].gm ? mtl : g.p[gi].gm);
-            } else if (++ii == p.I) {
+            if (++ii == cI) {
                 ii = 0;
                 if (++m_in == gm) {
                     m_in = 0;
-                    if (++nt == p.n_tiles) {
+                    if (++nt == cNT) {
                         nt = 0;
                         ++grp;
-                        const int64_t lft = p.m_tiles - grp * p.gm;
-                        gm = (int)(lft < p.gm ? lft : p.gm);
+                        const int64_t lft = cMT - grp * cGM;
+                        gm = (int)(lft < cGM ? lft : cGM);
                     }
                 }
-                mt = grp * p.gm + m_in;
+                mt = grp * cGM + m_in;
             }
         }
         ++v;
-        const TcParams& p = g.p[gi];
         Unit x;
         x.mt = mt;
         x.nt = nt;
         x.ii = ii;
-        x.nst = min(p.KD, p.S_tot - x.ii * p.KD);
-        x.flush = (left == 0) || (x.ii == p.I - 1);
+        x.nst = min(cKD, cS - x.ii * cKD);
+        x.flush = (left == 0) || (x.ii == cI - 1);
         return x;
     }
 };
+
+// units of CTA `cta` over all layers of the launch
+__device__ __forceinline__ int64_t cta_total(const TcParams* P, int count, int grid, int64_t cta) {
+    int64_t n = 0;
+    for (int l = 0; l < count; ++l) n += cta_units(sched_of(P[l].U, P[l].I, grid), (cta + P[l].rot) % grid);
+    return n;
+}
 
 __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
     *abort_flag = 1;
@@ -499,9 +614,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Sched& sc = g.sched;
     const int64_t cta = blockIdx.x;
-    const int64_t nv = cta_units(sc, cta);   // units of this CTA
+    // the layers' parameters, copied once into shared memory: the roles read
+    // them at every unit, and shared-memory loads are cheap where dynamically
+    // indexed parameter-space loads are not
+    // (a one-layer launch reads its parameters straight from the parameter space)
+    __shared__ TcParams sp[G > 1 ? G : 1];
+    if constexpr (G > 1) {
+        static_assert(sizeof(TcParams) % 8 == 0, "TcParams is copied as 64-bit words");
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(&g.p[0]);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(sp);
+        const int nw = g.count * (int)(sizeof(TcParams) / 8);
+        for (int i = threadIdx.x; i < nw; i += NTHREADS) dst[i] = src[i];
+    }
+    const int count = g.count, grid = g.grid;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -528,15 +654,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int64_t nv = G == 1 ? cta_units(sched_of(g.p[0].U, g.p[0].I, grid), cta)
+                              : cta_total(sp, count, grid, cta);   // units of this CTA
 
     if (warp == W_APROD) {
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            Walker<G> wk(g, cta);
+            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
             for (int64_t v = 0; v < nv && ok; ++v) {
                 const Unit x = wk.next();
-                const TcParams& p = g.p[wk.gi];
+                const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
                 const int64_t m_tile = x.mt;
                 const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + (size_t)x.ii * p.KD) * A_STAGE;
                 for (int j = 0; j < x.nst; ++j, ++it) {
@@ -559,11 +687,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            Walker<G> wk(g, cta);
+            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
             int prefetched = -1;
             for (int64_t v = 0; v < nv && ok; ++v) {
                 const Unit x = wk.next();
-                const TcParams& p = g.p[wk.gi];
+                const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
                 const CUtensorMap* tmB = &g.tmB[wk.gi];
                 const CUtensorMap* tmF = &g.tmF[wk.gi];
                 if (prefetched != wk.gi) {
@@ -616,7 +744,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
         constexpr int TPT = W == 1 ? NDIG : NDIG / 2;   // planes written per thread
         int total = 0;
         {
-            Walker<G> wk(g, cta);
+            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
             for (int64_t v = 0; v < nv; ++v) total += wk.next().nst;
         }
         for (int it = 0; it < total; ++it) {
@@ -664,7 +792,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
             const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
             bool ok = true;
             int it = 0;
-            Walker<G> wk(g, cta);
+            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
             for (int64_t v = 0; v < nv && ok; ++v) {
                 const Unit x = wk.next();
                 const int set = (int)(v & 1);
@@ -707,10 +835,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
         int seg_ii = -1;   // first interval of the current segment
-        Walker<G> wk(g, cta);
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
         for (int64_t v = 0; v < nv; ++v) {
             const Unit x = wk.next();
-            const TcParams& p = g.p[wk.gi];
+            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
             const int set = (int)(v & 1);
             bool got = ptx::mbar_wait(&accFull[set], (int)((v >> 1) & 1), abort_flag, WAIT_LIMIT);
             if (!__all_sync(0xffffffffu, got)) {
@@ -753,29 +881,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 __syncwarp();
                 constexpr int RPI = 32 / ND;     // rows per instruction
                 constexpr int NIT = 32 / RPI;
+                constexpr int BATCH = NIT;        // addend loads in flight together
                 const int rr = lane / ND, cc = lane % ND;
                 const int64_t n = x.nt * ND + cc;
                 const int64_t mb = x.mt * BM + quad * 32;
-                // all addend loads first (independent, in flight together),
-                // then the stores or atomic adds
-                Sum cv[NIT];
 #pragma unroll
-                for (int i = 0; i < NIT; ++i) {
-                    const int64_t m = mb + i * RPI + rr;
-                    cv[i] = (whole && p.C && m < p.M && n < p.N) ? ldg_elem<W>(p.C, m * p.N + n) : (Sum)0;
-                }
+                for (int i0 = 0; i0 < NIT; i0 += BATCH) {
+                    // a batch of addend loads first, then its stores or atomic adds
+                    Sum cv[BATCH];
 #pragma unroll
-                for (int i = 0; i < NIT; ++i) {
-                    const int r = i * RPI + rr;
-                    const int64_t m = mb + r;
-                    if (m < p.M && n < p.N) {
-                        const Sum v = stg[r * (ND + 1) + cc];
-                        const int64_t e = m * p.N + n;
-                        if (whole) {
-                            st_elem<W>(p.Z, e, cv[i] + v);
-                        } else {
-                            if constexpr (W == 1) red_add_u64(p.Z + e, v);
-                            else atomic_add_u128(p.Z + 2 * e, v);
+                    for (int i = 0; i < BATCH; ++i) {
+                        const int64_t m = mb + (i0 + i) * RPI + rr;
+                        cv[i] = (whole && p.C && m < p.M && n < p.N) ? ldg_elem<W>(p.C, m * p.N + n) : (Sum)0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < BATCH; ++i) {
+                        const int r = (i0 + i) * RPI + rr;
+                        const int64_t m = mb + r;
+                        if (m < p.M && n < p.N) {
+                            const Sum v = stg[r * (ND + 1) + cc];
+                            const int64_t e = m * p.N + n;
+                            if (whole) {
+                                st_elem<W>(p.Z, e, cv[i] + v);
+                            } else {
+                                if constexpr (W == 1) red_add_u64(p.Z + e, v);
+                                else atomic_add_u128(p.Z + 2 * e, v);
+                            }
                         }
                     }
                 }
@@ -882,34 +1013,31 @@ bool fill(TcGroup<G>& tg, PrologueGroup<G>& pg, int j, const GemmArgs& a, uint8_
     else if (!make_map(&tg.tmB[j], a.B, a.K, a.N, W, Cfg<W>::ND)) return false;
     const int gm = a.gm > 0 ? a.gm : GM_DEFAULT;
     tg.p[j] = TcParams{Ap, a.Z, a.C, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND,
-                       pl.m_tiles, pl.n_tiles, pl.U, gm};
+                       pl.m_tiles, pl.n_tiles, pl.U, gm, 0};
     pg.p[j] = PrologueParams{a.E, a.X, a.alpha, a.coef, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z,
-                             tg.u_off[j], pl.I, pl.m_tiles, pl.n_tiles, gm};
-    tg.u_off[j + 1] = tg.u_off[j] + pl.U;
+                             pl.I, pl.m_tiles, pl.n_tiles, gm};
     pg.b_off[j + 1] = pg.b_off[j] + pl.m_tiles * pl.S_tot;
     return true;
 }
 
-// The schedule of a launch of U units whose largest tile has I_max intervals.
-Sched make_sched(int64_t U, int64_t I_max, int sms) {
-    Sched s{};
-    s.G = (int)(U < sms ? U : sms);
-    s.c = I_max;
-    s.nfull = U / ((int64_t)s.G * s.c);
-    s.S = s.nfull * s.G * s.c;
-    s.L = U - s.S;
-    return s;
-}
-
 template <int W, int G>
 cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) {
-    int64_t i_max = 1;
-    for (int j = 0; j < tg.count; ++j) i_max = tg.p[j].I > i_max ? tg.p[j].I : i_max;
-    tg.sched = pg.sched = make_sched(tg.u_off[tg.count], i_max, sm_count());
+    // one CTA per SM (fewer when the launch has fewer units); each layer's
+    // CTA index is rotated by the units of the layers before it
+    int64_t total = 0;
+    for (int j = 0; j < tg.count; ++j) total += tg.p[j].U;
+    const int sms = sm_count();
+    const int grid = (int)(total < sms ? (total > 0 ? total : 1) : sms);
+    int64_t acc = 0;
+    for (int j = 0; j < tg.count; ++j) {
+        tg.p[j].rot = acc % grid;
+        acc += tg.p[j].U;
+    }
+    tg.grid = pg.grid = grid;
     prologue_kernel<W, G><<<(unsigned)pg.b_off[pg.count], 256, 0, st>>>(pg);
     cudaError_t e = ensure_smem_attr<W, G>();
     if (e != cudaSuccess) return e;
-    ring_gemm_tc_kernel<W, G><<<(unsigned)tg.sched.G, NTHREADS, Layout<W>::SMEM, st>>>(tg);
+    ring_gemm_tc_kernel<W, G><<<(unsigned)grid, NTHREADS, Layout<W>::SMEM, st>>>(tg);
     return cudaGetLastError();
 }
 
@@ -918,22 +1046,39 @@ cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t 
     TcGroup<1> tg{};
     PrologueGroup<1> pg{};
     tg.count = pg.count = 1;
+    pg.b_off[0] = 0;
     if (!fill<W, 1>(tg, pg, 0, a, Ap, pl)) return cudaErrorInvalidValue;
     return launch_group<W, 1>(tg, pg, st);
 }
+
+// One launch pair for the layers order[i0 .. i0 + cnt) (cnt <= G).
+template <int W, int G>
+cudaError_t launch_chunk(const GemmArgs* a, uint8_t* const* Ap, const int* order, int cnt, cudaStream_t st) {
+    static_assert(alignof(TcGroup<G>) >= 64, "tensor map alignment");
+    auto* tg = new (std::nothrow) TcGroup<G>;
+    auto* pg = new (std::nothrow) PrologueGroup<G>;
+    cudaError_t e = (tg && pg) ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) {
+        tg->count = pg->count = cnt;
+        pg->b_off[0] = 0;
+        for (int j = 0; j < cnt && e == cudaSuccess; ++j) {
+            const GemmArgs& x = a[order[j]];
+            if (!fill<W, G>(*tg, *pg, j, x, Ap[order[j]], make_plan(x.M, x.K, x.N, W, x.one_half)))
+                e = cudaErrorInvalidValue;
+        }
+        if (e == cudaSuccess) e = launch_group<W, G>(*tg, *pg, st);
+    }
+    delete tg;
+    delete pg;
+    return e;
+}
+
+constexpr int GSMALL = 16;   // small groups use a kernel with a smaller parameter block
 
 // Layers [0, n) in launches of up to GMAX layers; layer i's digit planes at
 // Ap[i].  Every layer is eligible and has the ring width W.
 template <int W>
 cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st) {
-    static_assert(alignof(TcGroup<GMAX>) >= 64, "tensor map alignment");
-    auto* tg = new (std::nothrow) TcGroup<GMAX>;
-    auto* pg = new (std::nothrow) PrologueGroup<GMAX>;
-    if (!tg || !pg) {
-        delete tg;
-        delete pg;
-        return cudaErrorMemoryAllocation;
-    }
     // layers with more K intervals first, so that whole tiles of the long
     // layers line up with the CTAs' ranges (the order changes no result)
     std::vector<int> order(n);
@@ -946,19 +1091,9 @@ cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream
     cudaError_t e = cudaSuccess;
     for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += GMAX) {
         const int cnt = n - i0 < GMAX ? n - i0 : GMAX;
-        tg->count = pg->count = cnt;
-        tg->u_off[0] = 0;
-        pg->b_off[0] = 0;
-        for (int j = 0; j < cnt && e == cudaSuccess; ++j) {
-            const int li = order[i0 + j];
-            const GemmArgs& x = a[li];
-            if (!fill<W, GMAX>(*tg, *pg, j, x, Ap[li], make_plan(x.M, x.K, x.N, W, x.one_half)))
-                e = cudaErrorInvalidValue;
-        }
-        if (e == cudaSuccess) e = launch_group<W, GMAX>(*tg, *pg, st);
+        e = cnt <= GSMALL ? launch_chunk<W, GSMALL>(a, Ap, order.data() + i0, cnt, st)
+                          : launch_chunk<W, GMAX>(a, Ap, order.data() + i0, cnt, st);
     }
-    delete tg;
-    delete pg;
     return e;
 }
 
