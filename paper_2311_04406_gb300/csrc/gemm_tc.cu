@@ -788,45 +788,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
             ptx::mbar_arrive(&full[s]);
         }
     } else if (warp == W_MMA) {
-        if (lane == 0) {
-            const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
-            bool ok = true;
-            int it = 0;
-            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
-            for (int64_t v = 0; v < nv && ok; ++v) {
-                const Unit x = wk.next();
-                const int set = (int)(v & 1);
-                if (!ptx::mbar_wait(&accEmpty[set], (int)((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
-                    record_timeout(abort_flag);
+        // The whole warp runs the loop (waits included) and one elected lane
+        // issues the MMAs and commits.
+        const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
+        bool ok = true;
+        int it = 0;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const int set = (int)(v & 1);
+            const bool got = ptx::mbar_wait(&accEmpty[set], (int)((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            ptx::tc_fence_after();
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int s = it % STAGES;
+                const bool ready = ptx::mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, ready)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
                     break;
                 }
                 ptx::tc_fence_after();
-                for (int j = 0; j < x.nst; ++j, ++it) {
-                    const int s = it % STAGES;
-                    if (!ptx::mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT)) {
-                        record_timeout(abort_flag);
-                        ok = false;
-                        break;
-                    }
-                    ptx::tc_fence_after();
-                    const uint64_t bdesc =
-                        ptx::smem_desc_kmajor(bBase + s * B_STAGE_BYTES, CORE_LBO, CORE_SBO);
+                const uint32_t leader = ptx::elect_one();
+                const uint64_t bdesc = ptx::smem_desc_kmajor(bBase + s * B_STAGE_BYTES, CORE_LBO, CORE_SBO);
 #pragma unroll
-                    for (int i = 0; i < NDIG; ++i) {
-                        const uint64_t adesc = ptx::smem_desc_kmajor(
-                            aBase + s * A_STAGE + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
-                        const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
-                        ptx::mma_f16(tmem + set * NSTACK + i * ND, adesc, bdesc, idesc,
-                                     (j == 0 && i == 0) ? 0u : 1u);
-                    }
-                    ptx::mma_commit(&empty[s]);
+                for (int i = 0; i < NDIG; ++i) {
+                    const uint64_t adesc =
+                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
+                    const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
+                    ptx::mma_f16_if(leader, tmem + set * NSTACK + i * ND, adesc, bdesc, idesc,
+                                    (j == 0 && i == 0) ? 0u : 1u);
                 }
-                ptx::mma_commit(&accFull[set]);
+                ptx::mma_commit_if(leader, &empty[s]);
             }
-            // all MMAs of this CTA complete before TMEM is released
-            ptx::mma_commit(mmaDone);
-            ptx::mbar_wait(mmaDone, 0, abort_flag, WAIT_LIMIT);
+            if (ok) ptx::mma_commit_if(ptx::elect_one(), &accFull[set]);
         }
+        // all MMAs of this CTA complete before TMEM is released
+        ptx::mma_commit_if(ptx::elect_one(), mmaDone);
+        ptx::mbar_wait(mmaDone, 0, abort_flag, WAIT_LIMIT);
     } else {
         // drain warps: TMEM lane quadrant = warp % 4
         const int quad = warp & 3;
