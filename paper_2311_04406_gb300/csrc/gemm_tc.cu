@@ -657,71 +657,73 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     const int64_t nv = G == 1 ? cta_units(sched_of(g.p[0].U, g.p[0].I, grid), cta)
                               : cta_total(sp, count, grid, cta);   // units of this CTA
 
+    // The producer and MMA roles run as whole warps (waits included), with one
+    // elected lane issuing the copies, MMAs and commits.
     if (warp == W_APROD) {
-        if (lane == 0) {
-            int it = 0;
-            bool ok = true;
-            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
-            for (int64_t v = 0; v < nv && ok; ++v) {
-                const Unit x = wk.next();
-                const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
-                const int64_t m_tile = x.mt;
-                const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + (size_t)x.ii * p.KD) * A_STAGE;
-                for (int j = 0; j < x.nst; ++j, ++it) {
-                    const int s = it % STAGES;
-                    if (!ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
-                        record_timeout(abort_flag);
-                        ok = false;
-                        break;
-                    }
-                    ptx::mbar_arrive_expect_tx(&full[s], A_STAGE);
-                    ptx::bulk_g2s(sA + s * A_STAGE, src + (size_t)j * A_STAGE, A_STAGE, &full[s]);
+        int it = 0;
+        bool ok = true;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
+            const int64_t m_tile = x.mt;
+            const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + (size_t)x.ii * p.KD) * A_STAGE;
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int s = it % STAGES;
+                const bool free_ = ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, free_)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
                 }
+                const uint32_t leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &full[s], A_STAGE);
+                ptx::bulk_g2s_if(leader, sA + s * A_STAGE, src + (size_t)j * A_STAGE, A_STAGE, &full[s]);
             }
-            // copies still in flight (only possible after a timeout) must land
-            // before the CTA's shared memory is released
-            for (int j = max(0, it - STAGES); j < it; ++j)
-                ptx::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, abort_flag, WAIT_LIMIT);
         }
+        // copies still in flight (only possible after a timeout) must land
+        // before the CTA's shared memory is released
+        for (int j = max(0, it - STAGES); j < it; ++j)
+            ptx::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, abort_flag, WAIT_LIMIT);
     } else if (warp == W_BPROD) {
-        if (lane == 0) {
-            int it = 0;
-            bool ok = true;
-            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
-            int prefetched = -1;
-            for (int64_t v = 0; v < nv && ok; ++v) {
-                const Unit x = wk.next();
-                const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
-                const CUtensorMap* tmB = &g.tmB[wk.gi];
-                const CUtensorMap* tmF = &g.tmF[wk.gi];
-                if (prefetched != wk.gi) {
+        int it = 0;
+        bool ok = true;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        int prefetched = -1;
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
+            const CUtensorMap* tmB = &g.tmB[wk.gi];
+            const CUtensorMap* tmF = &g.tmF[wk.gi];
+            if (prefetched != wk.gi) {
+                if (lane == 0) {
                     ptx::prefetch_tmap(tmB);
                     ptx::prefetch_tmap(tmF);
-                    prefetched = wk.gi;
                 }
-                // x coordinate in 64-bit words (ND W words per tile)
-                const int x0 = (int)x.nt * ND * W;
-                for (int j = 0; j < x.nst; ++j, ++it) {
-                    const int r = it % RAW;
-                    if (!ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
-                        record_timeout(abort_flag);
-                        ok = false;
-                        break;
-                    }
-                    ptx::mbar_arrive_expect_tx(&rawFull[r], RAW_BYTES);
-                    // rows at or beyond K inside a padded half arrive zero-filled
-                    const int64_t kp0 = (int64_t)(x.ii * p.KD + j) * KS;
-                    if (p.one_half)
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, tmF, x0, (int)kp0, &rawFull[r]);
-                    else if (kp0 < p.Kp)
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, tmB, x0, (int)kp0, &rawFull[r]);
-                    else
-                        ptx::tma_load_2d(sRaw + r * RAW_BYTES, tmF, x0, (int)(kp0 - p.Kp), &rawFull[r]);
-                }
+                prefetched = wk.gi;
             }
-            for (int j = max(0, it - RAW); j < it; ++j)
-                ptx::mbar_wait(&rawFull[j % RAW], (j / RAW) & 1, abort_flag, WAIT_LIMIT);
+            // x coordinate in 64-bit words (ND W words per tile)
+            const int x0 = (int)x.nt * ND * W;
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int r = it % RAW;
+                const bool free_ = ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, free_)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                const uint32_t leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &rawFull[r], RAW_BYTES);
+                // rows at or beyond K inside a padded half arrive zero-filled
+                const int64_t kp0 = (int64_t)(x.ii * p.KD + j) * KS;
+                const bool second = p.one_half || kp0 >= p.Kp;
+                const CUtensorMap* tm = second ? tmF : tmB;
+                const int y = (int)(p.one_half || kp0 < p.Kp ? kp0 : kp0 - p.Kp);
+                ptx::tma_load_2d_if(leader, sRaw + r * RAW_BYTES, tm, x0, y, &rawFull[r]);
+            }
         }
+        for (int j = max(0, it - RAW); j < it; ++j)
+            ptx::mbar_wait(&rawFull[j % RAW], (j / RAW) & 1, abort_flag, WAIT_LIMIT);
     } else if (warp >= W_CONV0 && warp < W_CONV0 + 4) {
         // Each converter thread turns 4 consecutive K values of one column into
         // digit planes (half a core-matrix row per plane): all 8 planes for
