@@ -1095,8 +1095,10 @@ cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream
     cudaError_t e = cudaSuccess;
     for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += GMAX) {
         const int cnt = n - i0 < GMAX ? n - i0 : GMAX;
-        e = cnt <= GSMALL ? launch_chunk<W, GSMALL>(a, Ap, order.data() + i0, cnt, st)
-                          : launch_chunk<W, GMAX>(a, Ap, order.data() + i0, cnt, st);
+        // a lone layer takes the one-layer kernel (parameters at constant offsets)
+        e = cnt == 1        ? launch_chunk<W, 1>(a, Ap, order.data() + i0, cnt, st)
+            : cnt <= GSMALL ? launch_chunk<W, GSMALL>(a, Ap, order.data() + i0, cnt, st)
+                            : launch_chunk<W, GMAX>(a, Ap, order.data() + i0, cnt, st);
     }
     return e;
 }
