@@ -167,7 +167,9 @@ int mpc_tag_check(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
  * GPU: every tensor-core layer of the group (up to 64 per launch) is scheduled
  * by ONE persistent prologue + GEMM launch pair whose CTAs work through the
  * layers' (tile, K interval) units in turn; the remaining layers run the
- * integer-pipe kernels one by one.
+ * integer-pipe kernels one by one.  A tensor-core layer long enough to keep
+ * every SM busy for 64 waves of units gets a launch pair of its own (it gains
+ * nothing from sharing one and runs faster alone).
  *
  * layers[count], ptrs[count]: HOST arrays, read during the call only.  All
  * layers share one ring (MPC_E_RING otherwise); the party may differ per

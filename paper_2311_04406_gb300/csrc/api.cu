@@ -534,14 +534,20 @@ int mpc_launch_count_grouped(const mpc_layer* layers, int count, int which) {
     if (count < 0) return MPC_E_SHAPE;
     if (count == 0) return 0;
     if (!layers) return MPC_E_NULL;
-    int tc = 0, n = 0;
+    int n = 0;
+    std::vector<int64_t> tM, tK, tN;   // the tensor-core layers
     for (int i = 0; i < count; ++i) {
         CHK(check_layer(&layers[i]));
         if (!same_ring(layers[i].ring, layers[0].ring)) return MPC_E_RING;
         const mpc_layer& L = layers[i];
         if (which == MPC_WS_SHARE || which == MPC_WS_TAG_FULL) {
-            if (on_tc(L)) ++tc;
-            else if (L.M > 0 && L.N > 0) n += 1;
+            if (on_tc(L)) {
+                tM.push_back(L.M);
+                tK.push_back(L.K);
+                tN.push_back(L.N);
+            } else if (L.M > 0 && L.N > 0) {
+                n += 1;
+            }
         } else if (which == MPC_WS_TAG_COMPACT) {
             // counted below for the whole group
         } else {
@@ -557,7 +563,7 @@ int mpc_launch_count_grouped(const mpc_layer* layers, int count, int which) {
         }
         return mpcl::compact_grouped_launches(M.data(), K.data(), N.data(), count);
     }
-    return n + mpcl::gemm_tc_grouped_launches(tc);
+    return n + mpcl::gemm_tc_grouped_launches(tM.data(), tK.data(), tN.data(), (int)tM.size(), layers[0].ring.words);
 }
 
 }  // extern "C"

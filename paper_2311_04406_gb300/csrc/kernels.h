@@ -52,7 +52,7 @@ cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStr
 // (up to 64 layers per prologue + GEMM pair); layer i's digit planes at Ap[i]
 // (gemm_tc_workspace bytes, 256-byte aligned)
 cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st);
-int gemm_tc_grouped_launches(int n);
+int gemm_tc_grouped_launches(const int64_t* M, const int64_t* K, const int64_t* N, int n, int words);
 // 1 when a bounded wait on a barrier nothing arrives at gave up (as it must),
 // 0 if it did not, -1 on a CUDA error; synchronous
 int wait_selftest(long long limit, cudaStream_t st);

@@ -107,6 +107,10 @@ def test_grouped_host_logic(lib):
     # one prologue + GEMM pair for the three tensor-core layers, one kernel for the other
     assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_SHARE) == 2 + 1
     assert abi.mpc_launch_count_grouped(layers * 30, abi.MPC_WS_TAG_FULL) == 2 * 2 + 30
+    # a layer with units for >= 64 waves of the grid (2048 x 4096 x 4096: 131072 units) gets a
+    # launch pair of its own
+    long_ = abi.make_layer(2048, 4096, 4096)
+    assert abi.mpc_launch_count_grouped([long_] + layers, abi.MPC_WS_SHARE) == 2 + 2 + 1
     # the CompactTag tags of a group: rows, finalize and vec passes, one launch each per 64 layers
     assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_TAG_COMPACT) == 3
     assert abi.mpc_launch_count_grouped(layers * 20, abi.MPC_WS_TAG_COMPACT) == 6
