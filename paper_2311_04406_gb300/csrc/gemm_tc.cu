@@ -99,7 +99,8 @@ constexpr int NCONV = 128;               // converter threads
 constexpr int NDRAIN = 128;              // drain threads
 constexpr long long WAIT_LIMIT = 4000000000LL;   // clock cycles (about 2 s)
 constexpr int MAX_STAGES = 8;
-constexpr int NBARS = 2 * MAX_STAGES + 2 * RAW + 2 + 2 + 1;
+constexpr int NINFO = 4;                 // unit descriptors in flight from the MMA warp to the drain
+constexpr int NBARS = 2 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
 
 template <int W> struct Layout {
     static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE_BYTES;
@@ -111,11 +112,14 @@ template <int W> struct Layout {
     static constexpr uint32_t OFF_STG = OFF_RAW + RAW * RAW_BYTES;
     static constexpr uint32_t STG_BYTES = 4 * 32 * (Cfg<W>::ND + 1) * 8 * W;
     static constexpr uint32_t OFF_BAR = OFF_STG + STG_BYTES;
-    static constexpr uint32_t SMEM = OFF_BAR + NBARS * 8 + 16;
+    static constexpr uint32_t OFF_INFO = (OFF_BAR + NBARS * 8 + 16 + 15) / 16 * 16;   // int4 slots
+    static constexpr uint32_t SMEM = OFF_INFO + NINFO * 16;
 };
 static_assert(Cfg<1>::NDIG * Cfg<1>::ND == NSTACK && Cfg<2>::NDIG * Cfg<2>::ND == NSTACK, "stack");
 static_assert(Layout<1>::SMEM <= 227 * 1024 && Layout<2>::SMEM <= 227 * 1024, "smem");
 static_assert(Cfg<1>::STAGES <= MAX_STAGES && Cfg<2>::STAGES <= MAX_STAGES, "barrier slots");
+static_assert(Layout<1>::OFF_BAR % 16 == 0 && Layout<2>::OFF_BAR % 16 == 0, "barrier alignment");
+static_assert(Layout<1>::OFF_INFO % 16 == 0 && Layout<2>::OFF_INFO % 16 == 0, "int4 slots need 16-byte alignment");
 
 constexpr unsigned long long DIGIT_BIAS = 0x8080808080808080ULL;
 constexpr uint32_t F16_1152X2 = 0x64806480u;   // fp16 (1152, 1152)
@@ -610,8 +614,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     uint64_t* accFull = rawEmpty + RAW;
     uint64_t* accEmpty = accFull + 2;
     uint64_t* mmaDone = accEmpty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mmaDone + 1);
+    uint64_t* infoFull = mmaDone + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(infoFull + NINFO);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    // the MMA warp hands each unit's (row tile, column tile, interval, flush |
+    // layer << 1) to the drain warps through NINFO slots
+    int4* info = reinterpret_cast<int4*>(smem + Layout<W>::OFF_INFO);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t cta = blockIdx.x;
@@ -643,6 +651,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
             ptx::mbar_init(&accEmpty[b], NDRAIN);
         }
         ptx::mbar_init(mmaDone, 1);
+        for (int i = 0; i < NINFO; ++i) ptx::mbar_init(&infoFull[i], 1);
         *abort_flag = 0;
         ptx::fence_barrier_init();
     }
@@ -805,6 +814,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 break;
             }
             ptx::tc_fence_after();
+            // slot v % NINFO last held unit v - NINFO, which the drain finished
+            // before it released the accumulator set this wait was for
+            if (lane == 0) {
+                info[v % NINFO] = make_int4((int)x.mt, (int)x.nt, x.ii, (int)x.flush | (wk.gi << 1));
+                ptx::mbar_arrive(&infoFull[v % NINFO]);
+            }
             for (int j = 0; j < x.nst; ++j, ++it) {
                 const int s = it % STAGES;
                 const bool ready = ptx::mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT);
@@ -839,10 +854,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
         int seg_ii = -1;   // first interval of the current segment
-        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
         for (int64_t v = 0; v < nv; ++v) {
-            const Unit x = wk.next();
-            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
+            const bool have = ptx::mbar_wait(&infoFull[v % NINFO], (int)((v / NINFO) & 1), abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, have)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            const int4 u = info[v % NINFO];
+            const int x_ii = u.z;
+            const bool x_flush = (u.w & 1) != 0;
+            const TcParams& p = G == 1 ? g.p[0] : sp[u.w >> 1];
             const int set = (int)(v & 1);
             bool got = ptx::mbar_wait(&accFull[set], (int)((v >> 1) & 1), abort_flag, WAIT_LIMIT);
             if (!__all_sync(0xffffffffu, got)) {
@@ -869,11 +890,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                     sum[c] += dv << (8 * t);
                 }
             }
-            if (seg_ii < 0) seg_ii = x.ii;
-            if (x.flush) {
+            if (seg_ii < 0) seg_ii = x_ii;
+            if (x_flush) {
                 // a tile computed whole by this segment is written as C + sum;
                 // pieces of a split tile are added to Z (set to C by the prologue)
-                const bool whole = seg_ii == 0 && x.ii == p.I - 1;
+                const bool whole = seg_ii == 0 && x_ii == p.I - 1;
                 seg_ii = -1;
                 // The warp's 32 rows x ND sums go through shared memory so that
                 // the global accesses run along rows: lane = column (W = 1), or
@@ -887,8 +908,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 constexpr int NIT = 32 / RPI;
                 constexpr int BATCH = NIT;        // addend loads in flight together
                 const int rr = lane / ND, cc = lane % ND;
-                const int64_t n = x.nt * ND + cc;
-                const int64_t mb = x.mt * BM + quad * 32;
+                const int64_t n = (int64_t)u.y * ND + cc;
+                const int64_t mb = (int64_t)u.x * BM + quad * 32;
 #pragma unroll
                 for (int i0 = 0; i0 < NIT; i0 += BATCH) {
                     // a batch of addend loads first, then its stores or atomic adds
