@@ -100,7 +100,7 @@ constexpr int NDRAIN = 128;              // drain threads
 constexpr long long WAIT_LIMIT = 4000000000LL;   // clock cycles (about 2 s)
 constexpr int MAX_STAGES = 8;
 constexpr int NINFO = 4;                 // unit descriptors in flight from the MMA warp to the drain
-constexpr int NBARS = 2 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
+constexpr int NBARS = 4 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
 
 template <int W> struct Layout {
     static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE_BYTES;
@@ -599,6 +599,7 @@ template <int W, int G>
 __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_constant__ TcGroup<G> g) {
     constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND, STAGES = Cfg<W>::STAGES;
     constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
+    constexpr uint32_t A_HALF = A_STAGE / 2;
     using Sum = typename Elem<W>::T;
 
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -609,7 +610,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Layout<W>::OFF_BAR);
     uint64_t* full = bars;
     uint64_t* empty = full + MAX_STAGES;
-    uint64_t* rawFull = empty + MAX_STAGES;
+    // an A stage arrives and is released in two halves (planes 0 .. D/2 - 1 and
+    // D/2 .. D - 1): full / emptyLo for the first half (with the B planes on
+    // full), fullHi / empty for the second (empty also releases the B planes)
+    uint64_t* fullHi = empty + MAX_STAGES;
+    uint64_t* emptyLo = fullHi + MAX_STAGES;
+    uint64_t* rawFull = emptyLo + MAX_STAGES;
     uint64_t* rawEmpty = rawFull + RAW;
     uint64_t* accFull = rawEmpty + RAW;
     uint64_t* accEmpty = accFull + 2;
@@ -641,6 +647,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
         for (int s = 0; s < STAGES; ++s) {
             ptx::mbar_init(&full[s], 1 + NCONV);
             ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&fullHi[s], 1);
+            ptx::mbar_init(&emptyLo[s], 1);
         }
         for (int r = 0; r < RAW; ++r) {
             ptx::mbar_init(&rawFull[r], 1);
@@ -679,21 +687,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
             const uint8_t* src = p.Ap + ((size_t)m_tile * p.S_tot + (size_t)x.ii * p.KD) * A_STAGE;
             for (int j = 0; j < x.nst; ++j, ++it) {
                 const int s = it % STAGES;
-                const bool free_ = ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+                const uint32_t par = ((it / STAGES) & 1) ^ 1;
+                // first half once the MMAs that read the slot's first half are done
+                bool free_ = ptx::mbar_wait(&emptyLo[s], par, abort_flag, WAIT_LIMIT);
                 if (!__all_sync(0xffffffffu, free_)) {
                     if (lane == 0) record_timeout(abort_flag);
                     ok = false;
                     break;
                 }
-                const uint32_t leader = ptx::elect_one();
-                ptx::mbar_arrive_expect_tx_if(leader, &full[s], A_STAGE);
-                ptx::bulk_g2s_if(leader, sA + s * A_STAGE, src + (size_t)j * A_STAGE, A_STAGE, &full[s]);
+                uint32_t leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &full[s], A_HALF);
+                ptx::bulk_g2s_if(leader, sA + s * A_STAGE, src + (size_t)j * A_STAGE, A_HALF, &full[s]);
+                free_ = ptx::mbar_wait(&empty[s], par, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, free_)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &fullHi[s], A_HALF);
+                ptx::bulk_g2s_if(leader, sA + s * A_STAGE + A_HALF, src + (size_t)j * A_STAGE + A_HALF, A_HALF,
+                                 &fullHi[s]);
             }
         }
         // copies still in flight (only possible after a timeout) must land
         // before the CTA's shared memory is released
-        for (int j = max(0, it - STAGES); j < it; ++j)
+        for (int j = max(0, it - STAGES); j < it; ++j) {
             ptx::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, abort_flag, WAIT_LIMIT);
+            ptx::mbar_wait(&fullHi[j % STAGES], (j / STAGES) & 1, abort_flag, WAIT_LIMIT);
+        }
     } else if (warp == W_BPROD) {
         int it = 0;
         bool ok = true;
@@ -829,15 +851,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                     break;
                 }
                 ptx::tc_fence_after();
-                const uint32_t leader = ptx::elect_one();
+                uint32_t leader = ptx::elect_one();
                 const uint64_t bdesc = ptx::smem_desc_kmajor(bBase + s * B_STAGE_BYTES, CORE_LBO, CORE_SBO);
 #pragma unroll
-                for (int i = 0; i < NDIG; ++i) {
+                for (int i = 0; i < NDIG / 2; ++i) {
                     const uint64_t adesc =
                         ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
                     const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
                     ptx::mma_f16_if(leader, tmem + set * NSTACK + i * ND, adesc, bdesc, idesc,
                                     (j == 0 && i == 0) ? 0u : 1u);
+                }
+                ptx::mma_commit_if(leader, &emptyLo[s]);
+                const bool hi = ptx::mbar_wait(&fullHi[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, hi)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                leader = ptx::elect_one();
+#pragma unroll
+                for (int i = NDIG / 2; i < NDIG; ++i) {
+                    const uint64_t adesc =
+                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
+                    const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
+                    ptx::mma_f16_if(leader, tmem + set * NSTACK + i * ND, adesc, bdesc, idesc, 1u);
                 }
                 ptx::mma_commit_if(leader, &empty[s]);
             }
