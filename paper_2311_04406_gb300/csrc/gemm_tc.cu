@@ -29,7 +29,7 @@
 //   * the GEMM streams raw R tiles (16 K x ND elements) with 2-D TMA; four
 //     converter warps turn each into a stacked B operand of 256 rows: rows
 //     ND j .. ND j + ND - 1 hold digit plane j of the ND columns.
-//   * one thread issues, per 16-deep K step, D MMAs:
+//   * one elected lane of the MMA warp issues, per 16-deep K step, D MMAs:
 //     acc[:, ND i : 256] += L_i . [R_0 | ... | R_{D-1-i}], so that the product
 //     L_i . R_j lands in TMEM column block i + j -- the diagonal it belongs to.
 //     Two 256-column accumulator sets alternate, so draining one overlaps
