@@ -353,6 +353,8 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
 
 template <int W, int G>
 __global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ PrologueGroup<G> g) {
+    // the GEMM may be scheduled now: it waits for this grid before reading
+    ptx::grid_dep_launch();
     int gi = 0;
     if constexpr (G > 1) {
         // last layer whose first block is at or before this one
@@ -671,6 +673,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // Launched as a programmatic dependent of the prologue: the set-up above
+    // (barriers, TMEM, the parameter copy) overlaps the prologue's tail; its
+    // digit planes and the pre-set Z are read only after this wait.
+    ptx::grid_dep_wait();
     const int64_t nv = G == 1 ? cta_units(sched_of(g.p[0].U, g.p[0].I, grid), cta)
                               : cta_total(sp, count, grid, cta);   // units of this CTA
 
@@ -1100,7 +1106,20 @@ cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) 
     prologue_kernel<W, G><<<(unsigned)pg.b_off[pg.count], 256, 0, st>>>(pg);
     cudaError_t e = ensure_smem_attr<W, G>();
     if (e != cudaSuccess) return e;
-    ring_gemm_tc_kernel<W, G><<<(unsigned)grid, NTHREADS, Layout<W>::SMEM, st>>>(tg);
+    // programmatic dependent launch: the GEMM's CTAs may start (and set up)
+    // while the prologue finishes; they wait for it in the kernel
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = Layout<W>::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, ring_gemm_tc_kernel<W, G>, tg);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
