@@ -8,6 +8,26 @@
 
 namespace mpcl {
 
+// Launches `kernel` as a programmatic dependent of the kernel before it on
+// `st`: it may be scheduled while that kernel finishes, and it must execute
+// ptx::grid_dep_wait() before it reads anything that kernel (or any earlier
+// one) wrote.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 using u64 = unsigned long long;
 using u128 = unsigned __int128;
 

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "sm100_ptx.cuh"
 
 namespace mpcl {
 
@@ -178,6 +179,7 @@ __device__ __forceinline__ void rows_body(const RowsParams& p, int64_t g, int la
 
 template <int W, int VEC>
 __global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
+    ptx::grid_dep_launch();   // finalize and vec wait for this grid before reading
     rows_body<W, VEC>(p, (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5), threadIdx.x & 31);
 }
 
@@ -199,6 +201,8 @@ __device__ __forceinline__ void finalize_body(int64_t K, int64_t S, const u64* q
 template <int W>
 __global__ void finalize_kernel(int64_t K, int64_t S, const u64* qmb, const u64* qf,
                                 u64* vmb, u64* vf) {
+    ptx::grid_dep_launch();
+    ptx::grid_dep_wait();   // the rows pass's partials
     finalize_body<W>(K, S, qmb, qf, vmb, vf, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                      (int64_t)gridDim.x * blockDim.x);
 }
@@ -277,6 +281,7 @@ __device__ __forceinline__ void vec_body(const VecParams& p, int wpr, int64_t bl
 
 template <int W, int VEC>
 __global__ void __launch_bounds__(NT) vec_kernel(VecParams p, int wpr) {
+    ptx::grid_dep_wait();   // the rows partials and the finalized vectors
     vec_body<W, VEC>(p, wpr, blockIdx.x);
 }
 
@@ -318,6 +323,7 @@ __device__ __forceinline__ void vec_small_body(const VecParams& p, int64_t blk) 
 
 template <int W>
 __global__ void __launch_bounds__(NT) vec_small_kernel(VecParams p) {
+    ptx::grid_dep_wait();
     vec_small_body<W>(p, blockIdx.x);
 }
 
@@ -343,21 +349,25 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
     if (a.K > 0) {
         unsigned fb = (unsigned)((a.K + 255) / 256);
         if (fb > 1024) fb = 1024;
-        finalize_kernel<W><<<fb, 256, 0, st>>>(a.K, sp.S, rp.qmb, rp.qf,
-                                                (u64*)(ws + L.vmb), (u64*)(ws + L.vf));
+        const cudaError_t e = launch_dependent(finalize_kernel<W>, dim3(fb), dim3(256), 0, st, a.K, sp.S,
+                                               (const u64*)rp.qmb, (const u64*)rp.qf, (u64*)(ws + L.vmb),
+                                               (u64*)(ws + L.vf));
+        if (e != cudaSuccess) return e;
     }
     VecParams vp{a.M, a.K, sp.S, a.with_eu, a.alpha, a.E, a.mA, (const u64*)(ws + L.vmb),
                  (const u64*)(ws + L.vf), rp.pmr, rp.pd, rp.pmc, a.mDc, a.Dc};
     if (a.K < SMALL_K) {
-        vec_small_kernel<W><<<(unsigned)((a.M + NT - 1) / NT), NT, 0, st>>>(vp);
+        const cudaError_t e =
+            launch_dependent(vec_small_kernel<W>, dim3((unsigned)((a.M + NT - 1) / NT)), dim3(NT), 0, st, vp);
+        if (e != cudaSuccess) return e;
     } else {
         const int wpr = vec_warps_per_row(a.K);
         const int64_t rpb = WARPS / wpr;
         const unsigned vb = (unsigned)((a.M + rpb - 1) / rpb);
-        if (W == 1 && (a.K % 2) == 0)
-            vec_kernel<W, 2><<<vb, NT, 0, st>>>(vp, wpr);
-        else
-            vec_kernel<W, 1><<<vb, NT, 0, st>>>(vp, wpr);
+        const cudaError_t e = W == 1 && (a.K % 2) == 0
+                                  ? launch_dependent(vec_kernel<W, 2>, dim3(vb), dim3(NT), 0, st, vp, wpr)
+                                  : launch_dependent(vec_kernel<W, 1>, dim3(vb), dim3(NT), 0, st, vp, wpr);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -400,6 +410,7 @@ __device__ __forceinline__ int layer_of(const int64_t* off, int count, int64_t b
 
 template <int W>
 __global__ void __launch_bounds__(NT) rows_group_kernel(const __grid_constant__ CompactGroup g) {
+    ptx::grid_dep_launch();
     const int li = layer_of(g.rb, g.count, blockIdx.x);
     const CompactLayer& L = g.L[li];
     const int64_t task = ((int64_t)blockIdx.x - g.rb[li]) * WARPS + (threadIdx.x >> 5);
@@ -409,6 +420,8 @@ __global__ void __launch_bounds__(NT) rows_group_kernel(const __grid_constant__ 
 
 template <int W>
 __global__ void __launch_bounds__(256) finalize_group_kernel(const __grid_constant__ CompactGroup g) {
+    ptx::grid_dep_launch();
+    ptx::grid_dep_wait();
     const int li = layer_of(g.fb, g.count, blockIdx.x);
     const CompactLayer& L = g.L[li];
     const int64_t nb = g.fb[li + 1] - g.fb[li];
@@ -418,6 +431,7 @@ __global__ void __launch_bounds__(256) finalize_group_kernel(const __grid_consta
 
 template <int W>
 __global__ void __launch_bounds__(NT) vec_group_kernel(const __grid_constant__ CompactGroup g) {
+    ptx::grid_dep_wait();
     const int li = layer_of(g.vb, g.count, blockIdx.x);
     const CompactLayer& L = g.L[li];
     const int64_t blk = (int64_t)blockIdx.x - g.vb[li];
@@ -485,9 +499,11 @@ cudaError_t run_group(const CompactArgs* a, int n, char* const* ws, cudaStream_t
         if (cnt == 0) break;
         g->count = cnt;
         if (g->rb[cnt] > 0) rows_group_kernel<W><<<(unsigned)g->rb[cnt], NT, 0, st>>>(*g);
-        if (g->fb[cnt] > 0) finalize_group_kernel<W><<<(unsigned)g->fb[cnt], 256, 0, st>>>(*g);
-        if (g->vb[cnt] > 0) vec_group_kernel<W><<<(unsigned)g->vb[cnt], NT, 0, st>>>(*g);
-        e = cudaGetLastError();
+        if (g->fb[cnt] > 0)
+            e = launch_dependent(finalize_group_kernel<W>, dim3((unsigned)g->fb[cnt]), dim3(256), 0, st, *g);
+        if (e == cudaSuccess && g->vb[cnt] > 0)
+            e = launch_dependent(vec_group_kernel<W>, dim3((unsigned)g->vb[cnt]), dim3(NT), 0, st, *g);
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     delete g;
     return e;
