@@ -10,6 +10,7 @@
 // for any grid.
 #include "common.cuh"
 #include "kernels.h"
+#include "sm100_ptx.cuh"
 
 namespace mpcl {
 
@@ -45,6 +46,8 @@ __global__ void __launch_bounds__(NT) check_compact_kernel(int64_t M, const u64*
                                                            const u64* chi_hat, const u64* Dc,
                                                            const u64* mDc, u64* cs) {
     using T = typename Elem<W>::T;
+    ptx::grid_dep_launch();
+    ptx::grid_dep_wait();   // launched as a dependent of the kernel before it
     const T a = ld_elem<W>(alpha, 0);
     T acc = 0;
     for (int64_t r = threadIdx.x; r < M; r += NT)
@@ -132,8 +135,11 @@ int64_t batchrec_blocks(int64_t n) {
 
 cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u64* chi_hat,
                                  const u64* Dc, const u64* mDc, u64* cs, cudaStream_t st) {
-    if (words == 1) check_compact_kernel<1><<<1, NT, 0, st>>>(M, alpha, chi_hat, Dc, mDc, cs);
-    else check_compact_kernel<2><<<1, NT, 0, st>>>(M, alpha, chi_hat, Dc, mDc, cs);
+    const cudaError_t e = words == 1 ? launch_dependent(check_compact_kernel<1>, dim3(1), dim3(NT), 0, st, M, alpha,
+                                                        chi_hat, Dc, mDc, cs)
+                                     : launch_dependent(check_compact_kernel<2>, dim3(1), dim3(NT), 0, st, M, alpha,
+                                                        chi_hat, Dc, mDc, cs);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -180,6 +180,7 @@ __device__ __forceinline__ void rows_body(const RowsParams& p, int64_t g, int la
 template <int W, int VEC>
 __global__ void __launch_bounds__(NT) rows_kernel(RowsParams p) {
     ptx::grid_dep_launch();   // finalize and vec wait for this grid before reading
+    ptx::grid_dep_wait();     // launched as a dependent of the kernel before it
     rows_body<W, VEC>(p, (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5), threadIdx.x & 31);
 }
 
@@ -341,10 +342,10 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
     const int64_t tasks = (a.M + a.K) * sp.S;
     if (tasks > 0) {
         const unsigned blocks = (unsigned)((tasks + WARPS - 1) / WARPS);
-        if (W == 1 && (a.N % 2) == 0)
-            rows_kernel<W, 2><<<blocks, NT, 0, st>>>(rp);
-        else
-            rows_kernel<W, 1><<<blocks, NT, 0, st>>>(rp);
+        const cudaError_t e = W == 1 && (a.N % 2) == 0
+                                  ? launch_dependent(rows_kernel<W, 2>, dim3(blocks), dim3(NT), 0, st, rp)
+                                  : launch_dependent(rows_kernel<W, 1>, dim3(blocks), dim3(NT), 0, st, rp);
+        if (e != cudaSuccess) return e;
     }
     if (a.K > 0) {
         unsigned fb = (unsigned)((a.K + 255) / 256);
@@ -411,6 +412,7 @@ __device__ __forceinline__ int layer_of(const int64_t* off, int count, int64_t b
 template <int W>
 __global__ void __launch_bounds__(NT) rows_group_kernel(const __grid_constant__ CompactGroup g) {
     ptx::grid_dep_launch();
+    ptx::grid_dep_wait();
     const int li = layer_of(g.rb, g.count, blockIdx.x);
     const CompactLayer& L = g.L[li];
     const int64_t task = ((int64_t)blockIdx.x - g.rb[li]) * WARPS + (threadIdx.x >> 5);
@@ -498,7 +500,8 @@ cudaError_t run_group(const CompactArgs* a, int n, char* const* ws, cudaStream_t
         }
         if (cnt == 0) break;
         g->count = cnt;
-        if (g->rb[cnt] > 0) rows_group_kernel<W><<<(unsigned)g->rb[cnt], NT, 0, st>>>(*g);
+        if (g->rb[cnt] > 0)
+            e = launch_dependent(rows_group_kernel<W>, dim3((unsigned)g->rb[cnt]), dim3(NT), 0, st, *g);
         if (g->fb[cnt] > 0)
             e = launch_dependent(finalize_group_kernel<W>, dim3((unsigned)g->fb[cnt]), dim3(256), 0, st, *g);
         if (e == cudaSuccess && g->vb[cnt] > 0)

@@ -355,6 +355,8 @@ template <int W, int G>
 __global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ PrologueGroup<G> g) {
     // the GEMM may be scheduled now: it waits for this grid before reading
     ptx::grid_dep_launch();
+    // launched as a dependent of the kernel before it on the stream
+    ptx::grid_dep_wait();
     int gi = 0;
     if constexpr (G > 1) {
         // last layer whose first block is at or before this one
@@ -1103,8 +1105,9 @@ cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) 
         acc += tg.p[j].U;
     }
     tg.grid = pg.grid = grid;
-    prologue_kernel<W, G><<<(unsigned)pg.b_off[pg.count], 256, 0, st>>>(pg);
-    cudaError_t e = ensure_smem_attr<W, G>();
+    cudaError_t e = launch_dependent(prologue_kernel<W, G>, dim3((unsigned)pg.b_off[pg.count]), dim3(256), 0, st, pg);
+    if (e != cudaSuccess) return e;
+    e = ensure_smem_attr<W, G>();
     if (e != cudaSuccess) return e;
     // programmatic dependent launch: the GEMM's CTAs may start (and set up)
     // while the prologue finishes; they wait for it in the kernel
