@@ -65,7 +65,7 @@ namespace {
 #define MPCL_TC_STAGES_W1 4
 #endif
 #ifndef MPCL_TC_RAW
-#define MPCL_TC_RAW 4
+#define MPCL_TC_RAW 8
 #endif
 
 template <int W> struct Cfg;
@@ -85,7 +85,8 @@ template <> struct Cfg<2> {
 constexpr int BM = 128;                  // rows per tile (TMEM lanes)
 constexpr int KS = 16;                   // K per stage (one MMA K step)
 constexpr int NSTACK = 256;              // rows of the stacked B operand (NDIG * ND)
-constexpr int RAW = MPCL_TC_RAW;         // raw R tiles in flight
+constexpr int RAW_ONE = MPCL_TC_RAW;     // raw R tiles in flight, one-layer launches
+constexpr int RAW_GROUP = 4;             // grouped launches (their layer table also takes shared memory)
 constexpr uint32_t A_PLANE_BYTES = BM * KS * 2;            // 4 KB
 constexpr uint32_t B_STAGE_BYTES = NSTACK * KS * 2;        // 8 KB
 constexpr uint32_t RAW_BYTES = 4096;                       // 16 K x (ND * W) words
@@ -100,9 +101,10 @@ constexpr int NDRAIN = 128;              // drain threads
 constexpr long long WAIT_LIMIT = 4000000000LL;   // clock cycles (about 2 s)
 constexpr int MAX_STAGES = 8;
 constexpr int NINFO = 4;                 // unit descriptors in flight from the MMA warp to the drain
-constexpr int NBARS = 4 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
 
-template <int W> struct Layout {
+template <int W, int G = 1> struct Layout {
+    static constexpr int RAW = G == 1 ? RAW_ONE : RAW_GROUP;   // raw tiles in flight
+    static constexpr int NBARS = 4 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
     static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE_BYTES;
     static constexpr uint32_t OFF_B = Cfg<W>::STAGES * A_STAGE;
     static constexpr uint32_t OFF_RAW = OFF_B + Cfg<W>::STAGES * B_STAGE_BYTES;
@@ -602,16 +604,17 @@ __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
 template <int W, int G>
 __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_constant__ TcGroup<G> g) {
     constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND, STAGES = Cfg<W>::STAGES;
-    constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
+    constexpr uint32_t A_STAGE = Layout<W, G>::A_STAGE;
     constexpr uint32_t A_HALF = A_STAGE / 2;
+    constexpr int RAW = Layout<W, G>::RAW;
     using Sum = typename Elem<W>::T;
 
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;
-    uint8_t* sB = smem + Layout<W>::OFF_B;
-    uint8_t* sRaw = smem + Layout<W>::OFF_RAW;
-    uint8_t* sStg = smem + Layout<W>::OFF_STG;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Layout<W>::OFF_BAR);
+    uint8_t* sB = smem + Layout<W, G>::OFF_B;
+    uint8_t* sRaw = smem + Layout<W, G>::OFF_RAW;
+    uint8_t* sStg = smem + Layout<W, G>::OFF_STG;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Layout<W, G>::OFF_BAR);
     uint64_t* full = bars;
     uint64_t* empty = full + MAX_STAGES;
     // an A stage arrives and is released in two halves (planes 0 .. D/2 - 1 and
@@ -629,7 +632,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     // the MMA warp hands each unit's (row tile, column tile, interval, flush |
     // layer << 1) to the drain warps through NINFO slots
-    int4* info = reinterpret_cast<int4*>(smem + Layout<W>::OFF_INFO);
+    int4* info = reinterpret_cast<int4*>(smem + Layout<W, G>::OFF_INFO);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t cta = blockIdx.x;
@@ -1070,7 +1073,7 @@ cudaError_t ensure_smem_attr() {
     if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
     if (dev >= 0 && dev < 64 && smem_set[dev]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Layout<W>::SMEM);
+                                         (int)Layout<W, G>::SMEM);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) smem_set[dev] = true;
     return cudaSuccess;
@@ -1114,7 +1117,7 @@ cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = Layout<W>::SMEM;
+    cfg.dynamicSmemBytes = Layout<W, G>::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1159,6 +1162,15 @@ cudaError_t launch_chunk(const GemmArgs* a, uint8_t* const* Ap, const int* order
 }
 
 constexpr int GSMALL = 16;   // small groups use a kernel with a smaller parameter block
+
+// dynamic shared memory plus the grouped kernels' static layer table stay
+// within the 227 KB a CTA may use (a launch over the limit fails)
+template <int W, int G> constexpr bool fits_smem() {
+    return Layout<W, G>::SMEM + (G > 1 ? G * sizeof(TcParams) : 0) <= 227 * 1024;
+}
+static_assert(fits_smem<1, 1>() && fits_smem<2, 1>() && fits_smem<1, GSMALL>() && fits_smem<2, GSMALL>() &&
+                  fits_smem<1, GMAX>() && fits_smem<2, GMAX>(),
+              "shared memory of a TC GEMM instantiation");
 
 // A layer with units for at least LONG_WAVES waves of the grid gains little
 // from sharing a launch (its last, partial wave is under 2 % of it), and the
