@@ -5,13 +5,15 @@
 //   a5  mZc  = mC.chi + E.(mB.chi) + mA.(F.chi) + alpha * E.(F.chi)
 //       mDc  = mR.chi - mZc,  Dc = D~.chi            (Eq. (compute-zcomptag))
 //
-// Three launches on the caller's stream:
+// Up to three launches on the caller's stream:
 //   1. rows_kernel   one pass over the five N-wide matrices.  A warp owns a
 //                    (row, column-chunk) task: it streams mR, D~, mC (writing
 //                    mZ on the fly) or mB, F, and leaves per-chunk partial
 //                    dot products with chi in the workspace.  Each input word
 //                    is read from HBM exactly once.
-//   2. finalize_kernel  sums the K-side partials into the vectors mB.chi, F.chi.
+//   2. finalize_kernel  sums the K-side partials into the vectors mB.chi, F.chi
+//                    (only when a row is split into several chunks; with one
+//                    chunk the partials are those vectors and vec reads them).
 //   3. vec_kernel    one warp per output row: the two M x K GEMVs over E and
 //                    mA against those vectors, then mZc, mDc and Dc.
 // Every sum is a wrapping sum mod 2^(64 W), so the split into chunks does not
@@ -347,7 +349,10 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
                                   : launch_dependent(rows_kernel<W, 1>, dim3(blocks), dim3(NT), 0, st, rp);
         if (e != cudaSuccess) return e;
     }
-    if (a.K > 0) {
+    // with one chunk per row the K-side partials already are the vectors
+    // mB.chi and F.chi: the vec pass reads them in place, no finalize pass
+    const bool fin = a.K > 0 && sp.S > 1;
+    if (fin) {
         unsigned fb = (unsigned)((a.K + 255) / 256);
         if (fb > 1024) fb = 1024;
         const cudaError_t e = launch_dependent(finalize_kernel<W>, dim3(fb), dim3(256), 0, st, a.K, sp.S,
@@ -355,8 +360,8 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
                                                (u64*)(ws + L.vf));
         if (e != cudaSuccess) return e;
     }
-    VecParams vp{a.M, a.K, sp.S, a.with_eu, a.alpha, a.E, a.mA, (const u64*)(ws + L.vmb),
-                 (const u64*)(ws + L.vf), rp.pmr, rp.pd, rp.pmc, a.mDc, a.Dc};
+    VecParams vp{a.M, a.K, sp.S, a.with_eu, a.alpha, a.E, a.mA, fin ? (const u64*)(ws + L.vmb) : rp.qmb,
+                 fin ? (const u64*)(ws + L.vf) : rp.qf, rp.pmr, rp.pd, rp.pmc, a.mDc, a.Dc};
     if (a.K < SMALL_K) {
         const cudaError_t e =
             launch_dependent(vec_small_kernel<W>, dim3((unsigned)((a.M + NT - 1) / NT)), dim3(NT), 0, st, vp);
@@ -452,7 +457,7 @@ CompactBlocks compact_blocks(int64_t M, int64_t K, int64_t N) {
     if (M == 0) return b;
     const Split sp = choose_split(M, K, N);
     b.rows = ((M + K) * sp.S + WARPS - 1) / WARPS;
-    if (K > 0) {
+    if (K > 0 && sp.S > 1) {   // with one chunk per row there is nothing to finalize
         b.fin = (K + 255) / 256;
         if (b.fin > 1024) b.fin = 1024;
     }
@@ -486,7 +491,10 @@ cudaError_t run_group(const CompactArgs* a, int n, char* const* ws, cudaStream_t
                               (u64*)(w + wl.qmb), (u64*)(w + wl.qf)};
             L.vmb = (u64*)(w + wl.vmb);
             L.vf = (u64*)(w + wl.vf);
-            L.vp = VecParams{x.M, x.K, sp.S, x.with_eu, x.alpha, x.E, x.mA, L.vmb, L.vf, L.rp.pmr, L.rp.pd,
+            // one chunk per row: the vec pass reads the partials in place (no finalize blocks)
+            const bool fin = x.K > 0 && sp.S > 1;
+            L.vp = VecParams{x.M, x.K, sp.S, x.with_eu, x.alpha, x.E, x.mA, fin ? L.vmb : L.rp.qmb,
+                             fin ? L.vf : L.rp.qf, L.rp.pmr, L.rp.pd,
                              L.rp.pmc, x.mDc, x.Dc};
             L.rows_vec2 = (x.N % 2) == 0;
             L.vec_small = x.K < SMALL_K;
@@ -517,7 +525,7 @@ cudaError_t run_group(const CompactArgs* a, int n, char* const* ws, cudaStream_t
 int compact_launches(int64_t M, int64_t K, int64_t N) {
     if (M == 0) return 0;
     Split sp = choose_split(M, K, N);
-    return ((M + K) * sp.S > 0 ? 1 : 0) + (K > 0 ? 1 : 0) + 1;
+    return ((M + K) * sp.S > 0 ? 1 : 0) + (K > 0 && sp.S > 1 ? 1 : 0) + 1;
 }
 
 size_t compact_workspace(int64_t M, int64_t K, int64_t N, int words) {
