@@ -25,7 +25,9 @@
 //   * prologue_kernel writes L as D fp16 digit planes in exactly the shared
 //     memory image the MMA reads (K-major, no swizzle, 8x16-byte core
 //     matrices), one block per (128-row tile, 16-deep K stage), so the GEMM
-//     fetches each A stage with a single bulk TMA copy.  It also sets Z = C.
+//     fetches each A stage with bulk TMA copies (two halves, each with its
+//     own barriers).  It also sets Z = C on the tiles computed in pieces.  The
+//     GEMM is launched as a programmatic dependent of the prologue.
 //   * the GEMM streams raw R tiles (16 K x ND elements) with 2-D TMA; four
 //     converter warps turn each into a stacked B operand of 256 rows: rows
 //     ND j .. ND j + ND - 1 hold digit plane j of the ND columns.
@@ -35,12 +37,15 @@
 //     Two 256-column accumulator sets alternate, so draining one overlaps
 //     MMAs into the other.
 //   * four drain warps read the diagonals with tcgen05.ld, convert them to
-//     integers and add d_t 2^(8t) into wrapping sums, one per output column.
+//     integers and add d_t 2^(8t) into wrapping sums, one per output column;
+//     the MMA warp hands them each unit's tile and flags through shared memory.
 //   * scheduling is persistent: the (output tile, Kd-deep K interval) work
-//     units are split evenly over the CTAs, so a CTA may cover parts of two
-//     tiles.  Each finished tile segment is added into Z with global atomics:
-//     exact and independent of the order of the additions, because addition
-//     mod 2^(64 W) is associative and commutative.
+//     units are dealt to the CTAs in waves of whole tiles, the remainder split
+//     evenly (see the schedule below), so a CTA may cover parts of two tiles.
+//     A tile computed whole is written as C + sum; the segments of a split
+//     tile are added into Z with global atomics: exact and independent of the
+//     order of the additions, because addition mod 2^(64 W) is associative
+//     and commutative.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
