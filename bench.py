@@ -232,7 +232,7 @@ def _host_inputs(layers, seed):
     return out
 
 
-class GpuRun:
+class GpuWorkload:
     def __init__(self, layers, torch, abi, pinned_host=False):
         self.torch, self.abi = torch, abi
         self.layers = layers
@@ -633,7 +633,7 @@ def run_ours(args):
         tc_after = sum(1 for L in shapes if abi.mpc_gemm_path(L) == 1)
         tune = {"shapes": n_tuned, "seconds": time.perf_counter() - t0, "tensor_core_layers": tc_after,
                 "choices": sorted({abi.mpc_autotune_choice(L)[:3] for L in shapes})}
-    run = GpuRun(layers, torch, abi, pinned_host=not args.no_e2e)
+    run = GpuWorkload(layers, torch, abi, pinned_host=not args.no_e2e)
     units = step_units(layers)
     if args.grouped:
         run.setup_grouped()
