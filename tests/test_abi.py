@@ -208,3 +208,14 @@ def test_im2col_validation(lib):
     assert lib.mpc_im2col(R, 1, 1, 1, 1, 5, 1, 1, 0x1000, 0x2000, None) == abi.MPC_E_SHAPE
     assert lib.mpc_im2col(R, 1, 1, 4, 4, 3, 1, 1, 0x1008, 0x2000, None) == abi.MPC_E_ALIGN
     assert lib.mpc_im2col(R, 0, 3, 4, 4, 3, 1, 1, None, None, None) == 0        # empty batch
+
+
+def test_compact_launch_counts(lib):
+    """CompactTag launches: rows + finalize + vec when a row is split into
+    several chunks (the dense layer: M + K rows too few to fill the GPU, N >
+    1024), rows + vec when every row is one chunk (the vec pass then reads the
+    K-side partials in place)."""
+    assert abi.mpc_launch_count(abi.make_layer(128, 4096, 4096), abi.MPC_WS_TAG_COMPACT) == 3
+    assert abi.mpc_launch_count(abi.make_layer(1024, 576, 64), abi.MPC_WS_TAG_COMPACT) == 2
+    assert abi.mpc_launch_count(abi.make_layer(8192, 1024, 4096), abi.MPC_WS_TAG_COMPACT) == 2
+    assert abi.mpc_launch_count(abi.make_layer(0, 8, 8), abi.MPC_WS_TAG_COMPACT) == 0
