@@ -468,16 +468,27 @@ class GpuWorkload:
         """One step with its host copies pipelined: the inputs are copied in
         the order the step consumes them (layer by layer, party by party) on a
         copy stream, each call waits only for its own inputs, and each party's
-        outputs are copied back on a second stream as soon as they exist."""
+        outputs are copied back on a second stream as soon as they exist.  A
+        layer's inputs for the next step are copied as soon as this step's
+        calls on that layer are done (not after the whole step), so the copies
+        of one step overlap the calls of the one before.  Workloads whose
+        layers read other layers' operands (training) wait for the whole
+        previous step instead."""
         torch = self.torch
         st = torch.cuda.current_stream()
         if not hasattr(self, "_h2d_stream"):
             self._h2d_stream, self._d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
         cs, ds = self._h2d_stream, self._d2h_stream
-        cs.wait_stream(st)        # the previous step is done with the buffers
+        prev = getattr(self, "_consumed", None)
+        cross = prev is not None and not self.links
+        if not cross:
+            cs.wait_stream(st)    # the previous step is done with the buffers
         ready = {}
         for i in range(len(self.items)):
             with torch.cuda.stream(cs):
+                if cross:
+                    for p in range(PARTIES):
+                        cs.wait_event(prev[(i, p)])   # the previous step's calls on layer i are done
                 for h, d in self.h2d_by.get((i, "pub"), []):
                     d.copy_(h, non_blocking=True)
                 for p in range(PARTIES):
@@ -487,6 +498,7 @@ class GpuWorkload:
                     ev.record(cs)
                     ready[(i, p)] = ev
         ds.wait_stream(st)
+        consumed = {}
         for i in range(len(self.items)):
             for p in range(PARTIES):
                 st.wait_event(ready[(i, p)])
@@ -495,11 +507,14 @@ class GpuWorkload:
                 self.compact(i, p)
                 done = torch.cuda.Event()
                 done.record(st)
+                consumed[(i, p)] = done
                 ds.wait_event(done)
                 with torch.cuda.stream(ds):
                     for h, d in self.d2h_by[(i, p)]:
                         h.copy_(d, non_blocking=True)
+        # the next step's calls overwrite the outputs only after they are read back
         st.wait_stream(ds)
+        self._consumed = consumed
 
     def h2d(self):
         self._spread(self.h2d_pairs, lambda h, d: d.copy_(h, non_blocking=True))
@@ -794,7 +809,8 @@ def run_ours(args):
                "ms_per_step": e2e_ms, "h2d_bytes_per_step": run.h2d_bytes(),
                "d2h_bytes_per_step": run.d2h_bytes(), "host_buffers": "pinned",
                "copies": "pipelined with the calls (inputs layer by layer and party by party on a copy "
-                         "stream, outputs back as produced)" if pipelined else
+                         "stream, a layer's next inputs as soon as its calls are done, outputs back as "
+                         "produced)" if pipelined else
                          "all inputs, then the step, then all outputs"}
 
     cpu = None
