@@ -232,13 +232,47 @@ def _host_inputs(layers, seed):
     return out
 
 
+def device_inputs(layers, torch, seed=SEED):
+    """The same structure as host_inputs, generated on the device: uniform
+    64-bit words (torch's seeded generator) and keys and combiners uniform in
+    [0, 2^s).  For timing-only records of workloads too large to generate on
+    the host quickly; the values are not those of host_inputs."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    smax = 1 << min(RING.s, 63)
+
+    def words(*dims):
+        return torch.randint(-(1 << 63), (1 << 63) - 1, ring_shape(*dims), dtype=torch.int64, device="cuda",
+                             generator=g)
+
+    def key(*dims):
+        v = torch.zeros(ring_shape(*dims), dtype=torch.int64, device="cuda")
+        lo = torch.randint(0, smax, dims, dtype=torch.int64, device="cuda", generator=g)
+        if RING.words == 1:
+            v.copy_(lo)
+        else:
+            v[..., 0] = lo
+        return v
+
+    out = []
+    for L in layers:
+        M, K, N = L.M, L.K, L.N
+        pub = dict(E=words(M, K), F=words(K, N), Dt=words(M, N), chi=key(N), chi_hat=key(M))
+        parties = [dict(alpha=key(1), A=words(M, K), B=words(K, N), C=words(M, N), mA=words(M, K),
+                        mB=words(K, N), mC=words(M, N), mR=words(M, N)) for _ in range(PARTIES)]
+        out.append((L, pub, parties))
+    return out
+
+
 class GpuWorkload:
-    def __init__(self, layers, torch, abi, pinned_host=False):
+    def __init__(self, layers, torch, abi, pinned_host=False, device_gen=False):
         self.torch, self.abi = torch, abi
         self.layers = layers
         self.stream = torch.cuda.current_stream()
-        hi = host_inputs(layers)
-        t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64))
+        if device_gen and pinned_host:
+            raise ValueError("device-generated inputs have no host copy")
+        hi = device_inputs(layers, torch) if device_gen else host_inputs(layers)
+        t = (lambda a: a) if device_gen else (lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)))
         self.items = []
         self.h2d_pairs = []   # (host pinned, device) for the e2e copy
         self.h2d_by = {}      # (layer, party or "pub") -> its pairs, for the pipelined e2e step
@@ -257,10 +291,14 @@ class GpuWorkload:
             derived = set(self.links[li][1:4]) if li in self.links else set()
             M, K, N = L.M, L.K, L.N
             dpub = {k: t(v).cuda() for k, v in pub.items()}
+            if device_gen:
+                pub.clear()
             dpar = []
             for p, sh in enumerate(parties):
                 lay = abi.make_layer(M, K, N, RING.k, RING.s, p, PARTIES)
                 d = {k: t(v).cuda() for k, v in sh.items()}
+                if device_gen:
+                    sh.clear()
                 d["Z"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
                 d["mZfull"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
                 d["mZ"] = torch.empty(ring_shape(M, N), dtype=torch.int64, device="cuda")
@@ -678,6 +716,7 @@ def run_ours(args):
             ev[k + 1].record(st)
         torch.cuda.synchronize()
     barrier(ws)
+    check_device(abi, "the timed steps")
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = max_over_ranks(total_ms, ws)
@@ -783,6 +822,8 @@ def run_ours(args):
                 "per_unit": "8 w (4MN + 2KN + 2MK) bytes per call", "peak_source": f"{src} hbm_gbs",
                 "traffic": profile_traffic("rows_kernel") if per_group is None else None}
 
+    launches = run.launches_per_step_grouped() if args.grouped else run.launches_per_step()
+
     # end-to-end: the same step through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -808,6 +849,7 @@ def run_ours(args):
         b.record(st)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        check_device(abi, "the end-to-end steps")
         e2e_ms = max_over_ranks(max(a.elapsed_time(b), wall * 1e3), ws) / e2e_steps
         e2e = {"value": ws * units / (e2e_ms / 1e3) / 1e9, "unit": "ring-GMAC/s",
                "ms_per_step": e2e_ms, "h2d_bytes_per_step": run.h2d_bytes(),
@@ -816,6 +858,19 @@ def run_ours(args):
                          "stream, a layer's next inputs as soon as its calls are done, two device buffer "
                          "sets taken in turn, outputs back as produced)" if pipelined else
                          "all inputs, then the step, then all outputs"}
+
+    # the other configurations' records, on one GPU only
+    extras = {}
+    if ws == 1 and args.workload == "cnn" and PROTOCOL == "plain" and PASS == "forward" and not args.no_extras:
+        # drop every reference to the main workload's buffers (bound methods and
+        # the captured graph hold the workload too)
+        run = runs = step_eager = step_fn = graph = None
+        import gc
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        extras["grouped_uneven"] = extra_grouped_uneven(torch, abi, args.warmup)
+        extras["serving"] = extra_serving(torch, abi)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -831,15 +886,7 @@ def run_ours(args):
             "ms_per_step_eager_api": eager_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (uniform ring words from seeded SplitMix64; shapes of the paper's layers)",
-            "config": {"workload": workload + ("" if PROTOCOL == "plain" else f"_truncated_f{TRUNC_F}"),
-                       "protocol": "CompactTag with OptMAC&Trunc (truncated layer)" if PROTOCOL == "trunc"
-                       else "CompactTag (untruncated layer) beside the SPDZ2k full tag",
-                       "layers": [[L.M, L.K, L.N] for L in layers],
-                       "pass": "forward" if PASS == "forward" else
-                       "training: forward + grad X (M,N,K) + grad W (K,M,N) per layer, with device transposes",
-                       "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
-                       "parties": PARTIES, "parallelism": f"replicas x{ws}",
-                       "l2": f"inputs larger than L2 ({run_bytes(layers) / 2**20:.0f} MiB per step > 129 MiB)"},
+            "config": make_config(workload, layers, ws),
             "tag_overhead_ratio": sum_co / sum_fu,
             "per_layer": per_layer,
             "per_group_call": per_group,
@@ -848,16 +895,123 @@ def run_ours(args):
             "ms_per_step_per_layer_calls": per_layer_calls_ms,
             "roofline": roof,
             "compact_hbm_roofline": hbm_roof,
-            "gpu_launches": (run.launches_per_step_grouped() if args.grouped else run.launches_per_step())
-            * args.steps,
+            "gpu_launches": launches * args.steps,
             "clocks": ck.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "device_status": "ok",
         }
+        line.update(extras)
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def make_config(workload, layers, ws) -> dict:
+    """The workload description both arms print (the same keys and values)."""
+    return {"workload": workload + ("" if PROTOCOL == "plain" else f"_truncated_f{TRUNC_F}"),
+            "protocol": "CompactTag with OptMAC&Trunc (truncated layer)" if PROTOCOL == "trunc"
+            else "CompactTag (untruncated layer) beside the SPDZ2k full tag",
+            "layers": [[L.M, L.K, L.N] for L in layers],
+            "pass": "forward" if PASS == "forward" else
+            "training: forward + grad X (M,N,K) + grad W (K,M,N) per layer, with device transposes",
+            "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
+            "parties": PARTIES, "parallelism": f"replicas x{ws}",
+            "l2": f"inputs larger than L2 ({run_bytes(layers) / 2**20:.0f} MiB per step > 129 MiB)"}
+
+
+def check_device(abi, where: str):
+    """A kernel whose bounded wait gave up returned early with wrong outputs
+    and set the library's device flag: such a run reports nothing."""
+    st = abi.mpc_device_status()
+    if st != 0:
+        raise SystemExit(f"bench: {abi.mpc_status_str(st)} during {where}; the results are invalid")
+
+
+# ---------------------------------------------------------------------------
+# records of the other configurations in the default run (one GPU)
+
+EXTRA_STEPS = 10
+
+
+def extra_grouped_uneven(torch, abi, warmup):
+    """256 uneven layers (M in [1, 4096] log-uniform, K and N in {64 .. 4096}),
+    Z_2^64, two parties: the launch table is filled for their shapes, then one
+    step (per party: one grouped share call, one grouped full-tag call, one
+    grouped CompactTag call and the checks) is captured as a CUDA graph and
+    replayed.  Inputs are generated on the device (41 GiB)."""
+    layers = synth.uneven_layers(256)
+    t0 = time.perf_counter()
+    shapes = [abi.make_layer(L.M, L.K, L.N, RING.k, RING.s) for L in layers]
+    tuned = abi.mpc_autotune(shapes)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    tiles = {}
+    for L in shapes:
+        c = abi.mpc_autotune_choice(L)
+        key = "integer pipes" if c[0] == 0 else "tensor cores"
+        tiles[key] = tiles.get(key, 0) + 1
+    run = GpuWorkload(layers, torch, abi, device_gen=True)
+    run.setup_grouped()
+    for _ in range(warmup):
+        run.step_grouped()
+    torch.cuda.synchronize()
+    g = capture(torch, run.step_grouped)
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device()) as ck:
+        ms = timed_steps(torch, g.replay, EXTRA_STEPS)
+    check_device(abi, "the grouped uneven steps")
+    del g
+    sh = time_calls(torch, lambda: run.share_group(1), 50, True, budget_s=0.5)
+    fu = time_calls(torch, lambda: run.full_group(1), 50, True, budget_s=0.5)
+    co = time_calls(torch, lambda: run.compact_group(1), 50, True, budget_s=0.5)
+    check_device(abi, "the grouped uneven calls")
+    units = step_units(layers)
+    rec = {"workload": "uneven256_seeded", "layers": len(layers), "ring": f"Z_2^{RING.bits}",
+           "parties": PARTIES, "steps": EXTRA_STEPS, "ms_per_step": ms,
+           "ring_gmacs": units / (ms / 1e3) / 1e9,
+           "step_launch": "CUDA graph replay of one captured step (grouped persistent launches)",
+           "tag_overhead_ratio": pct(co, 50) / pct(fu, 50),
+           "share_ms_p50": pct(sh, 50), "full_tag_ms_p50": pct(fu, 50), "compact_tag_ms_p50": pct(co, 50),
+           "autotune": {"shapes": tuned, "seconds": tune_s, "choices": tiles},
+           "gpu_launches_per_step": run.launches_per_step_grouped(),
+           "inputs": "device-generated uniform words (41 GiB), resident", "clocks": ck.summary()}
+    del run
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    abi.mpc_autotune_clear()
+    return rec
+
+
+def extra_serving(torch, abi, n_requests=200, load=0.7):
+    """Serving (ResNet-18 / VGG16 requests, batch 1-32, Z_2^128): capacity from
+    a closed-loop run of 48 requests, then n_requests Poisson arrivals at
+    `load` of that capacity; request and tick latency percentiles from the
+    open-loop run."""
+    from paper_2311_04406_gb300.serve import Server, make_requests
+    srv = Server(ring=synth.Z128, mem_budget=96 << 30)
+    srv.run(make_requests(4, 1e9, seed=SEED + 1, all_at_once=True))
+    cap = srv.run(make_requests(48, 1e9, seed=SEED, all_at_once=True))
+    rate = load * cap["requests_per_s"]
+    with Clocks(torch.cuda.current_device()) as ck:
+        st = srv.run(make_requests(n_requests, rate, seed=SEED + 70))
+    rec = {"workload": WORKLOADS["serve"][0], "ring": "Z_2^128 (k=64, s=64)", "party": 0,
+           "capacity_requests_per_s": cap["requests_per_s"], "capacity_ring_gmacs": cap["ring_gmacs"],
+           "offered_fraction": load, "offered_rate_per_s": rate, "requests": st["requests"],
+           "requests_per_s": st["requests_per_s"], "ring_gmacs": st["ring_gmacs"],
+           "latency_ms_p50": st["latency_ms_p50"], "latency_ms_p99": st["latency_ms_p99"],
+           "tick_ms_p50": st["tick_ms_p50"], "tick_ms_p99": st["tick_ms_p99"], "ticks": st["ticks"],
+           "tick_launch": st.get("tick_launch"),
+           "scheduler": "memory-gated FCFS admission (96 GiB arena), one grouped share + tag call per tick "
+                        "over every admitted request's next layer, 2 ticks in flight",
+           "clocks": ck.summary()}
+    del srv
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return rec
 
 
 def abi_path_is_tc(abi, L) -> bool:
@@ -966,10 +1120,9 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64" if RING.words == 1 else "u128 (two u64 words)",
         "data": "synthetic (uniform ring words from seeded SplitMix64)",
-        "config": {"workload": wl_name.format(b=args.batch) + ("_train" if PASS == "train" else ""),
-                   "layers": [[L.M, L.K, L.N] for L in layers],
-                   "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
-                   "parties": PARTIES, "parallelism": "host cores (oracle)"},
+        "config": make_config(wl_name.format(b=args.batch) + ("_train" if PASS == "train" else ""), layers,
+                              int(os.environ.get("WORLD_SIZE", "1"))),
+        "runs_on": "host cores (the oracle), rank 0 alone",
         "cpu_baseline": {"value": value, "unit": "ring-GMAC/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": "per step: share + full tag at the first 1/64 of output rows and "
                                    "the whole CompactTag tag and check, both layers and parties"},
@@ -1046,6 +1199,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time eager API calls instead of graph replay")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the grouped uneven-layer and serving records")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cnn",
                     help="layer set (default: the CNN pair, conv 1024x576x64 + dense 128x4096x4096)")

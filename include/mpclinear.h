@@ -361,10 +361,15 @@ int mpc_gemm_path(const mpc_layer *layer);
  * host query. */
 int mpc_launch_count(const mpc_layer *layer, int which);
 
-/* Synchronous: reads and clears the device flag that a kernel sets when one of
- * its bounded waits gave up (so that it returned instead of hanging).
- * Returns MPC_E_TIMEOUT if it was set since the last query, MPC_OK if not,
- * MPC_E_CUDA if the flag could not be read.  Uses the current device. */
+/* Reads and clears the device flag that a kernel sets when one of its bounded
+ * waits gave up (so that it returned instead of hanging; its outputs are then
+ * wrong).  The read runs on a private non-blocking stream of the library and
+ * returns when it is done: it neither waits for nor orders itself with the
+ * caller's streams, so a kernel still running may set the flag after the read
+ * (the next query reports it).  To cover a given call, query after that call
+ * has completed.  Returns MPC_E_TIMEOUT if the flag was set since the last
+ * query, MPC_OK if not, MPC_E_CUDA if it could not be read.  Uses the current
+ * device. */
 int mpc_device_status(void);
 
 /* Self-test of the bounded device-side wait (no counterpart in the paper):

@@ -9,11 +9,14 @@ marshals numpy arrays into it.
 Storage convention: ring elements of Z_{2^b} are numpy uint64 arrays, shape
 `(..., )` for b <= 64 and `(..., 2)` holding (lo, hi) for 64 < b <= 128.
 
-Parity of every function is pinned in `tests/test_oracle.py` against what the
+Parity of every function is pinned in `tests/test_oracle*.py` against what the
 paper and the mathematics fix (a textbook product on the reduction n=1, the MAC
-relation, closed forms, special cases and tamper detection).  The literal
-mod 2^{k+2s} check (`check_compact_literal`) is parity unpinned: the paper's
-printed form fails on honest inputs, so it is kept only to record that fact.
+relation, closed forms, special cases, cases worked by hand and tamper
+detection).  The sampled checkers `linear_share_at` / `linear_tag_full_at` are
+pinned element by element against the full functions, and the literal
+mod 2^{k+2s} check (`check_compact_literal`) by a hand-worked case at k = s = 4
+and its special cases (`tests/test_oracle_pins.py`); the paper's printed form
+fails on honest inputs, which a test records.
 """
 from __future__ import annotations
 
@@ -182,11 +185,22 @@ def linear_share(bits, party, E, F, A, B, C):
     return out
 
 
+def _positions(M, N, rows, cols):
+    """Sampled positions as int64 arrays; every (row, col) must lie in the M x N output."""
+    rows = np.ascontiguousarray(rows, dtype=np.int64).reshape(-1)
+    cols = np.ascontiguousarray(cols, dtype=np.int64).reshape(-1)
+    if rows.size != cols.size:
+        raise ValueError("rows and cols must have the same length")
+    if rows.size and (rows.min() < 0 or rows.max() >= M or cols.min() < 0 or cols.max() >= N):
+        raise IndexError(f"sampled position outside the {M} x {N} output")
+    return rows, cols
+
+
 def linear_share_at(bits, party, E, F, A, B, C, rows, cols):
+    """a1 at the positions (rows[j], cols[j]) only."""
     M, K = E.shape[:2]
     N = F.shape[1]
-    rows = np.ascontiguousarray(rows, dtype=np.int64)
-    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    rows, cols = _positions(M, N, rows, cols)
     out = _new(bits, rows.size)
     _load().orc_linear_share_at(bits, M, K, N, int(party), _p(E), _p(F), _p(A), _p(B), _p(C),
                                 rows.size, rows.ctypes.data_as(_i64p), cols.ctypes.data_as(_i64p),
@@ -205,10 +219,10 @@ def linear_tag_full(bits, alpha, E, F, mA, mB, mC):
 
 
 def linear_tag_full_at(bits, alpha, E, F, mA, mB, mC, rows, cols):
+    """a2 at the positions (rows[j], cols[j]) only."""
     M, K = E.shape[:2]
     N = F.shape[1]
-    rows = np.ascontiguousarray(rows, dtype=np.int64)
-    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    rows, cols = _positions(M, N, rows, cols)
     out = _new(bits, rows.size)
     _load().orc_linear_tag_full_at(bits, M, K, N, _p(_scalar(alpha, bits)), _p(E), _p(F), _p(mA),
                                    _p(mB), _p(mC), rows.size, rows.ctypes.data_as(_i64p),
@@ -253,7 +267,9 @@ def check_compact(bits, alpha, chi_hat, Dc, mDc):
 
 
 def check_compact_literal(k, s, alpha, chi_hat, Dc, mDc) -> int:
-    """The printed mod 2^{k+2s} form of the check share (parity unpinned)."""
+    """The printed mod 2^{k+2s} form of the check share (Fig. Pi_CompactMatMul
+    verification steps 3-5): alpha_i D^c reduced mod 2^{k+s}, then the chi^
+    combination summed mod 2^{k+2s}."""
     bits = k + s
     M = Dc.shape[0]
     out = np.zeros(2, dtype=np.uint64)

@@ -1318,15 +1318,39 @@ int wait_selftest(long long limit, cudaStream_t st) {
     return v;
 }
 
+namespace {
+__device__ unsigned int g_tc_timeout_taken = 0;
+
+// takes the flag atomically: a wait that gives up while the flag is being
+// read is reported by the next query instead of being lost
+__global__ void take_timeout_kernel() { g_tc_timeout_taken = atomicExch(&g_tc_timeout, 0u); }
+
+// A non-blocking stream per device for the status query, so that reading the
+// flag neither waits for nor orders itself with the caller's streams (a
+// plain cudaMemcpyFromSymbol would run on the legacy default stream and wait
+// for all work queued on blocking streams).
+cudaStream_t status_stream() {
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+        streams[dev] = nullptr;
+    return streams[dev];
+}
+}  // namespace
+
 // Reads and clears the device flag that a bounded wait sets when it gives up.
+// Kernels still running may set it after the read; the next query sees that.
 int tc_timeout_flag(bool* set) {
+    cudaStream_t s = status_stream();
+    if (!s) return -1;
+    take_timeout_kernel<<<1, 1, 0, s>>>();
+    if (cudaGetLastError() != cudaSuccess) return -1;
     unsigned int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_tc_timeout, sizeof(v)) != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbolAsync(&v, g_tc_timeout_taken, sizeof(v), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return -1;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
     *set = v != 0;
-    if (v) {
-        unsigned int z = 0;
-        if (cudaMemcpyToSymbol(g_tc_timeout, &z, sizeof(z)) != cudaSuccess) return -1;
-    }
     return 0;
 }
 

@@ -298,6 +298,12 @@ class Server:
         else:
             a.mpc_linear_tag_grouped(layers, a.MPC_TAG_FULL, tp, ws=ws)
 
+    @staticmethod
+    def _check_device():
+        st = abi.mpc_device_status()
+        if st != 0:
+            raise RuntimeError(f"serving: {abi.mpc_status_str(st)}; the outputs of the retired ticks are invalid")
+
     # -- the loop -------------------------------------------------------------
     def run(self, requests, keep_outputs: bool = False, tag: str = None) -> dict:
         """Serve `requests` to completion; `tag` overrides the server's tag path
@@ -330,9 +336,11 @@ class Server:
         kept = []
 
         def retire(block: bool):
+            retired = False
             while inflight and (block or inflight[0][0].query()):
                 ev, fin = inflight.popleft()
                 ev.synchronize()
+                retired = True
                 t = start.elapsed_time(ev)
                 for r in fin:
                     r.done_ms = t
@@ -349,6 +357,10 @@ class Server:
                     r.region = None
                     finished_all.append(r)
                 block = False
+            if retired:
+                # the retired ticks have completed: a bounded wait that gave up
+                # in one of their kernels has set the library's device flag
+                self._check_device()
 
         while pending or waiting or active or inflight:
             now = time.perf_counter() - t0
@@ -394,6 +406,7 @@ class Server:
             elif pending:
                 time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
         torch.cuda.synchronize()
+        self._check_device()
         makespan_ms = max((r.done_ms for r in finished_all), default=0.0)
         lat = sorted(r.done_ms - 1e3 * r.arrival for r in finished_all)
         ticks = sorted(a.elapsed_time(b) for a, b in tick_ms)

@@ -62,6 +62,7 @@ def _call_share(lib, layer, ptrs):
     return lib.mpc_linear_share(ctypes.byref(layer), *ptrs, None, 0, None)
 
 
+@pytest.mark.hidden_gpu
 def test_validation_rejects_before_launch(lib):
     good = [0x1000] * 6
     L = abi.make_layer(4, 4, 4)
@@ -85,6 +86,7 @@ def test_validation_rejects_before_launch(lib):
     assert lib.mpc_linear_tag(ctypes.byref(L), abi.MPC_TAG_COMPACT, *args, None, 0, None) == -5
 
 
+@pytest.mark.hidden_gpu
 def test_empty_layers_are_noops(lib):
     # zero-sized layers enqueue nothing, so they succeed without a GPU
     L = abi.make_layer(0, 5, 4)
@@ -93,6 +95,7 @@ def test_empty_layers_are_noops(lib):
     assert _call_share(lib, L, [0x1000, None, 0x1000, None, None, None]) == 0
 
 
+@pytest.mark.hidden_gpu
 def test_grouped_host_logic(lib):
     """Grouped calls: workspace and launch counts are the sums over the group;
     invalid groups are rejected before any launch."""
@@ -183,6 +186,7 @@ def test_launch_table_host_logic(lib, tmp_path):
     assert abi.mpc_gemm_path(big) == 1
 
 
+@pytest.mark.hidden_gpu
 def test_lincomb_validation(lib):
     import ctypes
     ring = abi.mpc_ring(32, 32, 1)
@@ -199,6 +203,7 @@ def test_lincomb_validation(lib):
     assert lib.mpc_lincomb(R, 0, 2, c, p, None, None) == 0          # nothing to do, nothing launched
 
 
+@pytest.mark.hidden_gpu
 def test_im2col_validation(lib):
     import ctypes
     ring = abi.mpc_ring(32, 32, 1)
