@@ -685,7 +685,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         tc_after = sum(1 for L in shapes if abi.mpc_gemm_path(L) == 1)
         tune = {"shapes": n_tuned, "seconds": time.perf_counter() - t0, "tensor_core_layers": tc_after,
-                "choices": sorted({abi.mpc_autotune_choice(L)[:3] for L in shapes})}
+                "choices (path, tile rows, swizzle, K split)": sorted(
+                    {(c[0], c[4], c[1], c[2]) for c in (abi.mpc_autotune_choice(L) for L in shapes)})}
     run = GpuWorkload(layers, torch, abi, pinned_host=not args.no_e2e)
     units = step_units(layers)
     if args.grouped:
@@ -950,7 +951,7 @@ def extra_grouped_uneven(torch, abi, warmup):
     tiles = {}
     for L in shapes:
         c = abi.mpc_autotune_choice(L)
-        key = "integer pipes" if c[0] == 0 else "tensor cores"
+        key = "integer pipes" if c[0] == 0 else f"tensor cores, {c[4]}-row tiles"
         tiles[key] = tiles.get(key, 0) + 1
     run = GpuWorkload(layers, torch, abi, device_gen=True)
     run.setup_grouped()

@@ -205,31 +205,38 @@ int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
 
 /*
  * Launch table (autotuner).  The paper has no counterpart: every GEMM path of
- * this library computes the same exact sums, so the choice of path is a
- * matter of speed only.  For each layer shape (ring width, M, K, N) the table
- * holds a choice -- path 1, the tensor-core kernel, with `swizzle` row tiles
- * per tile-order group (1-64); or path 0, the integer-pipe kernels, with a
+ * this library computes the same exact sums, so the choice of path and tile
+ * shape is a matter of speed only.  For each layer shape (ring width, M, K, N)
+ * the table holds a choice -- path 1, the tensor-core kernel, with output
+ * tiles of `tile_rows` rows (128, or 64 for layers of at most 64 rows: an
+ * M = 64 MMA takes as long as an M = 128 one, so the 64-row tile halves only
+ * the shared-memory bytes of the left operand) and `swizzle` row tiles per
+ * tile-order group (1-64); or path 0, the integer-pipe kernels, with a
  * K-split target of `waves` x 152 blocks (0 = default).  Untuned shapes use a
- * built-in rule (tensor cores from 2^22 ring MACs, 2^20 for Z_2^128).  The
- * table is process-wide and thread-safe; workspace sizes do not depend on it.
+ * built-in rule (tensor cores from 2^22 ring MACs, 2^20 for Z_2^128; 64-row
+ * tiles for M <= 64).  The table is process-wide and thread-safe; workspace
+ * sizes do not depend on it.
  *
  * mpc_autotune: for each distinct shape of layers[count], times the
- *   candidates (swizzle 1/4/8/16 on the tensor cores; K-split 1/2/4/8 on the
- *   integer pipes, below 2^31 ring MACs) on `stream` and stores the fastest.
- *   Synchronous; allocates and frees its own scratch operands; do not call it
- *   during stream capture.  Returns the number of shapes tuned, or a status.
+ *   candidates (tile heights 128 and, for M <= 64, 64 rows, each with swizzle
+ *   1/4/8/16 on the tensor cores; K-split 1/2/4/8 on the integer pipes, below
+ *   2^31 ring MACs) on `stream` and stores the fastest.  Synchronous;
+ *   allocates and frees its own scratch operands; do not call it during
+ *   stream capture.  Returns the number of shapes tuned, or a status.
  * mpc_autotune_set: store a choice (MPC_E_MODE if the tensor-core kernel
- *   cannot run the shape, or a value is out of range).
- * mpc_autotune_choice: the choice a call would use now; returns 1 if it comes
- *   from the table, 0 for the built-in rule.
- * mpc_autotune_save / _load: the table as text ("mpclinear-autotune 1", then
- *   "words M K N path swizzle waves" per line); return the number of shapes,
- *   or MPC_E_IO.  Loading merges into the table.
+ *   cannot run the shape with that tile height, or a value is out of range;
+ *   tile_rows is ignored for path 0).
+ * mpc_autotune_choice: the choice a call would use now (tile_rows 0 for path
+ *   0); returns 1 if it comes from the table, 0 for the built-in rule.
+ * mpc_autotune_save / _load: the table as text ("mpclinear-autotune 2", then
+ *   "words M K N path tile_rows swizzle waves" per line; version-1 files
+ *   without tile_rows load as 128-row tiles); return the number of shapes, or
+ *   MPC_E_IO.  Loading merges into the table.
  * mpc_autotune_clear: empties the table; returns the number of shapes removed.
  */
 int mpc_autotune(const mpc_layer *layers, int count, void *stream);
-int mpc_autotune_set(const mpc_layer *layer, int path, int swizzle, int waves);
-int mpc_autotune_choice(const mpc_layer *layer, int *path, int *swizzle, int *waves);
+int mpc_autotune_set(const mpc_layer *layer, int path, int tile_rows, int swizzle, int waves);
+int mpc_autotune_choice(const mpc_layer *layer, int *path, int *tile_rows, int *swizzle, int *waves);
 int mpc_autotune_save(const char *path);
 int mpc_autotune_load(const char *path);
 int mpc_autotune_clear(void);

@@ -126,10 +126,10 @@ def load(build_if_missing: bool = False):
         lib.mpc_launch_count_grouped.restype = ctypes.c_int
         lib.mpc_autotune.argtypes = [L, ctypes.c_int, P]
         lib.mpc_autotune.restype = ctypes.c_int
-        lib.mpc_autotune_set.argtypes = [L, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.mpc_autotune_set.argtypes = [L, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.mpc_autotune_set.restype = ctypes.c_int
         IP = ctypes.POINTER(ctypes.c_int)
-        lib.mpc_autotune_choice.argtypes = [L, IP, IP, IP]
+        lib.mpc_autotune_choice.argtypes = [L, IP, IP, IP, IP]
         lib.mpc_autotune_choice.restype = ctypes.c_int
         lib.mpc_autotune_save.argtypes = [ctypes.c_char_p]
         lib.mpc_autotune_save.restype = ctypes.c_int
@@ -396,17 +396,19 @@ def mpc_autotune(layers, stream=None) -> int:
     return n
 
 
-def mpc_autotune_set(layer, path: int, swizzle: int = 8, waves: int = 0):
-    _check("mpc_autotune_set", load().mpc_autotune_set(ctypes.byref(layer), int(path), int(swizzle), int(waves)))
+def mpc_autotune_set(layer, path: int, swizzle: int = 8, waves: int = 0, tile_rows: int = 128):
+    _check("mpc_autotune_set", load().mpc_autotune_set(ctypes.byref(layer), int(path), int(tile_rows),
+                                                       int(swizzle), int(waves)))
 
 
 def mpc_autotune_choice(layer):
-    """(path, swizzle, waves, tuned) the next call for this layer shape would use."""
-    p, g, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    r = load().mpc_autotune_choice(ctypes.byref(layer), ctypes.byref(p), ctypes.byref(g), ctypes.byref(w))
+    """(path, swizzle, waves, tuned, tile_rows) the next call for this layer shape would use."""
+    p, t, g, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    r = load().mpc_autotune_choice(ctypes.byref(layer), ctypes.byref(p), ctypes.byref(t), ctypes.byref(g),
+                                   ctypes.byref(w))
     if r < 0:
         _check("mpc_autotune_choice", r)
-    return p.value, g.value, w.value, bool(r)
+    return p.value, g.value, w.value, bool(r), t.value
 
 
 def mpc_autotune_save(path: str) -> int:

@@ -66,6 +66,7 @@ int run_gemm(mpcl::GemmArgs g, void* ws, size_t ws_bytes, cudaStream_t st) {
             return MPC_E_WORKSPACE;
         if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return MPC_E_ALIGN;
         g.gm = c.gm;
+        g.rows = c.rows;
         return cuda_status(mpcl::launch_gemm_tc(g, ws, ws_bytes, st));
     }
     g.simt_waves = c.waves;
@@ -76,7 +77,7 @@ int run_gemm(mpcl::GemmArgs g, void* ws, size_t ws_bytes, cudaStream_t st) {
 
 extern "C" {
 
-int mpc_version(void) { return 100; }
+int mpc_version(void) { return 200; }
 
 int mpc_gemm_path(const mpc_layer* L) {
     int st = check_layer(L);
@@ -427,6 +428,7 @@ int run_gemm_group(const mpc_layer* layers, int count, const mpcl::GemmArgs* g, 
         mpcl::GemmArgs x = g[i];
         if (c.path == 1) {
             x.gm = c.gm;
+            x.rows = c.rows;
             tc.push_back(x);
             ap.push_back(cur);
         } else {

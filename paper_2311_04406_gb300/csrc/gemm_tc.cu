@@ -87,12 +87,19 @@ template <> struct Cfg<2> {
     static constexpr int STAGES = 2;
 };
 
-constexpr int BM = 128;                  // rows per tile (TMEM lanes)
+// Output tiles have R = 128 rows (one per TMEM lane) or R = 64 rows.  An
+// M = 64 MMA takes as long as an M = 128 one with the same N (measured on
+// GB300: 588 vs 611 clock cycles for the eight Z_2^64 MMAs of a stage), so a
+// 64-row tile only pays for layers with M <= 64, where it halves the A-plane
+// bytes that every stage moves through shared memory.  Its accumulator
+// occupies lanes 0-15 of each 32-lane TMEM quadrant q, holding rows
+// 16 q .. 16 q + 15 (measured).
+constexpr int BM = 128;                  // rows of the default tile
 constexpr int KS = 16;                   // K per stage (one MMA K step)
 constexpr int NSTACK = 256;              // rows of the stacked B operand (NDIG * ND)
 constexpr int RAW_ONE = MPCL_TC_RAW;     // raw R tiles in flight, one-layer launches
 constexpr int RAW_GROUP = 4;             // grouped launches (their layer table also takes shared memory)
-constexpr uint32_t A_PLANE_BYTES = BM * KS * 2;            // 4 KB
+template <int R> constexpr uint32_t a_plane_bytes() { return (uint32_t)R * KS * 2; }   // 4 or 2 KB
 constexpr uint32_t B_STAGE_BYTES = NSTACK * KS * 2;        // 8 KB
 constexpr uint32_t RAW_BYTES = 4096;                       // 16 K x (ND * W) words
 constexpr uint32_t CORE_LBO = 128;       // next core matrix along K
@@ -107,10 +114,11 @@ constexpr long long WAIT_LIMIT = 4000000000LL;   // clock cycles (about 2 s)
 constexpr int MAX_STAGES = 8;
 constexpr int NINFO = 4;                 // unit descriptors in flight from the MMA warp to the drain
 
-template <int W, int G = 1> struct Layout {
+template <int W, int G = 1, int R = BM> struct Layout {
     static constexpr int RAW = G == 1 ? RAW_ONE : RAW_GROUP;   // raw tiles in flight
     static constexpr int NBARS = 4 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
-    static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE_BYTES;
+    static constexpr uint32_t A_PLANE = a_plane_bytes<R>();
+    static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE;
     static constexpr uint32_t OFF_B = Cfg<W>::STAGES * A_STAGE;
     static constexpr uint32_t OFF_RAW = OFF_B + Cfg<W>::STAGES * B_STAGE_BYTES;
     // epilogue staging: per drain warp 32 rows x (ND + 1) sums (one element
@@ -253,18 +261,19 @@ template <int G> struct PrologueGroup {
     int grid;                 // CTAs of the GEMM launch
 };
 
-// thread `id` of `nthreads` working for one layer
-template <int W>
+// thread `id` of `nthreads` working for one layer (R-row tiles)
+template <int W, int R>
 __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid, int64_t id,
                                               int64_t nthreads) {
     constexpr int NDIG = Cfg<W>::NDIG;
-    constexpr uint32_t A_STAGE = Layout<W>::A_STAGE;
+    constexpr uint32_t A_STAGE = Layout<W, 1, R>::A_STAGE;
+    constexpr uint32_t A_PLANE = Layout<W, 1, R>::A_PLANE;
     {
         // Z = C (0 without an addend) on split tiles: their pieces are added
         // atomically.  A tile one CTA computes whole is written by that CTA.
         // 16-byte vectors: two elements of one row for W = 1 (N is even),
         // one element for W = 2.
-        // Blocks take tiles in turn; a split tile's 128 x ND block is copied by
+        // Blocks take tiles in turn; a split tile's R x ND block is copied by
         // the 256 threads, 16 vectors (ND elements) per row.
         constexpr int ND = Cfg<W>::ND;
         constexpr int VPR = ND * W / 2;                      // 16-byte vectors per tile row
@@ -279,9 +288,9 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
             if (u + p.I <= range_end_of(sc, u)) continue;   // whole: written by its CTA
             int64_t mt, nt;
             tile_mn(t, p.m_tiles, p.n_tiles, p.gm, &mt, &nt);
-            for (int q = tid; q < BM * VPR; q += 256) {
+            for (int q = tid; q < R * VPR; q += 256) {
                 const int r = q / VPR, j = q - r * VPR;
-                const int64_t m = mt * BM + r;
+                const int64_t m = mt * R + r;
                 const int64_t n = nt * ND + (int64_t)j * 2 / W;
                 if (m >= p.M || n >= p.N) continue;
                 const int64_t i = (m * p.N + n) * W / 2;     // vector index
@@ -289,13 +298,14 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
             }
         }
     }
-    const int64_t per_tile = (int64_t)p.S_tot * 256;
-    const int64_t m_tiles = (p.M + BM - 1) / BM;
+    // 2 R threads per (tile, stage): thread = (8-row group rg, K half kg, row r)
+    const int64_t per_tile = (int64_t)p.S_tot * 2 * R;
+    const int64_t m_tiles = (p.M + R - 1) / R;
     if (id >= m_tiles * per_tile) return;
-    const int r = id & 7, kg = (id >> 3) & 1, rg = (id >> 4) & 15;
-    const int64_t kstage = (id >> 8) % p.S_tot;
+    const int r = id & 7, kg = (id >> 3) & 1, rg = (int)((id >> 4) % (R / 8));
+    const int64_t kstage = (id / (2 * R)) % p.S_tot;
     const int64_t mt = id / per_tile;
-    const int64_t m = mt * BM + rg * 8 + r;
+    const int64_t m = mt * R + rg * 8 + r;
     const int64_t kp0 = kstage * KS + kg * 8;      // index in [0, 2 Kp)
     const bool first_half = !p.one_half && kp0 < p.Kp;
     const int64_t kk = (first_half || p.one_half) ? kp0 : kp0 - p.Kp;   // K index of the 8 values
@@ -354,11 +364,11 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
         o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
         o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
         o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
-        *reinterpret_cast<uint4*>(dst + t * A_PLANE_BYTES) = o;
+        *reinterpret_cast<uint4*>(dst + t * A_PLANE) = o;
     }
 }
 
-template <int W, int G>
+template <int W, int G, int R>
 __global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ PrologueGroup<G> g) {
     // the GEMM may be scheduled now: it waits for this grid before reading
     ptx::grid_dep_launch();
@@ -377,7 +387,7 @@ __global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ P
     }
     const int64_t lb = (int64_t)blockIdx.x - g.b_off[gi];
     const int64_t nb = g.b_off[gi + 1] - g.b_off[gi];
-    prologue_body<W>(g.p[gi], g.grid, lb * 256 + threadIdx.x, nb * 256);
+    prologue_body<W, R>(g.p[gi], g.grid, lb * 256 + threadIdx.x, nb * 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -606,20 +616,22 @@ __device__ __forceinline__ void record_timeout(volatile int* abort_flag) {
     atomicExch(&g_tc_timeout, 1u);
 }
 
-template <int W, int G>
+template <int W, int G, int R>
 __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_constant__ TcGroup<G> g) {
+    using Lay = Layout<W, G, R>;
     constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND, STAGES = Cfg<W>::STAGES;
-    constexpr uint32_t A_STAGE = Layout<W, G>::A_STAGE;
+    constexpr uint32_t A_STAGE = Lay::A_STAGE;
+    constexpr uint32_t A_PLANE = Lay::A_PLANE;
     constexpr uint32_t A_HALF = A_STAGE / 2;
-    constexpr int RAW = Layout<W, G>::RAW;
+    constexpr int RAW = Lay::RAW;
     using Sum = typename Elem<W>::T;
 
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;
-    uint8_t* sB = smem + Layout<W, G>::OFF_B;
-    uint8_t* sRaw = smem + Layout<W, G>::OFF_RAW;
-    uint8_t* sStg = smem + Layout<W, G>::OFF_STG;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Layout<W, G>::OFF_BAR);
+    uint8_t* sB = smem + Lay::OFF_B;
+    uint8_t* sRaw = smem + Lay::OFF_RAW;
+    uint8_t* sStg = smem + Lay::OFF_STG;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::OFF_BAR);
     uint64_t* full = bars;
     uint64_t* empty = full + MAX_STAGES;
     // an A stage arrives and is released in two halves (planes 0 .. D/2 - 1 and
@@ -637,7 +649,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     // the MMA warp hands each unit's (row tile, column tile, interval, flush |
     // layer << 1) to the drain warps through NINFO slots
-    int4* info = reinterpret_cast<int4*>(smem + Layout<W, G>::OFF_INFO);
+    int4* info = reinterpret_cast<int4*>(smem + Lay::OFF_INFO);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t cta = blockIdx.x;
@@ -657,18 +669,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            ptx::mbar_init(&full[s], 1 + NCONV);
+            ptx::mbar_init(&full[s], 1 + NCONV / 32);
             ptx::mbar_init(&empty[s], 1);
             ptx::mbar_init(&fullHi[s], 1);
             ptx::mbar_init(&emptyLo[s], 1);
         }
         for (int r = 0; r < RAW; ++r) {
             ptx::mbar_init(&rawFull[r], 1);
-            ptx::mbar_init(&rawEmpty[r], NCONV);
+            ptx::mbar_init(&rawEmpty[r], NCONV / 32);
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&accFull[b], 1);
-            ptx::mbar_init(&accEmpty[b], NDRAIN);
+            ptx::mbar_init(&accEmpty[b], NDRAIN / 32);
         }
         ptx::mbar_init(mmaDone, 1);
         for (int i = 0; i < NINFO; ++i) ptx::mbar_init(&infoFull[i], 1);
@@ -774,12 +786,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     } else if (warp >= W_CONV0 && warp < W_CONV0 + 4) {
         // Each converter thread turns 4 consecutive K values of one column into
         // digit planes (half a core-matrix row per plane): all 8 planes for
-        // Z_2^64, 8 of the 16 planes for Z_2^128.
+        // Z_2^64, 8 of the 16 planes for Z_2^128.  The barriers count one
+        // arrival per converter warp.
         const int ct = threadIdx.x - W_CONV0 * 32;   // 0..127
         int ncol, krow, tlo, boff;
         if constexpr (W == 1) {
+            // A raw tile row is 256 bytes, so every row starts at bank 0: the
+            // four (kg, half) lane groups of a warp read four different
+            // 8-column segments (the warp's segment rotated by 2 kg + half),
+            // which keeps each raw read at two wavefronts; the plane writes
+            // stay at two.
             const int cw = ct >> 5, n8 = lane & 7, half = (lane >> 3) & 1, kg = lane >> 4;
-            ncol = cw * 8 + n8;
+            ncol = ((cw + 2 * kg + half) & 3) * 8 + n8;
             krow = kg * 8 + half * 4;
             tlo = 0;
             boff = (ncol >> 3) * CORE_SBO + kg * CORE_LBO + (ncol & 7) * 16 + half * 8;
@@ -798,27 +816,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
         }
         for (int it = 0; it < total; ++it) {
             const int r = it % RAW;
-            if (!ptx::mbar_wait(&rawFull[r], (it / RAW) & 1, abort_flag, WAIT_LIMIT)) {
-                record_timeout(abort_flag);
+            // warp-uniform decisions: the warp arrives as one
+            if (!__all_sync(0xffffffffu, ptx::mbar_wait(&rawFull[r], (it / RAW) & 1, abort_flag, WAIT_LIMIT))) {
+                if (lane == 0) record_timeout(abort_flag);
                 break;
             }
             const u64* raw = reinterpret_cast<const u64*>(sRaw + r * RAW_BYTES);
             u64 e[4 * W];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int h = 0; h < W; ++h) e[q * W + h] = raw[((krow + q) * ND + ncol) * W + h];
+            for (int q = 0; q < 4; ++q) {
+                if constexpr (W == 1) {
+                    e[q] = raw[(krow + q) * ND + ncol];
+                } else {
+                    // one 16-byte load per element: a warp reads two whole rows
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(raw + ((krow + q) * ND + ncol) * 2);
+                    e[2 * q] = v.x;
+                    e[2 * q + 1] = v.y;
+                }
+            }
             // the next TMA write into this slot is an async-proxy access: order
             // these generic-proxy reads before it (without this fence the TMA
             // overwrote tiles still being read, measured on GB300)
             ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(&rawEmpty[r]);
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&rawEmpty[r]);
             Biased<W> b[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) b[q] = biased<W>(e + q * W);
             const int s = it % STAGES;
-            if (!ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT)) {
-                record_timeout(abort_flag);
+            if (!__all_sync(0xffffffffu,
+                            ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT))) {
+                if (lane == 0) record_timeout(abort_flag);
                 break;
             }
             uint8_t* dst = sB + s * B_STAGE_BYTES + boff;
@@ -833,8 +861,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 // stacked row t * ND + ncol: 8-row group (t * ND) / 8 + ncol / 8
                 *reinterpret_cast<uint2*>(dst + t * (ND / 8) * CORE_SBO) = o;
             }
+            // each thread orders its plane writes before the MMAs (async
+            // proxy); the warp then arrives once
             ptx::fence_proxy_async_smem();
-            ptx::mbar_arrive(&full[s]);
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&full[s]);
         }
     } else if (warp == W_MMA) {
         // The whole warp runs the loop (waits included) and one elected lane
@@ -872,8 +903,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
 #pragma unroll
                 for (int i = 0; i < NDIG / 2; ++i) {
                     const uint64_t adesc =
-                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
-                    const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
+                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE, CORE_LBO, CORE_SBO);
+                    const uint32_t idesc = ptx::idesc_f16_f32(R, (NDIG - i) * ND);
                     ptx::mma_f16_if(leader, tmem + set * NSTACK + i * ND, adesc, bdesc, idesc,
                                     (j == 0 && i == 0) ? 0u : 1u);
                 }
@@ -889,8 +920,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
 #pragma unroll
                 for (int i = NDIG / 2; i < NDIG; ++i) {
                     const uint64_t adesc =
-                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE_BYTES, CORE_LBO, CORE_SBO);
-                    const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
+                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE, CORE_LBO, CORE_SBO);
+                    const uint32_t idesc = ptx::idesc_f16_f32(R, (NDIG - i) * ND);
                     ptx::mma_f16_if(leader, tmem + set * NSTACK + i * ND, adesc, bdesc, idesc, 1u);
                 }
                 ptx::mma_commit_if(leader, &empty[s]);
@@ -932,8 +963,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 ptx::tmem_ld32(base + t0 * ND, f);
                 ptx::tmem_wait_ld();
                 if (t0 + DPL >= NDIG) {
+                    // every lane's loads are complete (wait::ld above); the
+                    // warp releases the accumulator set as one arrival
                     ptx::tc_fence_before();
-                    ptx::mbar_arrive(&accEmpty[set]);
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
                 }
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
@@ -950,20 +984,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 // pieces of a split tile are added to Z (set to C by the prologue)
                 const bool whole = seg_ii == 0 && x_ii == p.I - 1;
                 seg_ii = -1;
-                // The warp's 32 rows x ND sums go through shared memory so that
+                // The warp's rows x ND sums go through shared memory so that
                 // the global accesses run along rows: lane = column (W = 1), or
-                // two rows of 16 columns per instruction (W = 2).
+                // two rows of 16 columns per instruction (W = 2).  Lane l of
+                // quadrant q holds row q RPW + l of the tile; with 64-row tiles
+                // only lanes 0-15 hold rows (RPW = 16).
+                constexpr int RPW = R / 4;      // tile rows per drain warp
                 Sum* stg = reinterpret_cast<Sum*>(sStg) + quad * 32 * (ND + 1);
                 __syncwarp();
 #pragma unroll
                 for (int c = 0; c < ND; ++c) stg[lane * (ND + 1) + c] = sum[c];
                 __syncwarp();
                 constexpr int RPI = 32 / ND;     // rows per instruction
-                constexpr int NIT = 32 / RPI;
+                constexpr int NIT = RPW / RPI;
                 constexpr int BATCH = NIT;        // addend loads in flight together
                 const int rr = lane / ND, cc = lane % ND;
                 const int64_t n = (int64_t)u.y * ND + cc;
-                const int64_t mb = (int64_t)u.x * BM + quad * 32;
+                const int64_t mb = (int64_t)u.x * R + quad * RPW;
 #pragma unroll
                 for (int i0 = 0; i0 < NIT; i0 += BATCH) {
                     // a batch of addend loads first, then its stores or atomic adds
@@ -1000,6 +1037,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     if (warp == W_APROD) ptx::tmem_dealloc(tmem, TMEM_COLS);
 }
 static_assert(Layout<1>::SMEM <= 227 * 1024 && Layout<2>::SMEM <= 227 * 1024, "smem with staging");
+static_assert(Layout<1, 1, 64>::SMEM <= 227 * 1024 && Layout<2, 1, 64>::SMEM <= 227 * 1024, "smem, 64-row tiles");
 
 // ---------------------------------------------------------------------------
 // host side
@@ -1011,12 +1049,16 @@ struct Plan {
     size_t ap_bytes;
 };
 
-Plan make_plan(int64_t M, int64_t K, int64_t N, int words, int one_half = 0) {
+// tile rows of a launch: 64 or 128 (0 and anything else: 128)
+int tile_rows(int rows) { return rows == 64 ? 64 : BM; }
+
+Plan make_plan(int64_t M, int64_t K, int64_t N, int words, int one_half = 0, int rows = BM) {
     Plan pl{};
+    const int R = tile_rows(rows);
     pl.KD = words == 1 ? Cfg<1>::KD : Cfg<2>::KD;
     pl.ND = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
-    const uint32_t a_stage = words == 1 ? Layout<1>::A_STAGE : Layout<2>::A_STAGE;
-    pl.m_tiles = (M + BM - 1) / BM;
+    const uint32_t a_stage = (words == 1 ? Cfg<1>::NDIG : Cfg<2>::NDIG) * (uint32_t)R * KS * 2;
+    pl.m_tiles = (M + R - 1) / R;
     pl.n_tiles = (N + pl.ND - 1) / pl.ND;
     pl.Kp = ((K + KS - 1) / KS) * KS;
     pl.S_tot = (int)((one_half ? 1 : 2) * pl.Kp / KS);
@@ -1071,21 +1113,21 @@ static_assert(sizeof(TcGroup<GMAX>) + 64 <= 32764, "kernel parameter space");
 // The dynamic shared-memory opt-in is set once per device and kernel (a host
 // call that also keeps graph capture free of attribute changes after the
 // first use).
-template <int W, int G>
+template <int W, int G, int R>
 cudaError_t ensure_smem_attr() {
     static bool smem_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
     if (dev >= 0 && dev < 64 && smem_set[dev]) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Layout<W, G>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W, G, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Layout<W, G, R>::SMEM);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) smem_set[dev] = true;
     return cudaSuccess;
 }
 
-// Fills entry j of a group for layer `a` (digit planes at Ap).
-template <int W, int G>
+// Fills entry j of a group for layer `a` (digit planes at Ap, R-row tiles).
+template <int W, int G, int R>
 bool fill(TcGroup<G>& tg, PrologueGroup<G>& pg, int j, const GemmArgs& a, uint8_t* Ap, const Plan& pl) {
     if (!make_map(&tg.tmF[j], a.F, a.K, a.N, W, Cfg<W>::ND)) return false;
     if (a.one_half) tg.tmB[j] = tg.tmF[j];
@@ -1095,11 +1137,12 @@ bool fill(TcGroup<G>& tg, PrologueGroup<G>& pg, int j, const GemmArgs& a, uint8_
                        pl.m_tiles, pl.n_tiles, pl.U, gm, 0};
     pg.p[j] = PrologueParams{a.E, a.X, a.alpha, a.coef, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z,
                              pl.I, pl.m_tiles, pl.n_tiles, gm};
-    pg.b_off[j + 1] = pg.b_off[j] + pl.m_tiles * pl.S_tot;
+    // prologue blocks of 256 threads, 2 R threads per (row tile, stage)
+    pg.b_off[j + 1] = pg.b_off[j] + (pl.m_tiles * pl.S_tot * 2 * R + 255) / 256;
     return true;
 }
 
-template <int W, int G>
+template <int W, int G, int R>
 cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) {
     // one CTA per SM (fewer when the launch has fewer units); each layer's
     // CTA index is rotated by the units of the layers before it
@@ -1113,39 +1156,39 @@ cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) 
         acc += tg.p[j].U;
     }
     tg.grid = pg.grid = grid;
-    cudaError_t e = launch_dependent(prologue_kernel<W, G>, dim3((unsigned)pg.b_off[pg.count]), dim3(256), 0, st, pg);
+    cudaError_t e = launch_dependent(prologue_kernel<W, G, R>, dim3((unsigned)pg.b_off[pg.count]), dim3(256), 0, st, pg);
     if (e != cudaSuccess) return e;
-    e = ensure_smem_attr<W, G>();
+    e = ensure_smem_attr<W, G, R>();
     if (e != cudaSuccess) return e;
     // programmatic dependent launch: the GEMM's CTAs may start (and set up)
     // while the prologue finishes; they wait for it in the kernel
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = Layout<W, G>::SMEM;
+    cfg.dynamicSmemBytes = Layout<W, G, R>::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, ring_gemm_tc_kernel<W, G>, tg);
+    e = cudaLaunchKernelEx(&cfg, ring_gemm_tc_kernel<W, G, R>, tg);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template <int W>
+template <int W, int R>
 cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t st) {
     TcGroup<1> tg{};
     PrologueGroup<1> pg{};
     tg.count = pg.count = 1;
     pg.b_off[0] = 0;
-    if (!fill<W, 1>(tg, pg, 0, a, Ap, pl)) return cudaErrorInvalidValue;
-    return launch_group<W, 1>(tg, pg, st);
+    if (!fill<W, 1, R>(tg, pg, 0, a, Ap, pl)) return cudaErrorInvalidValue;
+    return launch_group<W, 1, R>(tg, pg, st);
 }
 
-// One launch pair for the layers order[i0 .. i0 + cnt) (cnt <= G).
-template <int W, int G>
+// One launch pair for the layers order[i0 .. i0 + cnt) (cnt <= G), R-row tiles.
+template <int W, int G, int R>
 cudaError_t launch_chunk(const GemmArgs* a, uint8_t* const* Ap, const int* order, int cnt, cudaStream_t st) {
     static_assert(alignof(TcGroup<G>) >= 64, "tensor map alignment");
     auto* tg = new (std::nothrow) TcGroup<G>;
@@ -1156,10 +1199,10 @@ cudaError_t launch_chunk(const GemmArgs* a, uint8_t* const* Ap, const int* order
         pg->b_off[0] = 0;
         for (int j = 0; j < cnt && e == cudaSuccess; ++j) {
             const GemmArgs& x = a[order[j]];
-            if (!fill<W, G>(*tg, *pg, j, x, Ap[order[j]], make_plan(x.M, x.K, x.N, W, x.one_half)))
+            if (!fill<W, G, R>(*tg, *pg, j, x, Ap[order[j]], make_plan(x.M, x.K, x.N, W, x.one_half, R)))
                 e = cudaErrorInvalidValue;
         }
-        if (e == cudaSuccess) e = launch_group<W, G>(*tg, *pg, st);
+        if (e == cudaSuccess) e = launch_group<W, G, R>(*tg, *pg, st);
     }
     delete tg;
     delete pg;
@@ -1170,11 +1213,13 @@ constexpr int GSMALL = 16;   // small groups use a kernel with a smaller paramet
 
 // dynamic shared memory plus the grouped kernels' static layer table stay
 // within the 227 KB a CTA may use (a launch over the limit fails)
-template <int W, int G> constexpr bool fits_smem() {
-    return Layout<W, G>::SMEM + (G > 1 ? G * sizeof(TcParams) : 0) <= 227 * 1024;
+template <int W, int G, int R = BM> constexpr bool fits_smem() {
+    return Layout<W, G, R>::SMEM + (G > 1 ? G * sizeof(TcParams) : 0) <= 227 * 1024;
 }
 static_assert(fits_smem<1, 1>() && fits_smem<2, 1>() && fits_smem<1, GSMALL>() && fits_smem<2, GSMALL>() &&
-                  fits_smem<1, GMAX>() && fits_smem<2, GMAX>(),
+                  fits_smem<1, GMAX>() && fits_smem<2, GMAX>() && fits_smem<1, 1, 64>() && fits_smem<2, 1, 64>() &&
+                  fits_smem<1, GSMALL, 64>() && fits_smem<2, GSMALL, 64>() && fits_smem<1, GMAX, 64>() &&
+                  fits_smem<2, GMAX, 64>(),
               "shared memory of a TC GEMM instantiation");
 
 // A layer with units for at least LONG_WAVES waves of the grid gains little
@@ -1183,53 +1228,64 @@ static_assert(fits_smem<1, 1>() && fits_smem<2, 1>() && fits_smem<1, GSMALL>() &
 // GB300 with pairs of long layers): grouped calls launch such layers alone.
 // (At 12 waves VGG16 b16's 15-wave layers ran 6 % slower alone than grouped.)
 constexpr int LONG_WAVES = 64;
-bool long_layer(int64_t M, int64_t K, int64_t N, int words, int one_half, int sms) {
-    return make_plan(M, K, N, words, one_half).U >= (int64_t)LONG_WAVES * sms;
+bool long_layer(int64_t M, int64_t K, int64_t N, int words, int one_half, int sms, int rows = BM) {
+    return make_plan(M, K, N, words, one_half, rows).U >= (int64_t)LONG_WAVES * sms;
 }
 
-// Layers [0, n) in launches of up to GMAX layers; layer i's digit planes at
-// Ap[i].  Every layer is eligible and has the ring width W.
-template <int W>
-cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st) {
+// The layers idx[0 .. n) (all with R-row tiles) in launches of up to GMAX
+// layers; layer i's digit planes at Ap[i].  Every layer is eligible and has
+// the ring width W.
+template <int W, int R>
+cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t* const* Ap, cudaStream_t st) {
     // layers with more K intervals first, so that whole tiles of the long
     // layers line up with the CTAs' ranges (the order changes no result)
-    std::vector<int> order(n);
-    std::vector<int> iv(n);
-    for (int i = 0; i < n; ++i) {
-        order[i] = i;
-        iv[i] = make_plan(a[i].M, a[i].K, a[i].N, W, a[i].one_half).I;
-    }
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return iv[x] > iv[y]; });
+    std::vector<std::pair<int, int>> by_iv;   // (intervals per tile, layer)
+    for (int i : order) by_iv.push_back({make_plan(a[i].M, a[i].K, a[i].N, W, a[i].one_half, R).I, i});
+    std::stable_sort(by_iv.begin(), by_iv.end(),
+                     [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first > y.first; });
+    for (size_t j = 0; j < by_iv.size(); ++j) order[j] = by_iv[j].second;
     cudaError_t e = cudaSuccess;
     const int sms = sm_count();
     std::vector<int> rest;
     for (int i : order) {
-        if (long_layer(a[i].M, a[i].K, a[i].N, W, a[i].one_half, sms)) {
-            if (e == cudaSuccess) e = launch_chunk<W, 1>(a, Ap, &i, 1, st);
+        if (long_layer(a[i].M, a[i].K, a[i].N, W, a[i].one_half, sms, R)) {
+            if (e == cudaSuccess) e = launch_chunk<W, 1, R>(a, Ap, &i, 1, st);
         } else {
             rest.push_back(i);
         }
     }
-    order.swap(rest);
-    n = (int)order.size();
+    const int n = (int)rest.size();
     for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += GMAX) {
         const int cnt = n - i0 < GMAX ? n - i0 : GMAX;
         // a lone layer takes the one-layer kernel (parameters at constant offsets)
-        e = cnt == 1        ? launch_chunk<W, 1>(a, Ap, order.data() + i0, cnt, st)
-            : cnt <= GSMALL ? launch_chunk<W, GSMALL>(a, Ap, order.data() + i0, cnt, st)
-                            : launch_chunk<W, GMAX>(a, Ap, order.data() + i0, cnt, st);
+        e = cnt == 1        ? launch_chunk<W, 1, R>(a, Ap, rest.data() + i0, cnt, st)
+            : cnt <= GSMALL ? launch_chunk<W, GSMALL, R>(a, Ap, rest.data() + i0, cnt, st)
+                            : launch_chunk<W, GMAX, R>(a, Ap, rest.data() + i0, cnt, st);
     }
+    return e;
+}
+
+// Layers [0, n): those with 128-row tiles and those with 64-row tiles in
+// launches of their own (one kernel instantiation per tile height).
+template <int W>
+cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st) {
+    std::vector<int> big, small;
+    for (int i = 0; i < n; ++i) (tile_rows(a[i].rows) == 64 ? small : big).push_back(i);
+    cudaError_t e = cudaSuccess;
+    if (!big.empty()) e = launch_many_rows<W, BM>(a, big, Ap, st);
+    if (e == cudaSuccess && !small.empty()) e = launch_many_rows<W, 64>(a, small, Ap, st);
     return e;
 }
 
 }  // namespace
 
-bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words) {
+bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words, int rows) {
     if (words != 1 && words != 2) return false;
     if (M <= 8 || N < 1 || K < 1) return false;        // skinny layers stream better on the SIMT GEMV
     if (words == 1 && N % 2 != 0) return false;       // TMA row stride: 16-byte multiple
     if (K > (int64_t(1) << 30) || N > (int64_t(1) << 28)) return false;
-    if ((M + BM - 1) / BM > 65535) return false;
+    const int R = tile_rows(rows);
+    if ((M + R - 1) / R > 65535) return false;
     return true;
 }
 
@@ -1240,17 +1296,23 @@ bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
     return macs >= (words == 1 ? (double)(1 << 22) : (double)(1 << 20));
 }
 
+// the digit planes of either tile height fit (a 64-row tiling never needs
+// more than a 128-row one: ceil(M / 64) <= 2 ceil(M / 128))
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half) {
     if (!gemm_tc_feasible(M, K, N, words)) return 0;
-    return align256(make_plan(M, K, N, words, one_half).ap_bytes);
+    size_t b = make_plan(M, K, N, words, one_half, BM).ap_bytes;
+    if (gemm_tc_feasible(M, K, N, words, 64)) b = std::max(b, make_plan(M, K, N, words, one_half, 64).ap_bytes);
+    return align256(b);
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
-    if (!gemm_tc_feasible(a.M, a.K, a.N, a.words)) return cudaErrorNotSupported;
-    Plan pl = make_plan(a.M, a.K, a.N, a.words, a.one_half);
+    const int R = tile_rows(a.rows);
+    if (!gemm_tc_feasible(a.M, a.K, a.N, a.words, R)) return cudaErrorNotSupported;
+    Plan pl = make_plan(a.M, a.K, a.N, a.words, a.one_half, R);
     if (ws_bytes < align256(pl.ap_bytes) || ws == nullptr) return cudaErrorInvalidValue;
     uint8_t* Ap = static_cast<uint8_t*>(ws);
-    return a.words == 1 ? launch<1>(a, Ap, pl, st) : launch<2>(a, Ap, pl, st);
+    if (R == 64) return a.words == 1 ? launch<1, 64>(a, Ap, pl, st) : launch<2, 64>(a, Ap, pl, st);
+    return a.words == 1 ? launch<1, BM>(a, Ap, pl, st) : launch<2, BM>(a, Ap, pl, st);
 }
 
 int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words) {
@@ -1261,7 +1323,7 @@ cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap,
     if (n <= 0) return cudaSuccess;
     const int w = a[0].words;
     for (int i = 0; i < n; ++i)
-        if (a[i].words != w || !gemm_tc_feasible(a[i].M, a[i].K, a[i].N, w) || !Ap[i] ||
+        if (a[i].words != w || !gemm_tc_feasible(a[i].M, a[i].K, a[i].N, w, a[i].rows) || !Ap[i] ||
             reinterpret_cast<uintptr_t>(Ap[i]) % 256 != 0)
             return cudaErrorInvalidValue;
     return w == 1 ? launch_many<1>(a, n, Ap, st) : launch_many<2>(a, n, Ap, st);
@@ -1269,12 +1331,13 @@ cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap,
 
 int gemm_tc_grouped_launches(const int64_t* M, const int64_t* K, const int64_t* N, int n, int words) {
     const int sms = sm_count();
-    int alone = 0, rest = 0;
+    int alone = 0, rest[2] = {0, 0};
     for (int i = 0; i < n; ++i) {
-        if (long_layer(M[i], K[i], N[i], words, 0, sms)) ++alone;
-        else ++rest;
+        const int R = tile_rows(gemm_choice(M[i], K[i], N[i], words).rows);
+        if (long_layer(M[i], K[i], N[i], words, 0, sms, R)) ++alone;
+        else ++rest[R == 64];
     }
-    return 2 * alone + 2 * ((rest + GMAX - 1) / GMAX);
+    return 2 * alone + 2 * ((rest[0] + GMAX - 1) / GMAX) + 2 * ((rest[1] + GMAX - 1) / GMAX);
 }
 
 // ---------------------------------------------------------------------------

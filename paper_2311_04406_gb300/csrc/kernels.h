@@ -30,16 +30,19 @@ struct GemmArgs {
     int one_half;      // 1: Z = C + (X + cE) . F over K only (the public product E.F)
     int gm;            // tensor cores: row tiles per swizzle group (0: default)
     int simt_waves;    // integer pipes: K-split target in waves of 152 blocks (0: default)
+    int rows;          // tensor cores: tile rows, 128 or 64 (0: 128)
 };
 
-// The launch choice of one GEMM shape: path 1 = tensor cores (gm = swizzle
-// width), path 0 = integer pipes (waves = K-split target).  From the autotune
-// table when the shape was tuned (tuned = 1), else the built-in heuristic.
+// The launch choice of one GEMM shape: path 1 = tensor cores (rows = tile
+// height 128 or 64, gm = swizzle width), path 0 = integer pipes (waves =
+// K-split target).  From the autotune table when the shape was tuned
+// (tuned = 1), else the built-in heuristic.
 struct Choice {
     int path;
     int gm;
     int waves;
     int tuned;
+    int rows;
 };
 Choice gemm_choice(int64_t M, int64_t K, int64_t N, int words);
 
@@ -58,7 +61,8 @@ int gemm_tc_grouped_launches(const int64_t* M, const int64_t* K, const int64_t* 
 int wait_selftest(long long limit, cudaStream_t st);
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half = 0);
 bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words);   // heuristic preference
-bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words);   // the kernel can run the shape
+// the kernel can run the shape with `rows`-row tiles (128 or 64)
+bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words, int rows = 128);
 int gemm_tc_launches(int64_t M, int64_t K, int64_t N, int words);
 int tc_timeout_flag(bool* set);   // synchronous; 0 on success
 

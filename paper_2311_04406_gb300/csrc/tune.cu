@@ -3,14 +3,16 @@
 // Every GEMM path computes the same exact sums, so the choice of path and
 // tiling changes only the time a layer takes.  For each layer shape
 // (ring width, M, K, N) the table holds a Choice: the tensor-core kernel with
-// a row-tile swizzle width, or the integer-pipe kernels with a K-split
-// target.  Shapes not in the table use the built-in heuristic
-// (gemm_tc_eligible).  mpc_autotune times the candidates of each distinct
-// shape on the caller's stream and stores the fastest; the table can be saved
-// to and loaded from a text file:
-//     mpclinear-autotune 1
-//     <words> <M> <K> <N> <path> <swizzle> <waves>      (one line per shape)
-// The table is process-wide and guarded by a mutex.
+// a tile height (128 or 64 rows) and a row-tile swizzle width, or the
+// integer-pipe kernels with a K-split target.  Shapes not in the table use
+// the built-in heuristic (gemm_tc_eligible; 64-row tiles for M <= 64).
+// mpc_autotune times the candidates of each distinct shape on the caller's
+// stream and stores the fastest; the table can be saved to and loaded from a
+// text file:
+//     mpclinear-autotune 2
+//     <words> <M> <K> <N> <path> <rows> <swizzle> <waves>   (one line per shape)
+// (version 1 files, without <rows>, load as 128-row tiles).  The table is
+// process-wide and guarded by a mutex.
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -33,9 +35,15 @@ std::map<Key, Choice>& table() {
 }
 
 bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
-    if (c.path == 1) return gemm_tc_feasible(M, K, N, words) && c.gm >= 1 && c.gm <= 64;
+    if (c.path == 1)
+        return (c.rows == 64 || c.rows == 128) && gemm_tc_feasible(M, K, N, words, c.rows) && c.gm >= 1 &&
+               c.gm <= 64;
     return c.path == 0 && c.waves >= 0 && c.waves <= 64;
 }
+
+// Built-in tile height: 64-row tiles where the layer has at most 64 rows (an
+// M = 64 MMA costs as much as an M = 128 one, so they pay only there).
+int default_rows(int64_t M) { return M <= 64 ? 64 : 128; }
 
 }  // namespace
 
@@ -50,6 +58,7 @@ Choice gemm_choice(int64_t M, int64_t K, int64_t N, int words) {
     c.gm = 0;
     c.waves = 0;
     c.tuned = 0;
+    c.rows = c.path == 1 ? default_rows(M) : 0;
     return c;
 }
 
@@ -71,6 +80,7 @@ float time_candidate(const mpcl::GemmArgs& a, const mpcl::Choice& c, void* ws, s
     mpcl::GemmArgs g = a;
     g.gm = c.gm;
     g.simt_waves = c.waves;
+    g.rows = c.rows;
     auto run = [&]() -> cudaError_t {
         return c.path == 1 ? mpcl::launch_gemm_tc(g, ws, ws_bytes, st) : mpcl::launch_gemm_simt(g, st);
     };
@@ -118,11 +128,16 @@ int mpc_autotune(const mpc_layer* layers, int count, void* stream) {
         std::vector<mpcl::Choice> cands;
         const bool tc = mpcl::gemm_tc_feasible(M, K, N, w);
         const double macs = 2.0 * (double)M * (double)K * (double)N;
+        // tile heights: 64 rows only where the layer has at most 64 rows (it
+        // would double the MMA work of taller layers)
         if (tc)
-            for (int gm : {1, 4, 8, 16}) cands.push_back(mpcl::Choice{1, gm, 0, 1});
+            for (int rows : {128, 64}) {
+                if (rows == 64 && (M > 64 || !mpcl::gemm_tc_feasible(M, K, N, w, 64))) continue;
+                for (int gm : {1, 4, 8, 16}) cands.push_back(mpcl::Choice{1, gm, 0, 1, rows});
+            }
         // the integer pipes are far slower on large products: not timed there
         if (!tc || macs < 2147483648.0)
-            for (int wv : {1, 2, 4, 8}) cands.push_back(mpcl::Choice{0, 0, wv, 1});
+            for (int wv : {1, 2, 4, 8}) cands.push_back(mpcl::Choice{0, 0, wv, 1, 0});
         // operands (contents do not matter for the time: every path is exact)
         const size_t e = 8 * (size_t)w;
         const size_t b_mk = e * (size_t)(M * K), b_kn = e * (size_t)(K * N), b_mn = e * (size_t)(M * N);
@@ -173,21 +188,22 @@ int mpc_autotune(const mpc_layer* layers, int count, void* stream) {
     return status == MPC_OK ? tuned : status;
 }
 
-int mpc_autotune_set(const mpc_layer* layer, int path, int swizzle, int waves) {
+int mpc_autotune_set(const mpc_layer* layer, int path, int tile_rows, int swizzle, int waves) {
     int s = check_shape(layer);
     if (s != MPC_OK) return s;
-    mpcl::Choice c{path, swizzle, waves, 1};
+    mpcl::Choice c{path, swizzle, waves, 1, path == 1 ? tile_rows : 0};
     if (!mpcl::choice_ok(c, layer->M, layer->K, layer->N, layer->ring.words)) return MPC_E_MODE;
     std::lock_guard<std::mutex> lk(mpcl::g_mu);
     mpcl::table()[std::make_tuple(layer->ring.words, layer->M, layer->K, layer->N)] = c;
     return MPC_OK;
 }
 
-int mpc_autotune_choice(const mpc_layer* layer, int* path, int* swizzle, int* waves) {
+int mpc_autotune_choice(const mpc_layer* layer, int* path, int* tile_rows, int* swizzle, int* waves) {
     int s = check_shape(layer);
     if (s != MPC_OK) return s;
     const mpcl::Choice c = mpcl::gemm_choice(layer->M, layer->K, layer->N, layer->ring.words);
     if (path) *path = c.path;
+    if (tile_rows) *tile_rows = c.rows;
     if (swizzle) *swizzle = c.gm;
     if (waves) *waves = c.waves;
     return c.tuned ? 1 : 0;
@@ -205,12 +221,12 @@ int mpc_autotune_save(const char* path) {
     FILE* f = std::fopen(path, "w");
     if (!f) return MPC_E_IO;
     std::lock_guard<std::mutex> lk(mpcl::g_mu);
-    std::fprintf(f, "mpclinear-autotune 1\n");
+    std::fprintf(f, "mpclinear-autotune 2\n");
     for (const auto& kv : mpcl::table()) {
         const auto& k = kv.first;
         const auto& c = kv.second;
-        std::fprintf(f, "%d %lld %lld %lld %d %d %d\n", std::get<0>(k), (long long)std::get<1>(k),
-                     (long long)std::get<2>(k), (long long)std::get<3>(k), c.path, c.gm, c.waves);
+        std::fprintf(f, "%d %lld %lld %lld %d %d %d %d\n", std::get<0>(k), (long long)std::get<1>(k),
+                     (long long)std::get<2>(k), (long long)std::get<3>(k), c.path, c.rows, c.gm, c.waves);
     }
     const int n = (int)mpcl::table().size();
     return std::fclose(f) == 0 ? n : MPC_E_IO;
@@ -221,15 +237,19 @@ int mpc_autotune_load(const char* path) {
     FILE* f = std::fopen(path, "r");
     if (!f) return MPC_E_IO;
     int version = 0;
-    if (std::fscanf(f, "mpclinear-autotune %d", &version) != 1 || version != 1) {
+    if (std::fscanf(f, "mpclinear-autotune %d", &version) != 1 || (version != 1 && version != 2)) {
         std::fclose(f);
         return MPC_E_IO;
     }
     std::vector<std::pair<std::tuple<int, int64_t, int64_t, int64_t>, mpcl::Choice>> rows;
-    int w, path_, gm, waves;
+    int w, path_, tr = 128, gm, waves;
     long long M, K, N;
-    while (std::fscanf(f, "%d %lld %lld %lld %d %d %d", &w, &M, &K, &N, &path_, &gm, &waves) == 7) {
-        mpcl::Choice c{path_, gm, waves, 1};
+    auto next = [&]() {
+        if (version == 1) return std::fscanf(f, "%d %lld %lld %lld %d %d %d", &w, &M, &K, &N, &path_, &gm, &waves) == 7;
+        return std::fscanf(f, "%d %lld %lld %lld %d %d %d %d", &w, &M, &K, &N, &path_, &tr, &gm, &waves) == 8;
+    };
+    while (next()) {
+        mpcl::Choice c{path_, gm, waves, 1, path_ == 1 ? tr : 0};
         if ((w != 1 && w != 2) || M < 0 || K < 0 || N < 0 || !mpcl::choice_ok(c, M, K, N, w)) {
             std::fclose(f);
             return MPC_E_IO;

@@ -107,13 +107,17 @@ def test_grouped_host_logic(lib):
     assert ws == sum(-(-abi.mpc_workspace_size(L, abi.MPC_WS_SHARE) // 256) * 256 for L in layers)
     cws = abi.mpc_workspace_size_grouped(layers, abi.MPC_WS_TAG_COMPACT)
     assert cws == sum(-(-abi.mpc_workspace_size(L, abi.MPC_WS_TAG_COMPACT) // 256) * 256 for L in layers)
-    # one prologue + GEMM pair for the three tensor-core layers, one kernel for the other
-    assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_SHARE) == 2 + 1
+    # one prologue + GEMM pair for the two tensor-core layers with 128-row tiles, one for the
+    # layer with 64-row tiles (M = 64), one kernel for the integer-pipe layer
+    assert abi.mpc_autotune_choice(layers[3])[4] == 64
+    assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_SHARE) == 2 + 2 + 1
+    # 60 + 30 tensor-core layers: one launch pair per tile height (at most 64 layers each)
     assert abi.mpc_launch_count_grouped(layers * 30, abi.MPC_WS_TAG_FULL) == 2 * 2 + 30
+    assert abi.mpc_launch_count_grouped(layers[:1] * 65, abi.MPC_WS_TAG_FULL) == 2 * 2
     # a layer with units for >= 64 waves of the grid (2048 x 4096 x 4096: 131072 units) gets a
     # launch pair of its own
     long_ = abi.make_layer(2048, 4096, 4096)
-    assert abi.mpc_launch_count_grouped([long_] + layers, abi.MPC_WS_SHARE) == 2 + 2 + 1
+    assert abi.mpc_launch_count_grouped([long_] + layers, abi.MPC_WS_SHARE) == 2 + 2 + 2 + 1
     # the CompactTag tags of a group: rows, finalize and vec passes, one launch each per 64 layers
     assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_TAG_COMPACT) == 3
     assert abi.mpc_launch_count_grouped(layers * 20, abi.MPC_WS_TAG_COMPACT) == 6
@@ -148,11 +152,14 @@ def test_launch_table_host_logic(lib, tmp_path):
     big = abi.make_layer(128, 4096, 4096)
     small = abi.make_layer(64, 128, 64)
     skinny = abi.make_layer(4, 512, 512)
-    assert abi.mpc_autotune_choice(big) == (1, 0, 0, False)      # built-in rule
+    assert abi.mpc_autotune_choice(big) == (1, 0, 0, False, 128)      # built-in rule
     assert abi.mpc_autotune_choice(small)[0] == 0
+    assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512)) == (1, 0, 0, False, 64)
     ws_before = abi.mpc_workspace_size(small, abi.MPC_WS_SHARE)
     abi.mpc_autotune_set(small, 1, 4, 0)
-    assert abi.mpc_autotune_choice(small) == (1, 4, 0, True)
+    assert abi.mpc_autotune_choice(small) == (1, 4, 0, True, 128)
+    abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=64)
+    assert abi.mpc_autotune_choice(small) == (1, 4, 0, True, 64)
     assert abi.mpc_gemm_path(small) == 1
     assert abi.mpc_workspace_size(small, abi.MPC_WS_SHARE) == ws_before   # independent of the table
     abi.mpc_autotune_set(big, 0, 0, 8)
@@ -164,14 +171,20 @@ def test_launch_table_host_logic(lib, tmp_path):
         abi.mpc_autotune_set(abi.make_layer(64, 64, 63), 1, 8, 0)
     with pytest.raises(abi.MpcError):
         abi.mpc_autotune_set(small, 1, 0, 0)
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=32)      # tile heights: 128 or 64
     f = tmp_path / "table.txt"
     assert abi.mpc_autotune_save(str(f)) == 2
     lines = f.read_text().split("\n")
-    assert lines[0] == "mpclinear-autotune 1" and "1 64 128 64 1 4 0" in lines
+    assert lines[0] == "mpclinear-autotune 2" and "1 64 128 64 1 64 4 0" in lines
     assert abi.mpc_autotune_clear() == 2
     assert abi.mpc_autotune_choice(small)[3] is False
     assert abi.mpc_autotune_load(str(f)) == 2
-    assert abi.mpc_autotune_choice(small) == (1, 4, 0, True)
+    assert abi.mpc_autotune_choice(small) == (1, 4, 0, True, 64)
+    old = tmp_path / "v1.txt"                                    # version 1: no tile height, 128 rows
+    old.write_text("mpclinear-autotune 1\n1 64 128 64 1 8 0\n")
+    assert abi.mpc_autotune_load(str(old)) == 1
+    assert abi.mpc_autotune_choice(small) == (1, 8, 0, True, 128)
     bad = tmp_path / "bad.txt"
     bad.write_text("mpclinear-autotune 1\n1 4 512 512 1 8 0\n")   # tensor cores on M = 4
     with pytest.raises(abi.MpcError):

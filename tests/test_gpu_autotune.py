@@ -1,6 +1,6 @@
-"""The launch table: every choice it can hold (tensor cores with any swizzle
-width, integer pipes with any K split) gives the same bits as the oracle, and
-mpc_autotune fills the table from measured times."""
+"""The launch table: every choice it can hold (tensor cores with either tile
+height and any swizzle width, integer pipes with any K split) gives the same
+bits as the oracle, and mpc_autotune fills the table from measured times."""
 import numpy as np
 import pytest
 
@@ -28,6 +28,7 @@ def operands(ring, M, K, N, seed):
 
 
 CHOICES = [(1, 1, 0), (1, 4, 0), (1, 16, 0), (1, 64, 0), (0, 0, 1), (0, 0, 2), (0, 0, 8)]
+TILE_ROWS = (128, 64)
 
 
 @pytest.mark.parametrize("ring,shape", [(synth.Z64, (300, 200, 96)), (synth.Z64, (1100, 64, 66)),
@@ -39,42 +40,86 @@ def test_every_choice_is_exact(ring, shape):
     want = O.linear_share(ring.bits, 0, E, F, A, B, C)
     L = abi.make_layer(M, K, N, ring.k, ring.s, 0, 2)
     for path, gm, waves in CHOICES:
-        abi.mpc_autotune_set(L, path, gm if path else 0, waves)
-        assert abi.mpc_gemm_path(L) == path
-        Z = empty_like_ring((M, N), ring.words)
-        abi.mpc_linear_share(L, dev(E), dev(F), dev(A), dev(B), dev(C), Z)
-        assert np.array_equal(host(Z), want), (path, gm, waves)
+        for rows in (TILE_ROWS if path else (0,)):
+            abi.mpc_autotune_set(L, path, gm if path else 0, waves, tile_rows=rows or 128)
+            assert abi.mpc_gemm_path(L) == path
+            assert abi.mpc_autotune_choice(L)[4] == rows
+            Z = empty_like_ring((M, N), ring.words)
+            abi.mpc_linear_share(L, dev(E), dev(F), dev(A), dev(B), dev(C), Z)
+            assert np.array_equal(host(Z), want), (path, rows, gm, waves)
     abi.mpc_autotune_clear()
     assert abi.mpc_device_status() == 0
 
 
-def test_grouped_with_mixed_choices():
-    ring = synth.Z64
-    shapes = [(300, 200, 96), (1100, 64, 66), (64, 256, 256), (520, 128, 130)]
-    layers = [abi.make_layer(M, K, N) for M, K, N in shapes]
-    for L, (path, gm, waves) in zip(layers, [(1, 1, 0), (0, 0, 4), (1, 16, 0), (1, 4, 0)]):
-        abi.mpc_autotune_set(L, path, gm, waves)
+# ragged heights around both tile heights (M <= 8 runs on the integer pipes
+# only), ragged K (one partial 16-deep stage; a K below one stage) and N
+@pytest.mark.parametrize("ring", [synth.Z64, synth.Z128], ids=["w1", "w2"])
+@pytest.mark.parametrize("M", [9, 17, 63, 64, 65, 130])
+def test_both_tile_heights_are_exact(ring, M):
+    for K, N in ((27, 34), (300, 96), (5, 66)):
+        E, F, A, B, C = operands(ring, M, K, N, 1000 * M + K)
+        mA, mB, mC = operands(ring, M, K, N, 2000 * M + K)[2:]
+        alpha = synth.uniform(M, 9, 0, (1,), ring.bits)
+        want_z = O.linear_share(ring.bits, 0, E, F, A, B, C)
+        want_t = O.linear_tag_full(ring.bits, alpha, E, F, mA, mB, mC)
+        L = abi.make_layer(M, K, N, ring.k, ring.s, 0, 2)
+        for rows in TILE_ROWS:
+            for gm in (1, 8):
+                abi.mpc_autotune_set(L, 1, gm, 0, tile_rows=rows)
+                Z = empty_like_ring((M, N), ring.words)
+                abi.mpc_linear_share(L, dev(E), dev(F), dev(A), dev(B), dev(C), Z)
+                assert np.array_equal(host(Z), want_z), (M, K, N, rows, gm)
+                mZ = empty_like_ring((M, N), ring.words)
+                abi.mpc_linear_tag(L, abi.MPC_TAG_FULL, dev(alpha), dev(E), dev(F), dev(mA), dev(mB), dev(mC), mZ)
+                assert np.array_equal(host(mZ), want_t), (M, K, N, rows, gm, "tag")
+        abi.mpc_autotune_clear()
+    assert abi.mpc_device_status() == 0
+
+
+def test_built_in_rule_takes_64_row_tiles_for_short_layers():
+    abi.mpc_autotune_clear()
+    assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512))[::4] == (1, 64)
+    assert abi.mpc_autotune_choice(abi.make_layer(65, 4608, 512))[::4] == (1, 128)
+    assert abi.mpc_autotune_choice(abi.make_layer(16, 2304, 512, 64, 64))[::4] == (1, 64)
+
+
+@pytest.mark.parametrize("ring", [synth.Z64, synth.Z128], ids=["w1", "w2"])
+def test_grouped_with_mixed_choices(ring):
+    """One grouped call over layers with 128-row tiles, 64-row tiles and the
+    integer pipes (the tensor-core layers of each tile height share a
+    persistent launch)."""
+    shapes = [(300, 200, 96), (1100, 64, 66), (64, 256, 256), (520, 128, 130), (40, 300, 96), (17, 1000, 34),
+              (64, 27, 64), (130, 600, 66)]
+    choices = [(1, 1, 0, 128), (0, 0, 4, 0), (1, 16, 0, 64), (1, 4, 0, 128), (1, 8, 0, 64), (1, 1, 0, 64),
+               (1, 8, 0, 128), (1, 8, 0, 64)]
+    layers = [abi.make_layer(M, K, N, ring.k, ring.s) for M, K, N in shapes]
+    for L, (path, gm, waves, rows) in zip(layers, choices):
+        abi.mpc_autotune_set(L, path, gm, waves, tile_rows=rows or 128)
     data = [operands(ring, M, K, N, 7 * M + K) for M, K, N in shapes]
-    Zs = [empty_like_ring((M, N), 1) for M, K, N in shapes]
+    Zs = [empty_like_ring((M, N), ring.words) for M, K, N in shapes]
     abi.mpc_linear_share_grouped(layers, [dict(E=dev(E), F=dev(F), A_i=dev(A), B_i=dev(B), C_i=dev(C), Z_i=Z)
                                           for (E, F, A, B, C), Z in zip(data, Zs)])
-    for (E, F, A, B, C), Z in zip(data, Zs):
-        assert np.array_equal(host(Z), O.linear_share(64, 0, E, F, A, B, C))
+    for (E, F, A, B, C), Z, sh in zip(data, Zs, shapes):
+        assert np.array_equal(host(Z), O.linear_share(ring.bits, 0, E, F, A, B, C)), sh
     abi.mpc_autotune_clear()
+    assert abi.mpc_device_status() == 0
 
 
 def test_autotune_fills_the_table(tmp_path):
     abi.mpc_autotune_clear()
     layers = [abi.make_layer(M, K, N) for M, K, N in [(1024, 576, 64), (128, 1024, 1024), (4, 512, 512),
-                                                        (1024, 576, 64)]]
-    assert abi.mpc_autotune(layers) == 3
+                                                        (1024, 576, 64), (32, 4608, 512)]]
+    assert abi.mpc_autotune(layers) == 4
     for L in layers:
-        path, gm, waves, tuned = abi.mpc_autotune_choice(L)
+        path, gm, waves, tuned, rows = abi.mpc_autotune_choice(L)
         assert tuned
         assert path in (0, 1)
+        assert rows == (0 if path == 0 else rows) and rows in (0, 64, 128)
     assert abi.mpc_autotune_choice(layers[2])[0] == 0      # M <= 8: integer pipes only
     f = tmp_path / "t.txt"
-    assert abi.mpc_autotune_save(str(f)) == 3
+    assert abi.mpc_autotune_save(str(f)) == 4
+    saved = {tuple(abi.mpc_autotune_choice(L)) for L in layers}
     abi.mpc_autotune_clear()
-    assert abi.mpc_autotune_load(str(f)) == 3
+    assert abi.mpc_autotune_load(str(f)) == 4
+    assert {tuple(abi.mpc_autotune_choice(L)) for L in layers} == saved
     abi.mpc_autotune_clear()
