@@ -199,6 +199,24 @@ int mpc_linear_tag_grouped(const mpc_layer *layers, int count, int mode, const m
  * arguments (as mpc_workspace_size). */
 size_t mpc_workspace_size_grouped(const mpc_layer *layers, int count, int which);
 
+/*
+ * a6 for many layers at once: the compact check share of each layer, exactly
+ * as mpc_tag_check(layer, MPC_CHECK_COMPACT, ...) computes it (Fig.
+ * Pi_CompactMatMul verification steps 3-5, reduced mod 2^(k+s)):
+ *     cs_i = sum_r chi^_r (alpha_i Dc_r - mDc_{i,r}),  r < M of that layer.
+ * layers[count], ptrs[count]: HOST arrays read during the call; every layer
+ * in one ring (MPC_E_RING otherwise); per layer alpha_i (1 element), chi_hat,
+ * Dc, mDc_i (M elements) and cs_i (1 element, output) are device pointers,
+ * 16-byte aligned.  One kernel per 64 layers, no workspace.  Batching only:
+ * the paper checks layer by layer.
+ */
+typedef struct {
+    const uint64_t *alpha_i, *chi_hat, *Dc, *mDc_i;
+    uint64_t *cs_i;
+} mpc_check_ptrs;
+
+int mpc_tag_check_grouped(const mpc_layer *layers, int count, const mpc_check_ptrs *ptrs, void *stream);
+
 /* Kernels one grouped call enqueues (which as above); negative on invalid
  * arguments. */
 int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
@@ -211,23 +229,25 @@ int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
  * tiles of `tile_rows` rows (128, or 64 for layers of at most 64 rows: an
  * M = 64 MMA takes as long as an M = 128 one, so the 64-row tile halves only
  * the shared-memory bytes of the left operand) and `swizzle` row tiles per
- * tile-order group (1-64); or path 0, the integer-pipe kernels, with a
- * K-split target of `waves` x 152 blocks (0 = default).  Untuned shapes use a
- * built-in rule (tensor cores from 2^22 ring MACs, 2^20 for Z_2^128; 64-row
- * tiles for M <= 64).  The table is process-wide and thread-safe; workspace
+ * tile-order group (1-64); or path 0, the integer-pipe kernels, with tiles
+ * of `tile_rows` rows (64 or 16; 0 = 16 when 64-row tiles would give fewer
+ * blocks than SMs, else 64; skinny layers with M <= 8 use a GEMV whatever the
+ * value) and a K-split target of `waves` x 152 blocks (0 = default).  Untuned
+ * shapes use a built-in rule (tensor cores from 2^22 ring MACs, 2^20 for
+ * Z_2^128; 64-row tensor-core tiles for M <= 64).  The table is process-wide and thread-safe; workspace
  * sizes do not depend on it.
  *
  * mpc_autotune: for each distinct shape of layers[count], times the
  *   candidates (tile heights 128 and, for M <= 64, 64 rows, each with swizzle
- *   1/4/8/16 on the tensor cores; K-split 1/2/4/8 on the integer pipes, below
- *   2^31 ring MACs) on `stream` and stores the fastest.  Synchronous;
+ *   1/4/8/16 on the tensor cores; tile heights 64 and 16 with K-split 1/2/4/8
+ *   on the integer pipes, below 2^31 ring MACs) on `stream` and stores the
+ *   fastest.  Synchronous;
  *   allocates and frees its own scratch operands; do not call it during
  *   stream capture.  Returns the number of shapes tuned, or a status.
  * mpc_autotune_set: store a choice (MPC_E_MODE if the tensor-core kernel
- *   cannot run the shape with that tile height, or a value is out of range;
- *   tile_rows is ignored for path 0).
- * mpc_autotune_choice: the choice a call would use now (tile_rows 0 for path
- *   0); returns 1 if it comes from the table, 0 for the built-in rule.
+ *   cannot run the shape with that tile height, or a value is out of range).
+ * mpc_autotune_choice: the choice a call would use now; returns 1 if it comes
+ *   from the table, 0 for the built-in rule.
  * mpc_autotune_save / _load: the table as text ("mpclinear-autotune 2", then
  *   "words M K N path tile_rows swizzle waves" per line; version-1 files
  *   without tile_rows load as 128-row tiles); return the number of shapes, or
@@ -294,6 +314,14 @@ int mpc_batchrec_mask(const mpc_ring *ring, int64_t rows, int64_t cols,
  */
 int mpc_lincomb(const mpc_ring *ring, int64_t n, int count, const int64_t *coef,
                 const uint64_t *const *in, uint64_t *out, void *stream);
+
+/* `groups` linear combinations with the same coefficients in one launch per
+ * 64 groups: out[g] = sum_j coef[j] * in[g * count + j] over n[g] elements
+ * (1 <= count <= 4; n, in and out are host arrays of sizes and device
+ * pointers).  The arithmetic of mpc_lincomb for each group; the groups must
+ * not overlap one another's outputs (they run concurrently).  No workspace. */
+int mpc_lincomb_grouped(const mpc_ring *ring, int groups, const int64_t *n, int count, const int64_t *coef,
+                        const uint64_t *const *in, uint64_t *const *out, void *stream);
 
 /*
  * im2col view of a convolution (§2.6): for a batch of `channels` x height x

@@ -33,7 +33,8 @@ ABI_FUNCTIONS = ("mpc_linear_share", "mpc_linear_tag", "mpc_tag_check", "mpc_wor
                  "mpc_optmac_trunc", "mpc_batchrec_mask", "mpc_transpose",
                  "mpc_linear_share_grouped", "mpc_linear_tag_grouped", "mpc_workspace_size_grouped",
                  "mpc_launch_count_grouped", "mpc_autotune", "mpc_autotune_set", "mpc_autotune_choice",
-                 "mpc_autotune_save", "mpc_autotune_load", "mpc_autotune_clear", "mpc_selftest_wait", "mpc_lincomb", "mpc_im2col")
+                 "mpc_autotune_save", "mpc_autotune_load", "mpc_autotune_clear", "mpc_selftest_wait", "mpc_lincomb", "mpc_im2col",
+                 "mpc_tag_check_grouped", "mpc_lincomb_grouped")
 (MPC_E_NULL, MPC_E_SHAPE, MPC_E_RING, MPC_E_ALIGN, MPC_E_WORKSPACE, MPC_E_CUDA, MPC_E_MODE, MPC_E_PARTY,
  MPC_E_TIMEOUT, MPC_E_SCRATCH_LIMIT, MPC_E_IO) = range(-1, -12, -1)
 MPC_NOALLOC_SCRATCH_BYTES = 4 << 20
@@ -58,6 +59,13 @@ class mpc_share_ptrs(ctypes.Structure):
 
 class mpc_tag_ptrs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in TAG_PTR_FIELDS]
+
+
+CHECK_PTR_FIELDS = ("alpha_i", "chi_hat", "Dc", "mDc_i", "cs_i")
+
+
+class mpc_check_ptrs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in CHECK_PTR_FIELDS]
 
 
 class MpcError(RuntimeError):
@@ -110,6 +118,12 @@ def load(build_if_missing: bool = False):
         lib.mpc_lincomb.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_void_p), P, P]
         lib.mpc_lincomb.restype = ctypes.c_int
+        lib.mpc_lincomb_grouped.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), P]
+        lib.mpc_lincomb_grouped.restype = ctypes.c_int
+        lib.mpc_tag_check_grouped.argtypes = [L, ctypes.c_int, ctypes.POINTER(mpc_check_ptrs), P]
+        lib.mpc_tag_check_grouped.restype = ctypes.c_int
         lib.mpc_im2col.argtypes = [ctypes.POINTER(mpc_ring)] + [ctypes.c_int64] * 4 + [ctypes.c_int] * 3 + [P, P, P]
         lib.mpc_im2col.restype = ctypes.c_int
         lib.mpc_transpose.argtypes = [ctypes.POINTER(mpc_ring), ctypes.c_int64, ctypes.c_int64, P, P, P]
@@ -316,6 +330,34 @@ def mpc_lincomb(k, s, coefs, ins, out, stream=None):
     return out
 
 
+def mpc_lincomb_grouped(k, s, coefs, ins, outs, stream=None):
+    """outs[g] = sum_j coefs[j] * ins[g][j] for every group g (one launch per 64 groups)."""
+    ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
+    G = len(outs)
+    if G == 0:
+        return outs
+    cnt = len(coefs)
+    n = (ctypes.c_int64 * G)(*[o.numel() // ring.words for o in outs])
+    c = (ctypes.c_int64 * cnt)(*[int(x) for x in coefs])
+    p = (ctypes.c_void_p * (G * cnt))(*[_ptr(t) for g in ins for t in g])
+    o = (ctypes.c_void_p * G)(*[_ptr(t) for t in outs])
+    _check("mpc_lincomb_grouped", load().mpc_lincomb_grouped(ctypes.byref(ring), G, n, cnt, c, p, o,
+                                                             _stream(stream)))
+    return outs
+
+
+def mpc_tag_check_grouped(layers, ptrs, stream=None):
+    """Compact check shares of many layers: ptrs[i] is a dict of CHECK_PTR_FIELDS tensors."""
+    if not layers:
+        return
+    arr = (mpc_layer * len(layers))(*layers)
+    pa = (mpc_check_ptrs * len(layers))()
+    for i, d in enumerate(ptrs):
+        for f in CHECK_PTR_FIELDS:
+            setattr(pa[i], f, _ptr(d[f]))
+    _check("mpc_tag_check_grouped", load().mpc_tag_check_grouped(arr, len(layers), pa, _stream(stream)))
+
+
 def mpc_im2col(k, s, batch, channels, height, width, f, pad, stride, src, dst, stream=None):
     """dst = the im2col matrix of NCHW images src for an f x f filter (zero padding, stride)."""
     ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
@@ -396,7 +438,11 @@ def mpc_autotune(layers, stream=None) -> int:
     return n
 
 
-def mpc_autotune_set(layer, path: int, swizzle: int = 8, waves: int = 0, tile_rows: int = 128):
+def mpc_autotune_set(layer, path: int, swizzle: int = 8, waves: int = 0, tile_rows: int = None):
+    """tile_rows: 128 or 64 for the tensor cores (default 128); 64, 16 or 0 (by grid size) for the
+    integer pipes (default 0)."""
+    if tile_rows is None:
+        tile_rows = 128 if path == 1 else 0
     _check("mpc_autotune_set", load().mpc_autotune_set(ctypes.byref(layer), int(path), int(tile_rows),
                                                        int(swizzle), int(waves)))
 

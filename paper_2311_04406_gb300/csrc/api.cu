@@ -70,6 +70,7 @@ int run_gemm(mpcl::GemmArgs g, void* ws, size_t ws_bytes, cudaStream_t st) {
         return cuda_status(mpcl::launch_gemm_tc(g, ws, ws_bytes, st));
     }
     g.simt_waves = c.waves;
+    g.rows = c.rows;
     return cuda_status(mpcl::launch_gemm_simt(g, st));
 }
 
@@ -180,6 +181,21 @@ int mpc_lincomb(const mpc_ring* ring, int64_t n, int count, const int64_t* coef,
     CHK(check_ptr(out, n));
     return cuda_status(mpcl::launch_lincomb(n, ring->words, count, coef, (const u64* const*)in, (u64*)out,
                                             (cudaStream_t)stream));
+}
+
+int mpc_lincomb_grouped(const mpc_ring* ring, int groups, const int64_t* n, int count, const int64_t* coef,
+                        const uint64_t* const* in, uint64_t* const* out, void* stream) {
+    if (groups < 0 || count < 1 || count > mpcl::LINCOMB_GROUP_TERMS) return MPC_E_SHAPE;
+    if (groups == 0) return MPC_OK;
+    if (!ring || !coef || !in || !out || !n) return MPC_E_NULL;
+    if (!ring_ok(*ring)) return MPC_E_RING;
+    for (int g = 0; g < groups; ++g) {
+        if (n[g] < 0 || n[g] > kMaxElems) return MPC_E_SHAPE;
+        for (int j = 0; j < count; ++j) CHK(check_ptr(in[(size_t)g * count + j], n[g]));
+        CHK(check_ptr(out[g], n[g]));
+    }
+    return cuda_status(mpcl::launch_lincomb_grouped(groups, n, ring->words, count, coef, (const u64* const*)in,
+                                                    (u64* const*)out, (cudaStream_t)stream));
 }
 
 int mpc_im2col(const mpc_ring* ring, int64_t batch, int64_t channels, int64_t height, int64_t width, int f,
@@ -433,6 +449,7 @@ int run_gemm_group(const mpc_layer* layers, int count, const mpcl::GemmArgs* g, 
             ap.push_back(cur);
         } else {
             x.simt_waves = c.waves;
+            x.rows = c.rows;
             simt.push_back(x);
         }
         cur += (mpcl::gemm_tc_workspace(g[i].M, g[i].K, g[i].N, g[i].words) + 255) & ~size_t(255);
@@ -566,6 +583,34 @@ int mpc_launch_count_grouped(const mpc_layer* layers, int count, int which) {
         return mpcl::compact_grouped_launches(M.data(), K.data(), N.data(), count);
     }
     return n + mpcl::gemm_tc_grouped_launches(tM.data(), tK.data(), tN.data(), (int)tM.size(), layers[0].ring.words);
+}
+
+int mpc_tag_check_grouped(const mpc_layer* layers, int count, const mpc_check_ptrs* ptrs, void* stream) {
+    if (count < 0) return MPC_E_SHAPE;
+    if (count == 0) return MPC_OK;
+    if (!layers || !ptrs) return MPC_E_NULL;
+    std::vector<int64_t> M((size_t)count);
+    std::vector<const u64*> al(count), ch(count), dc(count), md(count);
+    std::vector<u64*> cs(count);
+    for (int i = 0; i < count; ++i) {
+        const mpc_layer* L = &layers[i];
+        CHK(check_layer(L));
+        if (!same_ring(L->ring, layers[0].ring)) return MPC_E_RING;
+        const mpc_check_ptrs& p = ptrs[i];
+        CHK(check_ptr(p.alpha_i, 1));
+        CHK(check_ptr(p.cs_i, 1));
+        CHK(check_ptr(p.chi_hat, L->M));
+        CHK(check_ptr(p.Dc, L->M));
+        CHK(check_ptr(p.mDc_i, L->M));
+        M[i] = L->M;
+        al[i] = (const u64*)p.alpha_i;
+        ch[i] = (const u64*)p.chi_hat;
+        dc[i] = (const u64*)p.Dc;
+        md[i] = (const u64*)p.mDc_i;
+        cs[i] = (u64*)p.cs_i;
+    }
+    return cuda_status(mpcl::launch_check_compact_grouped(count, layers[0].ring.words, M.data(), al.data(), ch.data(),
+                                                          dc.data(), md.data(), cs.data(), (cudaStream_t)stream));
 }
 
 }  // extern "C"

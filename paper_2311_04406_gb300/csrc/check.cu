@@ -56,6 +56,32 @@ __global__ void __launch_bounds__(NT) check_compact_kernel(int64_t M, const u64*
     if (threadIdx.x == 0) st_elem<W>(cs, 0, tot);
 }
 
+// Up to CHECK_GROUP_MAX compact checks in one launch: block b computes the
+// check share of layer b (the same sum as check_compact_kernel).
+struct CheckGroup {
+    int count;
+    int64_t M[CHECK_GROUP_MAX];
+    const u64* alpha[CHECK_GROUP_MAX];
+    const u64* chi_hat[CHECK_GROUP_MAX];
+    const u64* Dc[CHECK_GROUP_MAX];
+    const u64* mDc[CHECK_GROUP_MAX];
+    u64* cs[CHECK_GROUP_MAX];
+};
+
+template <int W>
+__global__ void __launch_bounds__(NT) check_compact_group_kernel(const __grid_constant__ CheckGroup g) {
+    using T = typename Elem<W>::T;
+    ptx::grid_dep_launch();
+    ptx::grid_dep_wait();   // launched as a dependent of the kernel before it
+    const int l = blockIdx.x;
+    const T a = ld_elem<W>(g.alpha[l], 0);
+    T acc = 0;
+    for (int64_t r = threadIdx.x; r < g.M[l]; r += NT)
+        acc += ldg_elem<W>(g.chi_hat[l], r) * (a * ldg_elem<W>(g.Dc[l], r) - ldg_elem<W>(g.mDc[l], r));
+    T tot = block_sum<W>(acc);
+    if (threadIdx.x == 0) st_elem<W>(g.cs[l], 0, tot);
+}
+
 template <int W>
 __global__ void __launch_bounds__(NT) batchrec_partial_kernel(int64_t n, const u64* alpha,
                                                               const u64* chi, const u64* Wm,
@@ -140,6 +166,28 @@ cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u
                                      : launch_dependent(check_compact_kernel<2>, dim3(1), dim3(NT), 0, st, M, alpha,
                                                         chi_hat, Dc, mDc, cs);
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_compact_grouped(int n, int words, const int64_t* M, const u64* const* alpha,
+                                         const u64* const* chi_hat, const u64* const* Dc,
+                                         const u64* const* mDc, u64* const* cs, cudaStream_t st) {
+    for (int i0 = 0; i0 < n; i0 += CHECK_GROUP_MAX) {
+        CheckGroup g{};
+        g.count = n - i0 < CHECK_GROUP_MAX ? n - i0 : CHECK_GROUP_MAX;
+        for (int j = 0; j < g.count; ++j) {
+            g.M[j] = M[i0 + j];
+            g.alpha[j] = alpha[i0 + j];
+            g.chi_hat[j] = chi_hat[i0 + j];
+            g.Dc[j] = Dc[i0 + j];
+            g.mDc[j] = mDc[i0 + j];
+            g.cs[j] = cs[i0 + j];
+        }
+        const cudaError_t e =
+            words == 1 ? launch_dependent(check_compact_group_kernel<1>, dim3(g.count), dim3(NT), 0, st, g)
+                       : launch_dependent(check_compact_group_kernel<2>, dim3(g.count), dim3(NT), 0, st, g);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

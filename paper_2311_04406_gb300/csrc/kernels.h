@@ -102,6 +102,13 @@ cudaError_t launch_optmac_trunc(int64_t MN, int words, int k, int f, int party0,
 constexpr int LINCOMB_MAX = 16;
 cudaError_t launch_lincomb(int64_t n, int words, int count, const int64_t* coef, const u64* const* in, u64* out,
                            cudaStream_t st);
+// `groups` combinations with the same coefficients (count <= LINCOMB_GROUP_TERMS
+// terms each), LINCOMB_GROUP_MAX groups per launch; group g reads
+// in[g * count + j] and writes out[g] (n[g] elements)
+constexpr int LINCOMB_GROUP_MAX = 64;
+constexpr int LINCOMB_GROUP_TERMS = 4;
+cudaError_t launch_lincomb_grouped(int groups, const int64_t* n, int words, int count, const int64_t* coef,
+                                   const u64* const* in, u64* const* out, cudaStream_t st);
 
 // im2col of NCHW ring-element images for an f x f convolution (stride, zero padding)
 cudaError_t launch_im2col(int64_t B, int64_t C, int64_t H, int64_t W, int f, int pad, int stride, int words,
@@ -114,6 +121,11 @@ cudaError_t launch_transpose(int64_t rows, int64_t cols, int words, const u64* i
 // checks (a6)
 cudaError_t launch_check_compact(int64_t M, int words, const u64* alpha, const u64* chi_hat,
                                  const u64* Dc, const u64* mDc, u64* cs, cudaStream_t st);
+// n compact checks, CHECK_GROUP_MAX per launch (one block per check)
+constexpr int CHECK_GROUP_MAX = 64;
+cudaError_t launch_check_compact_grouped(int n, int words, const int64_t* M, const u64* const* alpha,
+                                         const u64* const* chi_hat, const u64* const* Dc,
+                                         const u64* const* mDc, u64* const* cs, cudaStream_t st);
 size_t check_batchrec_workspace(int64_t M, int64_t N, int words);
 cudaError_t launch_check_batchrec_seeded(int64_t M, int64_t N, int words, int s, const u64* alpha,
                                          const u64* seed, const u64* W, const u64* mW, u64* cs,

@@ -4,7 +4,8 @@
 // tiling changes only the time a layer takes.  For each layer shape
 // (ring width, M, K, N) the table holds a Choice: the tensor-core kernel with
 // a tile height (128 or 64 rows) and a row-tile swizzle width, or the
-// integer-pipe kernels with a K-split target.  Shapes not in the table use
+// integer-pipe kernels with a tile height (64 or 16 rows; 0 = by grid size)
+// and a K-split target.  Shapes not in the table use
 // the built-in heuristic (gemm_tc_eligible; 64-row tiles for M <= 64).
 // mpc_autotune times the candidates of each distinct shape on the caller's
 // stream and stores the fastest; the table can be saved to and loaded from a
@@ -38,7 +39,7 @@ bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
     if (c.path == 1)
         return (c.rows == 64 || c.rows == 128) && gemm_tc_feasible(M, K, N, words, c.rows) && c.gm >= 1 &&
                c.gm <= 64;
-    return c.path == 0 && c.waves >= 0 && c.waves <= 64;
+    return c.path == 0 && c.waves >= 0 && c.waves <= 64 && (c.rows == 0 || c.rows == 16 || c.rows == 64);
 }
 
 // Built-in tile height: 64-row tiles where the layer has at most 64 rows (an
@@ -135,9 +136,13 @@ int mpc_autotune(const mpc_layer* layers, int count, void* stream) {
                 if (rows == 64 && (M > 64 || !mpcl::gemm_tc_feasible(M, K, N, w, 64))) continue;
                 for (int gm : {1, 4, 8, 16}) cands.push_back(mpcl::Choice{1, gm, 0, 1, rows});
             }
-        // the integer pipes are far slower on large products: not timed there
+        // the integer pipes are far slower on large products: not timed there;
+        // their tile height (64 or 16 rows) matters only above M = 8
         if (!tc || macs < 2147483648.0)
-            for (int wv : {1, 2, 4, 8}) cands.push_back(mpcl::Choice{0, 0, wv, 1, 0});
+            for (int rows : {64, 16}) {
+                if (rows == 16 && M <= 8) continue;
+                for (int wv : {1, 2, 4, 8}) cands.push_back(mpcl::Choice{0, 0, wv, 1, M <= 8 ? 0 : rows});
+            }
         // operands (contents do not matter for the time: every path is exact)
         const size_t e = 8 * (size_t)w;
         const size_t b_mk = e * (size_t)(M * K), b_kn = e * (size_t)(K * N), b_mn = e * (size_t)(M * N);
@@ -191,7 +196,7 @@ int mpc_autotune(const mpc_layer* layers, int count, void* stream) {
 int mpc_autotune_set(const mpc_layer* layer, int path, int tile_rows, int swizzle, int waves) {
     int s = check_shape(layer);
     if (s != MPC_OK) return s;
-    mpcl::Choice c{path, swizzle, waves, 1, path == 1 ? tile_rows : 0};
+    mpcl::Choice c{path, swizzle, waves, 1, tile_rows};
     if (!mpcl::choice_ok(c, layer->M, layer->K, layer->N, layer->ring.words)) return MPC_E_MODE;
     std::lock_guard<std::mutex> lk(mpcl::g_mu);
     mpcl::table()[std::make_tuple(layer->ring.words, layer->M, layer->K, layer->N)] = c;
@@ -249,7 +254,7 @@ int mpc_autotune_load(const char* path) {
         return std::fscanf(f, "%d %lld %lld %lld %d %d %d %d", &w, &M, &K, &N, &path_, &tr, &gm, &waves) == 8;
     };
     while (next()) {
-        mpcl::Choice c{path_, gm, waves, 1, path_ == 1 ? tr : 0};
+        mpcl::Choice c{path_, gm, waves, 1, version == 1 ? (path_ == 1 ? 128 : 0) : tr};
         if ((w != 1 && w != 2) || M < 0 || K < 0 || N < 0 || !mpcl::choice_ok(c, M, K, N, w)) {
             std::fclose(f);
             return MPC_E_IO;

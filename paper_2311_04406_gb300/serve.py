@@ -12,11 +12,17 @@ completion.  The scheduler
     out of a seeded pool of uniform words standing in for the offline phase's
     output), so that input preparation overlaps the layers already running;
   * runs one "tick" at a time: the next linear layer of every admitted,
-    ready request, as ONE grouped share call, the opening of D~ on the device
-    (this party's R - Z plus the other parties' part, a resident input standing
-    in for the network exchange), ONE grouped tag call and the per-layer
-    checks (continuous batching: a request joins at the next tick after
-    admission and leaves after its last layer, whatever the others are doing);
+    ready request, as ONE grouped share call, ONE grouped opening of D~ on the
+    device (this party's R - Z plus the other parties' part, a resident input
+    standing in for the network exchange), ONE grouped tag call and ONE
+    grouped check call (continuous batching: a request joins at the next tick
+    after admission and leaves after its last layer, whatever the others are
+    doing);
+  * with graphs on, captures a tick as a CUDA graph the second time the same
+    tick recurs -- the same requests' arena ranges at the same layers, so
+    the same device pointers -- and replays it from then on (a stream of
+    same-shaped requests placed at the same offsets, e.g. repeated waves of
+    one model and batch size); other ticks are issued eagerly;
   * keeps at most `max_inflight` ticks queued on the device, and releases a
     finished request's memory once its last tick has completed.
 
@@ -184,9 +190,11 @@ def make_requests(n: int, rate: float, seed: int, max_batch: int = 32, models=("
 class Server:
     POOL_WORDS = 1 << 28          # 2 GiB of uniform words, larger than any one share tensor
 
+    MAX_GRAPHS = 256              # captured ticks kept (least recently used evicted)
+
     def __init__(self, ring=synth.Z128, party: int = 0, nparties: int = 2, mem_budget: int = 96 << 30,
                  tag: str = "compact", max_inflight: int = 2, max_group: int = 512, pool_seed: int = 0x5EED,
-                 ws_bytes: int = 8 << 30):
+                 ws_bytes: int = 8 << 30, graphs: bool = False):
         import torch
         if tag not in ("compact", "full"):
             raise ValueError("tag must be 'compact' or 'full'")
@@ -194,6 +202,11 @@ class Server:
         self.ring, self.party, self.nparties = ring, party, nparties
         self.mem_budget, self.tag = mem_budget, tag
         self.max_inflight, self.max_group = max_inflight, max_group
+        self.graphs = graphs
+        self._graphs = collections.OrderedDict()    # tick key -> (CUDAGraph, event of its last replay)
+        self._seen = collections.OrderedDict()      # tick keys issued eagerly once
+        self._cap_stream = None
+        self.tick_counts = {"eager": 0, "captured": 0, "replayed": 0}
         abi.load()
         # every admitted request's shares live in this arena: its size is the
         # memory budget that gates admission
@@ -259,21 +272,75 @@ class Server:
         which = (abi.MPC_WS_SHARE, abi.MPC_WS_TAG_COMPACT if self.tag == "compact" else abi.MPC_WS_TAG_FULL)
         return max(abi.mpc_workspace_size_grouped([L], w) for w in which)
 
-    def _tick(self, group):
-        """The next layer of every request in `group`, in as few grouped calls
-        as the workspace allows."""
-        part, used = [], 0
+    def _parts(self, group):
+        """`group` split into parts whose grouped calls fit the workspace; the
+        last part may need a workspace of its own (returned size > 0)."""
+        parts, part, used = [], [], 0
         for r in group:
             need = self._bufs(r, r.nxt)["ws_need"]
             if part and used + need > self.ws.numel():
-                self._tick_part(part, self.ws)
+                parts.append(part)
                 part, used = [], 0
             part.append(r)
             used += need
+        extra = used if (part and used > self.ws.numel()) else 0
         if part:
-            ws = self.ws if used <= self.ws.numel() else self.torch.empty(used, dtype=self.torch.uint8,
-                                                                          device="cuda")
+            parts.append(part)
+        return parts, extra
+
+    def _tick_eager(self, parts, extra):
+        for i, part in enumerate(parts):
+            ws = self.ws
+            if extra and i == len(parts) - 1:
+                ws = self.torch.empty(extra, dtype=self.torch.uint8, device="cuda")
             self._tick_part(part, ws)
+
+    def _tick(self, group):
+        """The next layer of every request in `group`, in as few grouped calls
+        as the workspace allows; replayed from a captured graph when this exact
+        tick ran before (graphs on)."""
+        parts, extra = self._parts(group)
+        if not self.graphs or extra:
+            self.tick_counts["eager"] += 1
+            self._tick_eager(parts, extra)
+            return
+        torch = self.torch
+        key = (tuple((r.region[0], r.model, r.batch, r.nxt) for r in group), self.tag)
+        hit = self._graphs.get(key)
+        if hit is None and key not in self._seen:
+            self._seen[key] = True
+            while len(self._seen) > 4 * self.MAX_GRAPHS:
+                self._seen.popitem(last=False)
+            self.tick_counts["eager"] += 1
+            self._tick_eager(parts, extra)
+            return
+        st = torch.cuda.current_stream()
+        if hit is None:
+            # second time this tick occurs: capture it (recording only, on a
+            # side stream; nothing runs until the replay below)
+            if self._cap_stream is None:
+                self._cap_stream = torch.cuda.Stream()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(self._cap_stream):
+                g.capture_begin(capture_error_mode="thread_local")
+                try:
+                    self._tick_eager(parts, 0)
+                finally:
+                    g.capture_end()
+            self._seen.pop(key, None)
+            self.tick_counts["captured"] += 1
+            while len(self._graphs) >= self.MAX_GRAPHS:
+                _, (old, ev) = self._graphs.popitem(last=False)
+                ev.synchronize()          # not destroyed while a replay may still run
+                del old
+        else:
+            g = hit[0]
+            self._graphs.move_to_end(key)
+            self.tick_counts["replayed"] += 1
+        g.replay()
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self._graphs[key] = (g, ev)
 
     def _tick_part(self, group, ws):
         a = abi
@@ -283,18 +350,18 @@ class Server:
                                                  Z_i=d["Z"]) for d in bufs], ws=ws)
         if self.tag == "compact":
             # the opening between the share and the tag (Fig. Pi_OptMAC): this
-            # party's [D]_i = [R]_i - [Z]_i plus the other parties' part
+            # party's [D]_i = [R]_i - [Z]_i plus the other parties' part, for
+            # every layer of the tick in one call
             k, s = self.ring.k, self.ring.s
-            for d in bufs:
-                a.mpc_lincomb(k, s, [1, -1, 1], [d["R"], d["Z"], d["Drest"]], d["Dt"])
+            a.mpc_lincomb_grouped(k, s, [1, -1, 1], [[d["R"], d["Z"], d["Drest"]] for d in bufs],
+                                  [d["Dt"] for d in bufs])
         tp = [dict(alpha_i=d["alpha"], E=d["E"], F=d["F"], mA_i=d["mA"], mB_i=d["mB"], mC_i=d["mC"],
                    mR_i=d["mR"], Dtilde=d["Dt"], chi=d["chi"], mZ_i=d["mZ"], mDc_i=d["mDc"], Dc=d["Dc"])
               for d in bufs]
         if self.tag == "compact":
             a.mpc_linear_tag_grouped(layers, a.MPC_TAG_COMPACT, tp, ws=ws)
-            for d in bufs:
-                a.mpc_tag_check(d["layer"], a.MPC_CHECK_COMPACT, d["alpha"], d["chi_hat"], d["Dc"], d["mDc"],
-                                d["cs"])
+            a.mpc_tag_check_grouped(layers, [dict(alpha_i=d["alpha"], chi_hat=d["chi_hat"], Dc=d["Dc"],
+                                                  mDc_i=d["mDc"], cs_i=d["cs"]) for d in bufs])
         else:
             a.mpc_linear_tag_grouped(layers, a.MPC_TAG_FULL, tp, ws=ws)
 
@@ -317,6 +384,7 @@ class Server:
             finally:
                 self.tag = saved
         torch = self.torch
+        self.tick_counts = {"eager": 0, "captured": 0, "replayed": 0}
         st = torch.cuda.current_stream()
         side = torch.cuda.Stream()
         words = self.ring.words
@@ -424,4 +492,7 @@ class Server:
             "latency_ms_p50": q(lat, 50), "latency_ms_p99": q(lat, 99),
             "tick_ms_p50": q(ticks, 50), "tick_ms_p99": q(ticks, 99), "ticks": len(ticks),
             "peak_resident_bytes": peak_mem, "tag": self.tag,
+            "tick_launch": ("CUDA graph replay of recurring ticks, eager otherwise" if self.graphs
+                            else "eager grouped calls"),
+            "ticks_by_launch": dict(self.tick_counts),
         }

@@ -172,7 +172,9 @@ def test_launch_table_host_logic(lib, tmp_path):
     with pytest.raises(abi.MpcError):
         abi.mpc_autotune_set(small, 1, 0, 0)
     with pytest.raises(abi.MpcError):
-        abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=32)      # tile heights: 128 or 64
+        abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=32)      # tensor-core tile heights: 128 or 64
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_set(small, 0, 0, 2, tile_rows=128)     # integer pipes: 64, 16 or 0
     f = tmp_path / "table.txt"
     assert abi.mpc_autotune_save(str(f)) == 2
     lines = f.read_text().split("\n")

@@ -28,11 +28,13 @@ def operands(ring, M, K, N, seed):
 
 
 CHOICES = [(1, 1, 0), (1, 4, 0), (1, 16, 0), (1, 64, 0), (0, 0, 1), (0, 0, 2), (0, 0, 8)]
-TILE_ROWS = (128, 64)
+TILE_ROWS = (128, 64)          # tensor cores
+SIMT_ROWS = (0, 64, 16)        # integer pipes (0: chosen by grid size)
 
 
 @pytest.mark.parametrize("ring,shape", [(synth.Z64, (300, 200, 96)), (synth.Z64, (1100, 64, 66)),
-                                        (synth.Z128, (200, 130, 48)), (synth.Z64, (16, 4096, 512))],
+                                        (synth.Z128, (200, 130, 48)), (synth.Z64, (16, 4096, 512)),
+                                        (synth.Z64, (1024, 27, 64)), (synth.Z128, (33, 27, 70))],
                          ids=lambda x: str(x) if isinstance(x, tuple) else None)
 def test_every_choice_is_exact(ring, shape):
     M, K, N = shape
@@ -40,8 +42,8 @@ def test_every_choice_is_exact(ring, shape):
     want = O.linear_share(ring.bits, 0, E, F, A, B, C)
     L = abi.make_layer(M, K, N, ring.k, ring.s, 0, 2)
     for path, gm, waves in CHOICES:
-        for rows in (TILE_ROWS if path else (0,)):
-            abi.mpc_autotune_set(L, path, gm if path else 0, waves, tile_rows=rows or 128)
+        for rows in (TILE_ROWS if path else SIMT_ROWS):
+            abi.mpc_autotune_set(L, path, gm if path else 0, waves, tile_rows=rows)
             assert abi.mpc_gemm_path(L) == path
             assert abi.mpc_autotune_choice(L)[4] == rows
             Z = empty_like_ring((M, N), ring.words)
@@ -90,11 +92,11 @@ def test_grouped_with_mixed_choices(ring):
     persistent launch)."""
     shapes = [(300, 200, 96), (1100, 64, 66), (64, 256, 256), (520, 128, 130), (40, 300, 96), (17, 1000, 34),
               (64, 27, 64), (130, 600, 66)]
-    choices = [(1, 1, 0, 128), (0, 0, 4, 0), (1, 16, 0, 64), (1, 4, 0, 128), (1, 8, 0, 64), (1, 1, 0, 64),
-               (1, 8, 0, 128), (1, 8, 0, 64)]
+    choices = [(1, 1, 0, 128), (0, 0, 4, 16), (1, 16, 0, 64), (1, 4, 0, 128), (1, 8, 0, 64), (1, 1, 0, 64),
+               (1, 8, 0, 128), (0, 0, 2, 64)]
     layers = [abi.make_layer(M, K, N, ring.k, ring.s) for M, K, N in shapes]
     for L, (path, gm, waves, rows) in zip(layers, choices):
-        abi.mpc_autotune_set(L, path, gm, waves, tile_rows=rows or 128)
+        abi.mpc_autotune_set(L, path, gm, waves, tile_rows=rows)
     data = [operands(ring, M, K, N, 7 * M + K) for M, K, N in shapes]
     Zs = [empty_like_ring((M, N), ring.words) for M, K, N in shapes]
     abi.mpc_linear_share_grouped(layers, [dict(E=dev(E), F=dev(F), A_i=dev(A), B_i=dev(B), C_i=dev(C), Z_i=Z)

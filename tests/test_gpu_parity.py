@@ -196,7 +196,9 @@ def test_cnn_layers_full_size(layer):
 
 
 SKINNY = [(synth.Z64, (1, 4096, 512)), (synth.Z64, (8, 300, 70)), (synth.Z64, (3, 2048, 130)),
-          (synth.Z64, (1, 4096, 10)), (synth.Z128, (2, 1024, 96)), (synth.Z128, (7, 33, 5))]
+          (synth.Z64, (1, 4096, 10)), (synth.Z128, (2, 1024, 96)), (synth.Z128, (7, 33, 5)),
+          (synth.Z64, (4, 4608, 512)), (synth.Z64, (5, 1000, 71)), (synth.Z128, (8, 4608, 50)),
+          (synth.Z64, (1, 7, 3))]
 
 
 @pytest.mark.parametrize("ring,shape", SKINNY, ids=lambda x: str(x) if isinstance(x, tuple) else "")
