@@ -50,6 +50,7 @@ WORKLOADS = {
     "transformer_block": ("transformer_block_h1024_a16_t2048", lambda b: synth.transformer_block()),
     "uneven": ("uneven256_seeded", lambda b: synth.uneven_layers(256)),
     "serve": ("serve_resnet18_vgg16_b1-32_z128_poisson", None),
+    "layer": ("layer_{b}", None),          # one layer of the --shape given
 }
 L2_BYTES = 129 * 2**20
 
@@ -672,11 +673,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     abi.load()
-    wl_name, wl_fn = WORKLOADS[args.workload]
-    layers = wl_fn(args.batch)
-    if PASS == "train":
-        layers = layers + synth.backward_layers(layers)
-    workload = wl_name.format(b=args.batch) + ("_train" if PASS == "train" else "")
+    layers, workload = workload_layers(args)
     tune = None
     if args.autotune:
         t0 = time.perf_counter()
@@ -919,7 +916,9 @@ def make_config(workload, layers, ws) -> dict:
             "training: forward + grad X (M,N,K) + grad W (K,M,N) per layer, with device transposes",
             "ring": f"Z_2^{RING.bits} (k={RING.k}, s={RING.s})",
             "parties": PARTIES, "parallelism": f"replicas x{ws}",
-            "l2": f"inputs larger than L2 ({run_bytes(layers) / 2**20:.0f} MiB per step > 129 MiB)"}
+            "l2": (f"inputs larger than L2 ({run_bytes(layers) / 2**20:.0f} MiB per step > 129 MiB)"
+                   if run_bytes(layers) > L2_BYTES else
+                   f"inputs smaller than L2 ({run_bytes(layers) / 2**20:.1f} MiB per step): steps hit in L2")}
 
 
 def check_device(abi, where: str):
@@ -1095,17 +1094,31 @@ def cpu_baseline(layers, budget_s=15.0):
                        f"parties ({units:.3e} ring MACs)")}
 
 
+def workload_layers(args):
+    """(layers, workload name) of the command line."""
+    wl_name, wl_fn = WORKLOADS[args.workload]
+    if args.workload == "layer":
+        M, K, N = args.shape
+        layers = [synth.Layer(f"layer_{M}x{K}x{N}", M, K, N)]
+        name = f"layer_{M}x{K}x{N}"
+    elif wl_fn is None:
+        # the serving mix: one ResNet-18 and one VGG16 request at the mean batch
+        layers = synth.resnet18_layers(16) + synth.vgg16_layers(16)
+        name = wl_name
+    else:
+        layers = wl_fn(args.batch)
+        name = wl_name.format(b=args.batch)
+    if PASS == "train":
+        layers = layers + synth.backward_layers(layers)
+        name += "_train"
+    return layers, name
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl_name, wl_fn = WORKLOADS[args.workload]
-    if wl_fn is None:
-        # the serving mix: one ResNet-18 and one VGG16 request at the mean batch
-        wl_fn = lambda b: synth.resnet18_layers(16) + synth.vgg16_layers(16)
-    layers = wl_fn(args.batch)
-    if PASS == "train":
-        layers = layers + synth.backward_layers(layers)
+    layers, workload = workload_layers(args)
     run, units = cpu_sample(layers, 1.0 / 64)
     for _ in range(args.warmup):
         run()
@@ -1121,8 +1134,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64" if RING.words == 1 else "u128 (two u64 words)",
         "data": "synthetic (uniform ring words from seeded SplitMix64)",
-        "config": make_config(wl_name.format(b=args.batch) + ("_train" if PASS == "train" else ""), layers,
-                              int(os.environ.get("WORLD_SIZE", "1"))),
+        "config": make_config(workload, layers, int(os.environ.get("WORLD_SIZE", "1"))),
         "runs_on": "host cores (the oracle), rank 0 alone",
         "cpu_baseline": {"value": value, "unit": "ring-GMAC/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": "per step: share + full tag at the first 1/64 of output rows and "
@@ -1206,6 +1218,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cnn",
                     help="layer set (default: the CNN pair, conv 1024x576x64 + dense 128x4096x4096)")
     ap.add_argument("--batch", type=int, default=1, help="batch size for vgg16 / resnet18")
+    ap.add_argument("--shape", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    help="M,K,N of the one layer of --workload layer")
     ap.add_argument("--ring", type=int, choices=[64, 128], default=64,
                     help="share ring Z_2^64 (k=s=32) or Z_2^128 (k=s=64)")
     ap.add_argument("--protocol", choices=["plain", "trunc"], default="plain",
@@ -1230,6 +1244,8 @@ def main():
         args.warmup = 3
     if args.grouped and PROTOCOL != "plain":
         ap.error("--grouped runs the untruncated layer (--protocol plain)")
+    if (args.workload == "layer") != (args.shape is not None) or (args.shape is not None and len(args.shape) != 3):
+        ap.error("--workload layer takes --shape M,K,N (and --shape needs --workload layer)")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":
