@@ -239,3 +239,37 @@ def test_compact_launch_counts(lib):
     assert abi.mpc_launch_count(abi.make_layer(1024, 576, 64), abi.MPC_WS_TAG_COMPACT) == 2
     assert abi.mpc_launch_count(abi.make_layer(8192, 1024, 4096), abi.MPC_WS_TAG_COMPACT) == 2
     assert abi.mpc_launch_count(abi.make_layer(0, 8, 8), abi.MPC_WS_TAG_COMPACT) == 0
+
+
+@pytest.mark.hidden_gpu
+def test_grouped_check_and_lincomb_validation(lib):
+    """mpc_tag_check_grouped / mpc_lincomb_grouped reject bad groups before any launch."""
+    layers = (abi.mpc_layer * 2)(abi.make_layer(8, 1, 1), abi.make_layer(8, 1, 1))
+    ptrs = (abi.mpc_check_ptrs * 2)()
+    for i in range(2):
+        for f in abi.CHECK_PTR_FIELDS:
+            setattr(ptrs[i], f, 0x1000)
+    assert lib.mpc_tag_check_grouped(layers, 0, ptrs, None) == 0            # nothing to do
+    assert lib.mpc_tag_check_grouped(layers, -1, ptrs, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_tag_check_grouped(None, 2, ptrs, None) == abi.MPC_E_NULL
+    ptrs[1].Dc = 0x1008
+    assert lib.mpc_tag_check_grouped(layers, 2, ptrs, None) == abi.MPC_E_ALIGN
+    ptrs[1].Dc = None
+    assert lib.mpc_tag_check_grouped(layers, 2, ptrs, None) == abi.MPC_E_NULL
+    ptrs[1].Dc = 0x1000
+    mixed = (abi.mpc_layer * 2)(abi.make_layer(8, 1, 1), abi.make_layer(8, 1, 1, 64, 64))
+    assert lib.mpc_tag_check_grouped(mixed, 2, ptrs, None) == abi.MPC_E_RING
+    ring = abi.mpc_ring(32, 32, 1)
+    R = ctypes.byref(ring)
+    n = (ctypes.c_int64 * 2)(8, 16)
+    c = (ctypes.c_int64 * 3)(1, -1, 1)
+    ins = (ctypes.c_void_p * 6)(*([0x1000] * 6))
+    outs = (ctypes.c_void_p * 2)(0x2000, 0x3000)
+    assert lib.mpc_lincomb_grouped(R, 0, n, 3, c, ins, outs, None) == 0
+    assert lib.mpc_lincomb_grouped(R, 2, n, 5, c, ins, outs, None) == abi.MPC_E_SHAPE    # at most 4 terms
+    assert lib.mpc_lincomb_grouped(R, -1, n, 3, c, ins, outs, None) == abi.MPC_E_SHAPE
+    assert lib.mpc_lincomb_grouped(None, 2, n, 3, c, ins, outs, None) == abi.MPC_E_NULL
+    bad = (ctypes.c_void_p * 6)(0x1000, 0x1000, 0x1000, 0x1000, 0x1008, 0x1000)
+    assert lib.mpc_lincomb_grouped(R, 2, n, 3, c, bad, outs, None) == abi.MPC_E_ALIGN
+    neg = (ctypes.c_int64 * 2)(8, -1)
+    assert lib.mpc_lincomb_grouped(R, 2, neg, 3, c, ins, outs, None) == abi.MPC_E_SHAPE
