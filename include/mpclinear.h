@@ -226,20 +226,23 @@ int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
  * this library computes the same exact sums, so the choice of path and tile
  * shape is a matter of speed only.  For each layer shape (ring width, M, K, N)
  * the table holds a choice -- path 1, the tensor-core kernel, with output
- * tiles of `tile_rows` rows (128, or 64 for layers of at most 64 rows: an
- * M = 64 MMA takes as long as an M = 128 one, so the 64-row tile halves only
- * the shared-memory bytes of the left operand) and `swizzle` row tiles per
- * tile-order group (1-64); or path 0, the integer-pipe kernels, with tiles
+ * tiles of `tile_rows` rows: 128; 64 (an M = 64 MMA takes as long as an
+ * M = 128 one, so the 64-row tile halves only the shared-memory bytes of the
+ * left operand); or the wide tile, tile_rows = 32 for Z_2^64 and 16 for
+ * Z_2^128, which puts 128 output columns on the tensor core's M side and that
+ * many of the layer's rows on its N side (for layers with few rows) -- and
+ * `swizzle` tiles per tile-order group (1-64); or path 0, the integer-pipe kernels, with tiles
  * of `tile_rows` rows (64 or 16; 0 = 16 when 64-row tiles would give fewer
  * blocks than SMs, else 64; skinny layers with M <= 8 use a GEMV whatever the
  * value) and a K-split target of `waves` x 152 blocks (0 = default).  Untuned
  * shapes use a built-in rule (tensor cores from 2^22 ring MACs, 2^20 for
- * Z_2^128; 64-row tensor-core tiles for M <= 64).  The table is process-wide and thread-safe; workspace
+ * Z_2^128; the wide tile up to two of its row tiles, 64-row tiles up to
+ * M = 64).  The table is process-wide and thread-safe; workspace
  * sizes do not depend on it.
  *
  * mpc_autotune: for each distinct shape of layers[count], times the
- *   candidates (tile heights 128 and, for M <= 64, 64 rows, each with swizzle
- *   1/4/8/16 on the tensor cores; tile heights 64 and 16 with K-split 1/2/4/8
+ *   candidates (128-row tiles, 64-row tiles for M <= 64, the wide tile for
+ *   M <= 128, each with swizzle 1/4/8/16 on the tensor cores; tile heights 64 and 16 with K-split 1/2/4/8
  *   on the integer pipes, below 2^31 ring MACs) on `stream` and stores the
  *   fastest.  Synchronous;
  *   allocates and frees its own scratch operands; do not call it during

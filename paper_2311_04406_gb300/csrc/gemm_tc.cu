@@ -95,6 +95,7 @@ template <> struct Cfg<2> {
 // occupies lanes 0-15 of each 32-lane TMEM quadrant q, holding rows
 // 16 q .. 16 q + 15 (measured).
 constexpr int BM = 128;                  // rows of the default tile
+constexpr int WIDE_COLS = 128;           // output columns of a wide tile (TMEM lanes)
 constexpr int KS = 16;                   // K per stage (one MMA K step)
 constexpr int NSTACK = 256;              // rows of the stacked B operand (NDIG * ND)
 constexpr int RAW_ONE = MPCL_TC_RAW;     // raw R tiles in flight, one-layer launches
@@ -261,8 +262,10 @@ template <int G> struct PrologueGroup {
     int grid;                 // CTAs of the GEMM launch
 };
 
-// thread `id` of `nthreads` working for one layer (R-row tiles)
-template <int W, int R>
+// thread `id` of `nthreads` working for one layer: digit planes of L in
+// R-row tiles; output tiles of R x ND (or, WIDE, ND x WIDE_COLS) for the Z = C
+// preset
+template <int W, int R, bool WIDE = false>
 __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid, int64_t id,
                                               int64_t nthreads) {
     constexpr int NDIG = Cfg<W>::NDIG;
@@ -273,10 +276,12 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
         // atomically.  A tile one CTA computes whole is written by that CTA.
         // 16-byte vectors: two elements of one row for W = 1 (N is even),
         // one element for W = 2.
-        // Blocks take tiles in turn; a split tile's R x ND block is copied by
-        // the 256 threads, 16 vectors (ND elements) per row.
+        // Blocks take tiles in turn; a split tile's TR x TC block is copied by
+        // the 256 threads, TC W / 2 vectors per row.  (A wide tile's first
+        // index counts column tiles, its second row tiles.)
         constexpr int ND = Cfg<W>::ND;
-        constexpr int VPR = ND * W / 2;                      // 16-byte vectors per tile row
+        constexpr int TR = WIDE ? ND : R, TC = WIDE ? WIDE_COLS : ND;
+        constexpr int VPR = TC * W / 2;                      // 16-byte vectors per tile row
         const int64_t blk = id >> 8, nblk = nthreads >> 8;
         const int tid = (int)(id & 255);
         const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C);
@@ -286,12 +291,13 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
         for (int64_t t = blk; t < T; t += nblk) {
             const int64_t u = t * p.I;
             if (u + p.I <= range_end_of(sc, u)) continue;   // whole: written by its CTA
-            int64_t mt, nt;
-            tile_mn(t, p.m_tiles, p.n_tiles, p.gm, &mt, &nt);
-            for (int q = tid; q < R * VPR; q += 256) {
+            int64_t ta, tb;
+            tile_mn(t, p.m_tiles, p.n_tiles, p.gm, &ta, &tb);
+            const int64_t mt = WIDE ? tb : ta, nt = WIDE ? ta : tb;
+            for (int q = tid; q < TR * VPR; q += 256) {
                 const int r = q / VPR, j = q - r * VPR;
-                const int64_t m = mt * R + r;
-                const int64_t n = nt * ND + (int64_t)j * 2 / W;
+                const int64_t m = mt * TR + r;
+                const int64_t n = nt * TC + (int64_t)j * 2 / W;
                 if (m >= p.M || n >= p.N) continue;
                 const int64_t i = (m * p.N + n) * W / 2;     // vector index
                 z2[i] = c2 ? __ldg(c2 + i) : make_ulonglong2(0, 0);
@@ -368,7 +374,7 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
     }
 }
 
-template <int W, int G, int R>
+template <int W, int G, int R, bool WIDE = false>
 __global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ PrologueGroup<G> g) {
     // the GEMM may be scheduled now: it waits for this grid before reading
     ptx::grid_dep_launch();
@@ -387,7 +393,7 @@ __global__ void __launch_bounds__(256) prologue_kernel(const __grid_constant__ P
     }
     const int64_t lb = (int64_t)blockIdx.x - g.b_off[gi];
     const int64_t nb = g.b_off[gi + 1] - g.b_off[gi];
-    prologue_body<W, R>(g.p[gi], g.grid, lb * 256 + threadIdx.x, nb * 256);
+    prologue_body<W, R, WIDE>(g.p[gi], g.grid, lb * 256 + threadIdx.x, nb * 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -1040,6 +1046,366 @@ static_assert(Layout<1>::SMEM <= 227 * 1024 && Layout<2>::SMEM <= 227 * 1024, "s
 static_assert(Layout<1, 1, 64>::SMEM <= 227 * 1024 && Layout<2, 1, 64>::SMEM <= 227 * 1024, "smem, 64-row tiles");
 
 // ---------------------------------------------------------------------------
+// the wide tile: Z^T = R^T . L^T for layers with few rows
+//
+// An MMA costs the same for 64 or 128 rows (above), so a layer with M rows
+// well below 128 wastes most of a row tile.  The wide tile exchanges the
+// roles of the operands: the 128 TMEM lanes hold WIDE_COLS = 128 output
+// COLUMNS, and the stacked operand holds ND of the layer's rows (ND = 32 for
+// Z_2^64, 16 for Z_2^128).  Per 16-deep K step, MMA i multiplies digit plane i
+// of R^T = [B ; F]^T (128 columns x 16 K, formed in shared memory by the
+// converter warps from raw 16 x 128 tiles of [B ; F]) by the first
+// (D - i) ND rows of the stack of L's digit planes (rows j ND + m hold digit j
+// of row m; the prologue writes them with ND-row tiles, which is exactly this
+// stacked layout, and the L producer copies one 8 KB stage at a time), into
+// TMEM column block i.  The product R_i . L_j again lands in block i + j, so
+// the MMA shapes, the exactness bound, the schedule and the drain's
+// arithmetic are those of the row tiles; a drain thread now holds the ND rows
+// of one output column, and its stores run along the rows (lane = column).
+// Work unit: (column tile, row tile of ND rows, Kd interval); the walker's
+// first index counts column tiles.
+
+template <int W, int G = 1> struct WideLayout {
+    static constexpr int STAGES = Cfg<W>::STAGES;            // operand stages: 4 (W = 1) or 2 (W = 2)
+    static constexpr int RAW = W == 1 ? 3 : 2;               // raw [B ; F] tiles in flight
+    static constexpr uint32_t A_PLANE = a_plane_bytes<WIDE_COLS>();      // 4 KB
+    static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE;
+    static constexpr uint32_t RAW_TILE = KS * WIDE_COLS * 8 * W;        // 16 or 32 KB
+    static constexpr int NBARS = 2 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
+    static constexpr uint32_t OFF_B = STAGES * A_STAGE;
+    static constexpr uint32_t OFF_RAW = OFF_B + STAGES * B_STAGE_BYTES;
+    static constexpr uint32_t OFF_BAR = OFF_RAW + RAW * RAW_TILE;
+    static constexpr uint32_t OFF_INFO = (OFF_BAR + NBARS * 8 + 16 + 15) / 16 * 16;
+    static constexpr uint32_t SMEM = OFF_INFO + NINFO * 16;
+};
+static_assert(Cfg<1>::NDIG * Cfg<1>::ND * KS * 2 == B_STAGE_BYTES && Cfg<2>::NDIG * Cfg<2>::ND * KS * 2 == B_STAGE_BYTES,
+              "a stage of the L stack is one B stage");
+static_assert(WideLayout<1>::OFF_BAR % 16 == 0 && WideLayout<2>::OFF_BAR % 16 == 0, "barrier alignment");
+static_assert(WideLayout<1>::OFF_INFO % 16 == 0 && WideLayout<2>::OFF_INFO % 16 == 0, "int4 slots");
+
+template <int W, int G>
+__global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __grid_constant__ TcGroup<G> g) {
+    using Lay = WideLayout<W, G>;
+    constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND, STAGES = Lay::STAGES, RAW = Lay::RAW;
+    constexpr uint32_t A_STAGE = Lay::A_STAGE, A_PLANE = Lay::A_PLANE, RAW_TILE = Lay::RAW_TILE;
+    using Sum = typename Elem<W>::T;
+
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;                       // R^T digit planes (converter warps)
+    uint8_t* sB = smem + Lay::OFF_B;          // L stack (copies of the prologue's planes)
+    uint8_t* sRaw = smem + Lay::OFF_RAW;      // raw 16 x 128 tiles of [B ; F] (TMA)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::OFF_BAR);
+    uint64_t* full = bars;                    // stage ready: the stack copy and the 4 converter warps
+    uint64_t* empty = full + MAX_STAGES;      // stage free: its MMAs are done
+    uint64_t* rawFull = empty + MAX_STAGES;
+    uint64_t* rawEmpty = rawFull + RAW;
+    uint64_t* accFull = rawEmpty + RAW;
+    uint64_t* accEmpty = accFull + 2;
+    uint64_t* mmaDone = accEmpty + 2;
+    uint64_t* infoFull = mmaDone + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(infoFull + NINFO);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int4* info = reinterpret_cast<int4*>(smem + Lay::OFF_INFO);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t cta = blockIdx.x;
+    __shared__ TcParams sp[G > 1 ? G : 1];
+    if constexpr (G > 1) {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(&g.p[0]);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(sp);
+        const int nw = g.count * (int)(sizeof(TcParams) / 8);
+        for (int i = threadIdx.x; i < nw; i += NTHREADS) dst[i] = src[i];
+    }
+    const int count = g.count, grid = g.grid;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1 + NCONV / 32);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int r = 0; r < RAW; ++r) {
+            ptx::mbar_init(&rawFull[r], 1);
+            ptx::mbar_init(&rawEmpty[r], NCONV / 32);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&accFull[b], 1);
+            ptx::mbar_init(&accEmpty[b], NDRAIN / 32);
+        }
+        ptx::mbar_init(mmaDone, 1);
+        for (int i = 0; i < NINFO; ++i) ptx::mbar_init(&infoFull[i], 1);
+        *abort_flag = 0;
+        ptx::fence_barrier_init();
+    }
+    if (warp == W_APROD) {
+        ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    ptx::grid_dep_wait();   // the prologue's planes and pre-set Z are read below
+    const int64_t nv = G == 1 ? cta_units(sched_of(g.p[0].U, g.p[0].I, grid), cta)
+                              : cta_total(sp, count, grid, cta);
+
+    if (warp == W_APROD) {
+        // the L stack: one 8 KB stage per 16-deep K step
+        int it = 0;
+        bool ok = true;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
+            const uint8_t* src = p.Ap + ((size_t)x.nt * p.S_tot + (size_t)x.ii * p.KD) * B_STAGE_BYTES;
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int s = it % STAGES;
+                const bool free_ = ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, free_)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                const uint32_t leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &full[s], B_STAGE_BYTES);
+                ptx::bulk_g2s_if(leader, sB + s * B_STAGE_BYTES, src + (size_t)j * B_STAGE_BYTES, B_STAGE_BYTES,
+                                 &full[s]);
+            }
+        }
+        // copies still in flight (only after a timeout) land before the CTA exits
+        for (int j = max(0, it - STAGES); j < it; ++j)
+            ptx::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, abort_flag, WAIT_LIMIT);
+    } else if (warp == W_BPROD) {
+        int it = 0;
+        bool ok = true;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        int prefetched = -1;
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
+            const CUtensorMap* tmB = &g.tmB[wk.gi];
+            const CUtensorMap* tmF = &g.tmF[wk.gi];
+            if (prefetched != wk.gi) {
+                if (lane == 0) {
+                    ptx::prefetch_tmap(tmB);
+                    ptx::prefetch_tmap(tmF);
+                }
+                prefetched = wk.gi;
+            }
+            const int x0 = (int)x.mt * WIDE_COLS * W;   // first word of the column tile
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int r = it % RAW;
+                const bool free_ = ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, free_)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                const uint32_t leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &rawFull[r], RAW_TILE);
+                const int64_t kp0 = (int64_t)(x.ii * p.KD + j) * KS;
+                const bool second = p.one_half || kp0 >= p.Kp;
+                const CUtensorMap* tm = second ? tmF : tmB;
+                const int y = (int)(p.one_half || kp0 < p.Kp ? kp0 : kp0 - p.Kp);
+                ptx::tma_load_2d_if(leader, sRaw + r * RAW_TILE, tm, x0, y, &rawFull[r]);
+            }
+        }
+        for (int j = max(0, it - RAW); j < it; ++j)
+            ptx::mbar_wait(&rawFull[j % RAW], (j / RAW) & 1, abort_flag, WAIT_LIMIT);
+    } else if (warp >= W_CONV0 && warp < W_CONV0 + 4) {
+        // converter thread n (0..127) forms row n of every R^T plane: the 16 K
+        // values of output column n, digit by digit, in two 8-K halves
+        const int n = threadIdx.x - W_CONV0 * 32;
+        int total = 0;
+        {
+            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+            for (int64_t v = 0; v < nv; ++v) total += wk.next().nst;
+        }
+        const uint32_t boff = (uint32_t)(n >> 3) * CORE_SBO + (uint32_t)(n & 7) * 16;
+        for (int it = 0; it < total; ++it) {
+            const int r = it % RAW;
+            if (!__all_sync(0xffffffffu, ptx::mbar_wait(&rawFull[r], (it / RAW) & 1, abort_flag, WAIT_LIMIT))) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            // raw tile: 16 rows (K) of 128 W words; lanes read consecutive columns
+            const u64* raw = reinterpret_cast<const u64*>(sRaw + r * RAW_TILE);
+            u64 e[16 * W];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if constexpr (W == 1) {
+                    e[k] = raw[k * WIDE_COLS + n];
+                } else {
+                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(raw + (k * WIDE_COLS + n) * 2);
+                    e[2 * k] = v.x;
+                    e[2 * k + 1] = v.y;
+                }
+            }
+            // order these generic-proxy reads before the next TMA write into the slot
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&rawEmpty[r]);
+            const int s = it % STAGES;
+            if (!__all_sync(0xffffffffu,
+                            ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT))) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            uint8_t* dst = sA + s * A_STAGE + boff;
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh) {
+                Biased<W> b[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
+#pragma unroll
+                for (int t = 0; t < NDIG; ++t) {
+                    const int wi = t >> 2;
+                    const uint32_t byte = t & 3;
+                    uint4 o;
+                    o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
+                    o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
+                    o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
+                    o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
+                    *reinterpret_cast<uint4*>(dst + t * A_PLANE + kh * CORE_LBO) = o;
+                }
+            }
+            // each thread orders its plane writes before the MMAs (async proxy);
+            // the warp then arrives once
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&full[s]);
+        }
+    } else if (warp == W_MMA) {
+        const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
+        bool ok = true;
+        int it = 0;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const int set = (int)(v & 1);
+            const bool got = ptx::mbar_wait(&accEmpty[set], (int)((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            ptx::tc_fence_after();
+            if (lane == 0) {
+                info[v % NINFO] = make_int4((int)x.mt, (int)x.nt, x.ii, (int)x.flush | (wk.gi << 1));
+                ptx::mbar_arrive(&infoFull[v % NINFO]);
+            }
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int s = it % STAGES;
+                const bool ready = ptx::mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, ready)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t leader = ptx::elect_one();
+                const uint64_t bdesc = ptx::smem_desc_kmajor(bBase + s * B_STAGE_BYTES, CORE_LBO, CORE_SBO);
+#pragma unroll
+                for (int i = 0; i < NDIG; ++i) {
+                    const uint64_t adesc =
+                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE, CORE_LBO, CORE_SBO);
+                    const uint32_t idesc = ptx::idesc_f16_f32(WIDE_COLS, (NDIG - i) * ND);
+                    ptx::mma_f16_if(leader, tmem + set * NSTACK + i * ND, adesc, bdesc, idesc,
+                                    (j == 0 && i == 0) ? 0u : 1u);
+                }
+                ptx::mma_commit_if(leader, &empty[s]);
+            }
+            if (ok) ptx::mma_commit_if(ptx::elect_one(), &accFull[set]);
+        }
+        ptx::mma_commit_if(ptx::elect_one(), mmaDone);
+        ptx::mbar_wait(mmaDone, 0, abort_flag, WAIT_LIMIT);
+    } else {
+        // drain: lane l of quadrant q holds output column 32 q + l of the tile
+        // and the sums of its ND rows
+        const int quad = warp & 3;
+        constexpr int DPL = 32 / ND;
+        Sum sum[ND];
+#pragma unroll
+        for (int c = 0; c < ND; ++c) sum[c] = 0;
+        int seg_ii = -1;
+        for (int64_t v = 0; v < nv; ++v) {
+            const bool have = ptx::mbar_wait(&infoFull[v % NINFO], (int)((v / NINFO) & 1), abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, have)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            const int4 u = info[v % NINFO];
+            const int x_ii = u.z;
+            const bool x_flush = (u.w & 1) != 0;
+            const TcParams& p = G == 1 ? g.p[0] : sp[u.w >> 1];
+            const int set = (int)(v & 1);
+            const bool got = ptx::mbar_wait(&accFull[set], (int)((v >> 1) & 1), abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * NSTACK;
+#pragma unroll
+            for (int t0 = 0; t0 < NDIG; t0 += DPL) {
+                uint32_t f[32];
+                ptx::tmem_ld32(base + t0 * ND, f);
+                ptx::tmem_wait_ld();
+                if (t0 + DPL >= NDIG) {
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int t = t0 + q / ND, c = q % ND;
+                    const long long d = __float2int_rn(__uint_as_float(f[q]));
+                    const Sum dv = (Sum)(W == 1 ? (Sum)(u64)d : (Sum)(__int128)d);
+                    sum[c] += dv << (8 * t);
+                }
+            }
+            if (seg_ii < 0) seg_ii = x_ii;
+            if (x_flush) {
+                // whole tiles store C + sum, pieces of split tiles are added
+                // (Z was set to C by the prologue); for each row the warp's
+                // lanes write 32 consecutive columns
+                const bool whole = seg_ii == 0 && x_ii == p.I - 1;
+                seg_ii = -1;
+                const int64_t n = (int64_t)u.x * WIDE_COLS + quad * 32 + lane;
+                const int64_t mb = (int64_t)u.y * ND;
+                constexpr int BATCH = 8;
+#pragma unroll
+                for (int c0 = 0; c0 < ND; c0 += BATCH) {
+                    Sum cv[BATCH];
+#pragma unroll
+                    for (int i = 0; i < BATCH; ++i) {
+                        const int64_t m = mb + c0 + i;
+                        cv[i] = (whole && p.C && m < p.M && n < p.N) ? ldg_elem<W>(p.C, m * p.N + n) : (Sum)0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < BATCH; ++i) {
+                        const int64_t m = mb + c0 + i;
+                        if (m < p.M && n < p.N) {
+                            const int64_t e = m * p.N + n;
+                            if (whole) {
+                                st_elem<W>(p.Z, e, cv[i] + sum[c0 + i]);
+                            } else {
+                                if constexpr (W == 1) red_add_u64(p.Z + e, sum[c0 + i]);
+                                else atomic_add_u128(p.Z + 2 * e, sum[c0 + i]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < ND; ++c) sum[c] = 0;
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == W_APROD) ptx::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 
 struct Plan {
@@ -1049,22 +1415,30 @@ struct Plan {
     size_t ap_bytes;
 };
 
-// tile rows of a launch: 64 or 128 (0 and anything else: 128)
+// The tile of a launch, from the launch table's `rows`: the wide tile when
+// rows is the ring's ND (32 for Z_2^64, 16 for Z_2^128), else row tiles of
+// 64 rows (rows == 64) or 128 (anything else).
+bool wide_rows(int rows, int words) { return rows == (words == 1 ? Cfg<1>::ND : Cfg<2>::ND); }
 int tile_rows(int rows) { return rows == 64 ? 64 : BM; }
 
+// Row tiles: m_tiles x n_tiles output tiles of R x ND, digit planes of L in
+// R-row tiles.  Wide tiles: m_tiles = column tiles (of WIDE_COLS columns),
+// n_tiles = row tiles (of ND rows), digit planes of L in ND-row tiles.
 Plan make_plan(int64_t M, int64_t K, int64_t N, int words, int one_half = 0, int rows = BM) {
     Plan pl{};
-    const int R = tile_rows(rows);
+    const bool wide = wide_rows(rows, words);
     pl.KD = words == 1 ? Cfg<1>::KD : Cfg<2>::KD;
     pl.ND = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
+    const int R = wide ? pl.ND : tile_rows(rows);   // rows of L per digit-plane tile
     const uint32_t a_stage = (words == 1 ? Cfg<1>::NDIG : Cfg<2>::NDIG) * (uint32_t)R * KS * 2;
-    pl.m_tiles = (M + R - 1) / R;
-    pl.n_tiles = (N + pl.ND - 1) / pl.ND;
+    const int64_t l_tiles = (M + R - 1) / R;
+    pl.m_tiles = wide ? (N + WIDE_COLS - 1) / WIDE_COLS : l_tiles;
+    pl.n_tiles = wide ? l_tiles : (N + pl.ND - 1) / pl.ND;
     pl.Kp = ((K + KS - 1) / KS) * KS;
     pl.S_tot = (int)((one_half ? 1 : 2) * pl.Kp / KS);
     pl.I = (pl.S_tot + pl.KD - 1) / pl.KD;
     pl.U = pl.m_tiles * pl.n_tiles * pl.I;
-    pl.ap_bytes = (size_t)pl.m_tiles * pl.S_tot * a_stage;
+    pl.ap_bytes = (size_t)l_tiles * pl.S_tot * a_stage;
     return pl;
 }
 
@@ -1113,36 +1487,51 @@ static_assert(sizeof(TcGroup<GMAX>) + 64 <= 32764, "kernel parameter space");
 // The dynamic shared-memory opt-in is set once per device and kernel (a host
 // call that also keeps graph capture free of attribute changes after the
 // first use).
-template <int W, int G, int R>
+// The GEMM kernel and its dynamic shared memory: row tiles of R rows, or the
+// wide tile.
+template <int W, int G, int R, bool WIDE> struct Gemm {
+    static constexpr uint32_t SMEM = WIDE ? WideLayout<W, G>::SMEM : Layout<W, G, R>::SMEM;
+    static constexpr int PR = WIDE ? Cfg<W>::ND : R;   // rows per digit-plane tile of L
+    static void (*kernel())(TcGroup<G>) {
+        if constexpr (WIDE) return ring_gemm_tc_wide_kernel<W, G>;
+        else return ring_gemm_tc_kernel<W, G, R>;
+    }
+};
+
+template <int W, int G, int R, bool WIDE = false>
 cudaError_t ensure_smem_attr() {
     static bool smem_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
     if (dev >= 0 && dev < 64 && smem_set[dev]) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_kernel<W, G, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Layout<W, G, R>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(Gemm<W, G, R, WIDE>::kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Gemm<W, G, R, WIDE>::SMEM);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) smem_set[dev] = true;
     return cudaSuccess;
 }
 
-// Fills entry j of a group for layer `a` (digit planes at Ap, R-row tiles).
-template <int W, int G, int R>
+// Fills entry j of a group for layer `a` (digit planes at Ap; R-row tiles,
+// or the wide tile).
+template <int W, int G, int R, bool WIDE = false>
 bool fill(TcGroup<G>& tg, PrologueGroup<G>& pg, int j, const GemmArgs& a, uint8_t* Ap, const Plan& pl) {
-    if (!make_map(&tg.tmF[j], a.F, a.K, a.N, W, Cfg<W>::ND)) return false;
+    constexpr int box = WIDE ? WIDE_COLS : Cfg<W>::ND;    // columns per raw tile of [B ; F]
+    if (!make_map(&tg.tmF[j], a.F, a.K, a.N, W, box)) return false;
     if (a.one_half) tg.tmB[j] = tg.tmF[j];
-    else if (!make_map(&tg.tmB[j], a.B, a.K, a.N, W, Cfg<W>::ND)) return false;
+    else if (!make_map(&tg.tmB[j], a.B, a.K, a.N, W, box)) return false;
     const int gm = a.gm > 0 ? a.gm : GM_DEFAULT;
     tg.p[j] = TcParams{Ap, a.Z, a.C, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND,
                        pl.m_tiles, pl.n_tiles, pl.U, gm, 0};
     pg.p[j] = PrologueParams{a.E, a.X, a.alpha, a.coef, a.one_half, a.M, a.K, a.N, pl.Kp, pl.S_tot, Ap, a.C, a.Z,
                              pl.I, pl.m_tiles, pl.n_tiles, gm};
-    // prologue blocks of 256 threads, 2 R threads per (row tile, stage)
-    pg.b_off[j + 1] = pg.b_off[j] + (pl.m_tiles * pl.S_tot * 2 * R + 255) / 256;
+    // prologue blocks of 256 threads, 2 PR threads per (plane tile, stage)
+    constexpr int PR = Gemm<W, G, R, WIDE>::PR;
+    const int64_t l_tiles = WIDE ? pl.n_tiles : pl.m_tiles;
+    pg.b_off[j + 1] = pg.b_off[j] + (l_tiles * pl.S_tot * 2 * PR + 255) / 256;
     return true;
 }
 
-template <int W, int G, int R>
+template <int W, int G, int R, bool WIDE = false>
 cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) {
     // one CTA per SM (fewer when the launch has fewer units); each layer's
     // CTA index is rotated by the units of the layers before it
@@ -1156,39 +1545,42 @@ cudaError_t launch_group(TcGroup<G>& tg, PrologueGroup<G>& pg, cudaStream_t st) 
         acc += tg.p[j].U;
     }
     tg.grid = pg.grid = grid;
-    cudaError_t e = launch_dependent(prologue_kernel<W, G, R>, dim3((unsigned)pg.b_off[pg.count]), dim3(256), 0, st, pg);
+    constexpr int PR = Gemm<W, G, R, WIDE>::PR;
+    cudaError_t e = launch_dependent(prologue_kernel<W, G, PR, WIDE>, dim3((unsigned)pg.b_off[pg.count]), dim3(256),
+                                     0, st, pg);
     if (e != cudaSuccess) return e;
-    e = ensure_smem_attr<W, G, R>();
+    e = ensure_smem_attr<W, G, R, WIDE>();
     if (e != cudaSuccess) return e;
     // programmatic dependent launch: the GEMM's CTAs may start (and set up)
     // while the prologue finishes; they wait for it in the kernel
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = Layout<W, G, R>::SMEM;
+    cfg.dynamicSmemBytes = Gemm<W, G, R, WIDE>::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, ring_gemm_tc_kernel<W, G, R>, tg);
+    e = cudaLaunchKernelEx(&cfg, Gemm<W, G, R, WIDE>::kernel(), tg);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template <int W, int R>
+template <int W, int R, bool WIDE = false>
 cudaError_t launch(const GemmArgs& a, uint8_t* Ap, const Plan& pl, cudaStream_t st) {
     TcGroup<1> tg{};
     PrologueGroup<1> pg{};
     tg.count = pg.count = 1;
     pg.b_off[0] = 0;
-    if (!fill<W, 1, R>(tg, pg, 0, a, Ap, pl)) return cudaErrorInvalidValue;
-    return launch_group<W, 1, R>(tg, pg, st);
+    if (!fill<W, 1, R, WIDE>(tg, pg, 0, a, Ap, pl)) return cudaErrorInvalidValue;
+    return launch_group<W, 1, R, WIDE>(tg, pg, st);
 }
 
-// One launch pair for the layers order[i0 .. i0 + cnt) (cnt <= G), R-row tiles.
-template <int W, int G, int R>
+// One launch pair for the layers order[i0 .. i0 + cnt) (cnt <= G), R-row tiles
+// or the wide tile.
+template <int W, int G, int R, bool WIDE = false>
 cudaError_t launch_chunk(const GemmArgs* a, uint8_t* const* Ap, const int* order, int cnt, cudaStream_t st) {
     static_assert(alignof(TcGroup<G>) >= 64, "tensor map alignment");
     auto* tg = new (std::nothrow) TcGroup<G>;
@@ -1199,10 +1591,11 @@ cudaError_t launch_chunk(const GemmArgs* a, uint8_t* const* Ap, const int* order
         pg->b_off[0] = 0;
         for (int j = 0; j < cnt && e == cudaSuccess; ++j) {
             const GemmArgs& x = a[order[j]];
-            if (!fill<W, G, R>(*tg, *pg, j, x, Ap[order[j]], make_plan(x.M, x.K, x.N, W, x.one_half, R)))
+            const int rows = WIDE ? Cfg<W>::ND : R;
+            if (!fill<W, G, R, WIDE>(*tg, *pg, j, x, Ap[order[j]], make_plan(x.M, x.K, x.N, W, x.one_half, rows)))
                 e = cudaErrorInvalidValue;
         }
-        if (e == cudaSuccess) e = launch_group<W, G, R>(*tg, *pg, st);
+        if (e == cudaSuccess) e = launch_group<W, G, R, WIDE>(*tg, *pg, st);
     }
     delete tg;
     delete pg;
@@ -1213,13 +1606,15 @@ constexpr int GSMALL = 16;   // small groups use a kernel with a smaller paramet
 
 // dynamic shared memory plus the grouped kernels' static layer table stay
 // within the 227 KB a CTA may use (a launch over the limit fails)
-template <int W, int G, int R = BM> constexpr bool fits_smem() {
-    return Layout<W, G, R>::SMEM + (G > 1 ? G * sizeof(TcParams) : 0) <= 227 * 1024;
+template <int W, int G, int R = BM, bool WIDE = false> constexpr bool fits_smem() {
+    return Gemm<W, G, R, WIDE>::SMEM + (G > 1 ? G * sizeof(TcParams) : 0) <= 227 * 1024;
 }
 static_assert(fits_smem<1, 1>() && fits_smem<2, 1>() && fits_smem<1, GSMALL>() && fits_smem<2, GSMALL>() &&
                   fits_smem<1, GMAX>() && fits_smem<2, GMAX>() && fits_smem<1, 1, 64>() && fits_smem<2, 1, 64>() &&
                   fits_smem<1, GSMALL, 64>() && fits_smem<2, GSMALL, 64>() && fits_smem<1, GMAX, 64>() &&
-                  fits_smem<2, GMAX, 64>(),
+                  fits_smem<2, GMAX, 64>() && fits_smem<1, 1, BM, true>() && fits_smem<2, 1, BM, true>() &&
+                  fits_smem<1, GSMALL, BM, true>() && fits_smem<2, GSMALL, BM, true>() &&
+                  fits_smem<1, GMAX, BM, true>() && fits_smem<2, GMAX, BM, true>(),
               "shared memory of a TC GEMM instantiation");
 
 // A layer with units for at least LONG_WAVES waves of the grid gains little
@@ -1235,12 +1630,13 @@ bool long_layer(int64_t M, int64_t K, int64_t N, int words, int one_half, int sm
 // The layers idx[0 .. n) (all with R-row tiles) in launches of up to GMAX
 // layers; layer i's digit planes at Ap[i].  Every layer is eligible and has
 // the ring width W.
-template <int W, int R>
+template <int W, int R, bool WIDE = false>
 cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t* const* Ap, cudaStream_t st) {
+    constexpr int rows = WIDE ? Cfg<W>::ND : R;
     // layers with more K intervals first, so that whole tiles of the long
     // layers line up with the CTAs' ranges (the order changes no result)
     std::vector<std::pair<int, int>> by_iv;   // (intervals per tile, layer)
-    for (int i : order) by_iv.push_back({make_plan(a[i].M, a[i].K, a[i].N, W, a[i].one_half, R).I, i});
+    for (int i : order) by_iv.push_back({make_plan(a[i].M, a[i].K, a[i].N, W, a[i].one_half, rows).I, i});
     std::stable_sort(by_iv.begin(), by_iv.end(),
                      [](const std::pair<int, int>& x, const std::pair<int, int>& y) { return x.first > y.first; });
     for (size_t j = 0; j < by_iv.size(); ++j) order[j] = by_iv[j].second;
@@ -1248,8 +1644,8 @@ cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t*
     const int sms = sm_count();
     std::vector<int> rest;
     for (int i : order) {
-        if (long_layer(a[i].M, a[i].K, a[i].N, W, a[i].one_half, sms, R)) {
-            if (e == cudaSuccess) e = launch_chunk<W, 1, R>(a, Ap, &i, 1, st);
+        if (long_layer(a[i].M, a[i].K, a[i].N, W, a[i].one_half, sms, rows)) {
+            if (e == cudaSuccess) e = launch_chunk<W, 1, R, WIDE>(a, Ap, &i, 1, st);
         } else {
             rest.push_back(i);
         }
@@ -1258,22 +1654,25 @@ cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t*
     for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += GMAX) {
         const int cnt = n - i0 < GMAX ? n - i0 : GMAX;
         // a lone layer takes the one-layer kernel (parameters at constant offsets)
-        e = cnt == 1        ? launch_chunk<W, 1, R>(a, Ap, rest.data() + i0, cnt, st)
-            : cnt <= GSMALL ? launch_chunk<W, GSMALL, R>(a, Ap, rest.data() + i0, cnt, st)
-                            : launch_chunk<W, GMAX, R>(a, Ap, rest.data() + i0, cnt, st);
+        e = cnt == 1        ? launch_chunk<W, 1, R, WIDE>(a, Ap, rest.data() + i0, cnt, st)
+            : cnt <= GSMALL ? launch_chunk<W, GSMALL, R, WIDE>(a, Ap, rest.data() + i0, cnt, st)
+                            : launch_chunk<W, GMAX, R, WIDE>(a, Ap, rest.data() + i0, cnt, st);
     }
     return e;
 }
 
-// Layers [0, n): those with 128-row tiles and those with 64-row tiles in
-// launches of their own (one kernel instantiation per tile height).
+// Layers [0, n): those with 128-row tiles, those with 64-row tiles and those
+// with the wide tile in launches of their own (one kernel instantiation per
+// tile).
 template <int W>
 cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st) {
-    std::vector<int> big, small;
-    for (int i = 0; i < n; ++i) (tile_rows(a[i].rows) == 64 ? small : big).push_back(i);
+    std::vector<int> big, small, wide;
+    for (int i = 0; i < n; ++i)
+        (wide_rows(a[i].rows, W) ? wide : tile_rows(a[i].rows) == 64 ? small : big).push_back(i);
     cudaError_t e = cudaSuccess;
     if (!big.empty()) e = launch_many_rows<W, BM>(a, big, Ap, st);
     if (e == cudaSuccess && !small.empty()) e = launch_many_rows<W, 64>(a, small, Ap, st);
+    if (e == cudaSuccess && !wide.empty()) e = launch_many_rows<W, BM, true>(a, wide, Ap, st);
     return e;
 }
 
@@ -1284,7 +1683,7 @@ bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words, int rows) {
     if (M <= 8 || N < 1 || K < 1) return false;        // skinny layers stream better on the SIMT GEMV
     if (words == 1 && N % 2 != 0) return false;       // TMA row stride: 16-byte multiple
     if (K > (int64_t(1) << 30) || N > (int64_t(1) << 28)) return false;
-    const int R = tile_rows(rows);
+    const int R = wide_rows(rows, words) ? (words == 1 ? Cfg<1>::ND : Cfg<2>::ND) : tile_rows(rows);
     if ((M + R - 1) / R > 65535) return false;
     return true;
 }
@@ -1296,22 +1695,25 @@ bool gemm_tc_eligible(int64_t M, int64_t K, int64_t N, int words) {
     return macs >= (words == 1 ? (double)(1 << 22) : (double)(1 << 20));
 }
 
-// the digit planes of either tile height fit (a 64-row tiling never needs
-// more than a 128-row one: ceil(M / 64) <= 2 ceil(M / 128))
+// the digit planes of every tile fit (the largest of the three tilings)
 size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_half) {
     if (!gemm_tc_feasible(M, K, N, words)) return 0;
+    const int wide = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
     size_t b = make_plan(M, K, N, words, one_half, BM).ap_bytes;
-    if (gemm_tc_feasible(M, K, N, words, 64)) b = std::max(b, make_plan(M, K, N, words, one_half, 64).ap_bytes);
+    for (int rows : {64, wide})
+        if (gemm_tc_feasible(M, K, N, words, rows)) b = std::max(b, make_plan(M, K, N, words, one_half, rows).ap_bytes);
     return align256(b);
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
-    const int R = tile_rows(a.rows);
-    if (!gemm_tc_feasible(a.M, a.K, a.N, a.words, R)) return cudaErrorNotSupported;
-    Plan pl = make_plan(a.M, a.K, a.N, a.words, a.one_half, R);
+    const bool wide = wide_rows(a.rows, a.words);
+    const int rows = wide ? a.rows : tile_rows(a.rows);
+    if (!gemm_tc_feasible(a.M, a.K, a.N, a.words, rows)) return cudaErrorNotSupported;
+    Plan pl = make_plan(a.M, a.K, a.N, a.words, a.one_half, rows);
     if (ws_bytes < align256(pl.ap_bytes) || ws == nullptr) return cudaErrorInvalidValue;
     uint8_t* Ap = static_cast<uint8_t*>(ws);
-    if (R == 64) return a.words == 1 ? launch<1, 64>(a, Ap, pl, st) : launch<2, 64>(a, Ap, pl, st);
+    if (wide) return a.words == 1 ? launch<1, BM, true>(a, Ap, pl, st) : launch<2, BM, true>(a, Ap, pl, st);
+    if (rows == 64) return a.words == 1 ? launch<1, 64>(a, Ap, pl, st) : launch<2, 64>(a, Ap, pl, st);
     return a.words == 1 ? launch<1, BM>(a, Ap, pl, st) : launch<2, BM>(a, Ap, pl, st);
 }
 
@@ -1331,13 +1733,16 @@ cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap,
 
 int gemm_tc_grouped_launches(const int64_t* M, const int64_t* K, const int64_t* N, int n, int words) {
     const int sms = sm_count();
-    int alone = 0, rest[2] = {0, 0};
+    int alone = 0, rest[3] = {0, 0, 0};
     for (int i = 0; i < n; ++i) {
-        const int R = tile_rows(gemm_choice(M[i], K[i], N[i], words).rows);
-        if (long_layer(M[i], K[i], N[i], words, 0, sms, R)) ++alone;
-        else ++rest[R == 64];
+        const int rows = gemm_choice(M[i], K[i], N[i], words).rows;
+        const int kind = wide_rows(rows, words) ? 2 : tile_rows(rows) == 64 ? 1 : 0;
+        if (long_layer(M[i], K[i], N[i], words, 0, sms, kind == 2 ? rows : tile_rows(rows))) ++alone;
+        else ++rest[kind];
     }
-    return 2 * alone + 2 * ((rest[0] + GMAX - 1) / GMAX) + 2 * ((rest[1] + GMAX - 1) / GMAX);
+    int pairs = alone;
+    for (int k = 0; k < 3; ++k) pairs += (rest[k] + GMAX - 1) / GMAX;
+    return 2 * pairs;
 }
 
 // ---------------------------------------------------------------------------

@@ -25,6 +25,9 @@
 
 namespace mpcl {
 
+// the wide tensor-core tile: this many rows by 128 columns (32 for Z_2^64, 16 for Z_2^128)
+int wide_tile_rows(int words) { return words == 1 ? 32 : 16; }
+
 namespace {
 
 using Key = std::tuple<int, int64_t, int64_t, int64_t>;
@@ -37,14 +40,19 @@ std::map<Key, Choice>& table() {
 
 bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
     if (c.path == 1)
-        return (c.rows == 64 || c.rows == 128) && gemm_tc_feasible(M, K, N, words, c.rows) && c.gm >= 1 &&
-               c.gm <= 64;
+        return (c.rows == 64 || c.rows == 128 || c.rows == wide_tile_rows(words)) &&
+               gemm_tc_feasible(M, K, N, words, c.rows) && c.gm >= 1 && c.gm <= 64;
     return c.path == 0 && c.waves >= 0 && c.waves <= 64 && (c.rows == 0 || c.rows == 16 || c.rows == 64);
 }
 
-// Built-in tile height: 64-row tiles where the layer has at most 64 rows (an
-// M = 64 MMA costs as much as an M = 128 one, so they pay only there).
-int default_rows(int64_t M) { return M <= 64 ? 64 : 128; }
+// Built-in tile: the wide tile (128 columns on the TMEM lanes, the layer's rows
+// in the stacked operand) for layers of at most two of its row tiles, 64-row
+// tiles up to 64 rows, 128-row tiles above (an M = 64 MMA costs as much as an
+// M = 128 one).
+int default_rows(int64_t M, int words) {
+    if (M <= 2 * wide_tile_rows(words)) return wide_tile_rows(words);
+    return M <= 64 ? 64 : 128;
+}
 
 }  // namespace
 
@@ -59,7 +67,7 @@ Choice gemm_choice(int64_t M, int64_t K, int64_t N, int words) {
     c.gm = 0;
     c.waves = 0;
     c.tuned = 0;
-    c.rows = c.path == 1 ? default_rows(M) : 0;
+    c.rows = c.path == 1 ? default_rows(M, words) : 0;
     return c;
 }
 
@@ -129,11 +137,13 @@ int mpc_autotune(const mpc_layer* layers, int count, void* stream) {
         std::vector<mpcl::Choice> cands;
         const bool tc = mpcl::gemm_tc_feasible(M, K, N, w);
         const double macs = 2.0 * (double)M * (double)K * (double)N;
-        // tile heights: 64 rows only where the layer has at most 64 rows (it
-        // would double the MMA work of taller layers)
+        // tiles: 64 rows only where the layer has at most 64 rows (it would
+        // double the MMA work of taller layers), the wide tile up to 128 rows
         if (tc)
-            for (int rows : {128, 64}) {
-                if (rows == 64 && (M > 64 || !mpcl::gemm_tc_feasible(M, K, N, w, 64))) continue;
+            for (int rows : {128, 64, mpcl::wide_tile_rows(w)}) {
+                if (rows == 64 && M > 64) continue;
+                if (rows == mpcl::wide_tile_rows(w) && M > 128) continue;
+                if (!mpcl::gemm_tc_feasible(M, K, N, w, rows)) continue;
                 for (int gm : {1, 4, 8, 16}) cands.push_back(mpcl::Choice{1, gm, 0, 1, rows});
             }
         // the integer pipes are far slower on large products: not timed there;

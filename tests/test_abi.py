@@ -108,8 +108,8 @@ def test_grouped_host_logic(lib):
     cws = abi.mpc_workspace_size_grouped(layers, abi.MPC_WS_TAG_COMPACT)
     assert cws == sum(-(-abi.mpc_workspace_size(L, abi.MPC_WS_TAG_COMPACT) // 256) * 256 for L in layers)
     # one prologue + GEMM pair for the two tensor-core layers with 128-row tiles, one for the
-    # layer with 64-row tiles (M = 64), one kernel for the integer-pipe layer
-    assert abi.mpc_autotune_choice(layers[3])[4] == 64
+    # layer with the wide tile (M = 64: two of its 32-row tiles), one kernel for the integer-pipe layer
+    assert abi.mpc_autotune_choice(layers[3])[4] == 32
     assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_SHARE) == 2 + 2 + 1
     # 60 + 30 tensor-core layers: one launch pair per tile height (at most 64 layers each)
     assert abi.mpc_launch_count_grouped(layers * 30, abi.MPC_WS_TAG_FULL) == 2 * 2 + 30
@@ -154,7 +154,12 @@ def test_launch_table_host_logic(lib, tmp_path):
     skinny = abi.make_layer(4, 512, 512)
     assert abi.mpc_autotune_choice(big) == (1, 0, 0, False, 128)      # built-in rule
     assert abi.mpc_autotune_choice(small)[0] == 0
-    assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512)) == (1, 0, 0, False, 64)
+    assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512)) == (1, 0, 0, False, 32)     # wide tile
+    assert abi.mpc_autotune_choice(abi.make_layer(65, 4608, 512)) == (1, 0, 0, False, 128)
+    assert abi.mpc_autotune_choice(abi.make_layer(32, 4608, 512, 64, 64)) == (1, 0, 0, False, 16)
+    abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=32)                 # the Z_2^64 wide tile
+    with pytest.raises(abi.MpcError):
+        abi.mpc_autotune_set(abi.make_layer(64, 128, 64, 64, 64), 1, 4, 0, tile_rows=32)   # Z_2^128: 16
     ws_before = abi.mpc_workspace_size(small, abi.MPC_WS_SHARE)
     abi.mpc_autotune_set(small, 1, 4, 0)
     assert abi.mpc_autotune_choice(small) == (1, 4, 0, True, 128)
@@ -172,7 +177,7 @@ def test_launch_table_host_logic(lib, tmp_path):
     with pytest.raises(abi.MpcError):
         abi.mpc_autotune_set(small, 1, 0, 0)
     with pytest.raises(abi.MpcError):
-        abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=32)      # tensor-core tile heights: 128 or 64
+        abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=48)      # tensor-core tiles: 128, 64 or the wide tile
     with pytest.raises(abi.MpcError):
         abi.mpc_autotune_set(small, 0, 0, 2, tile_rows=128)     # integer pipes: 64, 16 or 0
     f = tmp_path / "table.txt"

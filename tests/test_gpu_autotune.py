@@ -22,13 +22,17 @@ def _lib():
     abi.mpc_autotune_clear()
 
 
+def rows_of(rows, ring):
+    return (32 if ring.words == 1 else 16) if rows == "wide" else rows
+
+
 def operands(ring, M, K, N, seed):
     u = lambda t, shape: synth.uniform(seed, t, 1, shape, ring.bits)
     return u(1, (M, K)), u(2, (K, N)), u(3, (M, K)), u(4, (K, N)), u(5, (M, N))
 
 
 CHOICES = [(1, 1, 0), (1, 4, 0), (1, 16, 0), (1, 64, 0), (0, 0, 1), (0, 0, 2), (0, 0, 8)]
-TILE_ROWS = (128, 64)          # tensor cores
+TILE_ROWS = (128, 64, "wide")  # tensor cores ("wide": 128 columns x 32 rows, Z_2^64, or 16, Z_2^128)
 SIMT_ROWS = (0, 64, 16)        # integer pipes (0: chosen by grid size)
 
 
@@ -43,6 +47,7 @@ def test_every_choice_is_exact(ring, shape):
     L = abi.make_layer(M, K, N, ring.k, ring.s, 0, 2)
     for path, gm, waves in CHOICES:
         for rows in (TILE_ROWS if path else SIMT_ROWS):
+            rows = rows_of(rows, ring)
             abi.mpc_autotune_set(L, path, gm if path else 0, waves, tile_rows=rows)
             assert abi.mpc_gemm_path(L) == path
             assert abi.mpc_autotune_choice(L)[4] == rows
@@ -56,9 +61,9 @@ def test_every_choice_is_exact(ring, shape):
 # ragged heights around both tile heights (M <= 8 runs on the integer pipes
 # only), ragged K (one partial 16-deep stage; a K below one stage) and N
 @pytest.mark.parametrize("ring", [synth.Z64, synth.Z128], ids=["w1", "w2"])
-@pytest.mark.parametrize("M", [9, 17, 63, 64, 65, 130])
-def test_both_tile_heights_are_exact(ring, M):
-    for K, N in ((27, 34), (300, 96), (5, 66)):
+@pytest.mark.parametrize("M", [9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 130])
+def test_every_tile_is_exact(ring, M):
+    for K, N in ((27, 34), (300, 96), (5, 66), (40, 258)):
         E, F, A, B, C = operands(ring, M, K, N, 1000 * M + K)
         mA, mB, mC = operands(ring, M, K, N, 2000 * M + K)[2:]
         alpha = synth.uniform(M, 9, 0, (1,), ring.bits)
@@ -66,6 +71,7 @@ def test_both_tile_heights_are_exact(ring, M):
         want_t = O.linear_tag_full(ring.bits, alpha, E, F, mA, mB, mC)
         L = abi.make_layer(M, K, N, ring.k, ring.s, 0, 2)
         for rows in TILE_ROWS:
+            rows = rows_of(rows, ring)
             for gm in (1, 8):
                 abi.mpc_autotune_set(L, 1, gm, 0, tile_rows=rows)
                 Z = empty_like_ring((M, N), ring.words)
@@ -78,11 +84,12 @@ def test_both_tile_heights_are_exact(ring, M):
     assert abi.mpc_device_status() == 0
 
 
-def test_built_in_rule_takes_64_row_tiles_for_short_layers():
+def test_built_in_rule_takes_short_tiles_for_short_layers():
     abi.mpc_autotune_clear()
-    assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512))[::4] == (1, 64)
+    assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512))[::4] == (1, 32)        # wide
     assert abi.mpc_autotune_choice(abi.make_layer(65, 4608, 512))[::4] == (1, 128)
-    assert abi.mpc_autotune_choice(abi.make_layer(16, 2304, 512, 64, 64))[::4] == (1, 64)
+    assert abi.mpc_autotune_choice(abi.make_layer(16, 2304, 512, 64, 64))[::4] == (1, 16)
+    assert abi.mpc_autotune_choice(abi.make_layer(40, 2304, 512, 64, 64))[::4] == (1, 64)
 
 
 @pytest.mark.parametrize("ring", [synth.Z64, synth.Z128], ids=["w1", "w2"])
@@ -91,9 +98,10 @@ def test_grouped_with_mixed_choices(ring):
     integer pipes (the tensor-core layers of each tile height share a
     persistent launch)."""
     shapes = [(300, 200, 96), (1100, 64, 66), (64, 256, 256), (520, 128, 130), (40, 300, 96), (17, 1000, 34),
-              (64, 27, 64), (130, 600, 66)]
+              (64, 27, 64), (130, 600, 66), (12, 700, 300), (100, 64, 130), (33, 1500, 258)]
     choices = [(1, 1, 0, 128), (0, 0, 4, 16), (1, 16, 0, 64), (1, 4, 0, 128), (1, 8, 0, 64), (1, 1, 0, 64),
-               (1, 8, 0, 128), (0, 0, 2, 64)]
+               (1, 8, 0, 128), (0, 0, 2, 64), (1, 8, 0, "wide"), (1, 1, 0, "wide"), (1, 4, 0, "wide")]
+    choices = [(p_, g_, w_, rows_of(r_, ring)) for p_, g_, w_, r_ in choices]
     layers = [abi.make_layer(M, K, N, ring.k, ring.s) for M, K, N in shapes]
     for L, (path, gm, waves, rows) in zip(layers, choices):
         abi.mpc_autotune_set(L, path, gm, waves, tile_rows=rows)
@@ -116,7 +124,7 @@ def test_autotune_fills_the_table(tmp_path):
         path, gm, waves, tuned, rows = abi.mpc_autotune_choice(L)
         assert tuned
         assert path in (0, 1)
-        assert rows == (0 if path == 0 else rows) and rows in (0, 64, 128)
+        assert rows in ((0, 16, 64) if path == 0 else (128, 64, 32))
     assert abi.mpc_autotune_choice(layers[2])[0] == 0      # M <= 8: integer pipes only
     f = tmp_path / "t.txt"
     assert abi.mpc_autotune_save(str(f)) == 4
