@@ -230,19 +230,25 @@ int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
  * M = 128 one, so the 64-row tile halves only the shared-memory bytes of the
  * left operand); or the wide tile, tile_rows = 32 for Z_2^64 and 16 for
  * Z_2^128, which puts 128 output columns on the tensor core's M side and that
- * many of the layer's rows on its N side (for layers with few rows) -- and
+ * many of the layer's rows on its N side (for layers with few rows); or the
+ * tall tile, tile_rows = -128: 128-row tiles whose left operand [E | X] the
+ * GEMM turns into digit planes itself, with the c E term moved to the right
+ * operand ([E | X + cE].[B ; F] = [E | X].[B + cF ; F]), so that no digit
+ * plane of the left operand goes through memory (for tall, narrow layers;
+ * needs K words even for the 2-D loads) -- and
  * `swizzle` tiles per tile-order group (1-64); or path 0, the integer-pipe kernels, with tiles
  * of `tile_rows` rows (64 or 16; 0 = 16 when 64-row tiles would give fewer
  * blocks than SMs, else 64; skinny layers with M <= 8 use a GEMV whatever the
  * value) and a K-split target of `waves` x 152 blocks (0 = default).  Untuned
  * shapes use a built-in rule (tensor cores from 2^22 ring MACs, 2^20 for
  * Z_2^128; the wide tile up to two of its row tiles, 64-row tiles up to
- * M = 64).  The table is process-wide and thread-safe; workspace
+ * M = 64, the tall tile for Z_2^64 layers with N <= 64).  The table is process-wide and thread-safe; workspace
  * sizes do not depend on it.
  *
  * mpc_autotune: for each distinct shape of layers[count], times the
  *   candidates (128-row tiles, 64-row tiles for M <= 64, the wide tile for
- *   M <= 128, each with swizzle 1/4/8/16 on the tensor cores; tile heights 64 and 16 with K-split 1/2/4/8
+ *   M <= 128, the tall tile for M >= 128, each with swizzle 1/4/8/16 on the
+ *   tensor cores; tile heights 64 and 16 with K-split 1/2/4/8
  *   on the integer pipes, below 2^31 ring MACs) on `stream` and stores the
  *   fastest.  Synchronous;
  *   allocates and frees its own scratch operands; do not call it during

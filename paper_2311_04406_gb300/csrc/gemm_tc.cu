@@ -1406,6 +1406,489 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
 }
 
 // ---------------------------------------------------------------------------
+// the tall tile: the left operand converted inside the GEMM
+//
+// Row tiles of 128 x ND as above, but L's digit planes never go through HBM:
+// the c E term moves to the right operand, [E | X + cE] . [B ; F] =
+// [E | X] . [B + cF ; F], so each 16-deep stage of L is one raw tile of E or X
+// (128 rows x 16 K, loaded by 2-D TMA with the 128-byte swizzle so that the
+// converters' row reads hit distinct banks) that the converter warps turn
+// into the NDIG A planes.  The right operand R' = [B + cF ; F] is small for
+// the layers this tile serves (M >> N); a prologue writes its digit planes in
+// the stacked layout (per ND-column tile and stage: plane j holds rows
+// j ND .. j ND + ND - 1), copied one 8 KB stage at a time.  The MMAs, the
+// schedule and the drain's arithmetic are those of the 128-row tile; the
+// drain stores each lane's row directly (16-byte vectors along the row).
+// Stores of whole tiles are C + sum; split tiles add with atomics into Z,
+// which the prologue pre-sets to C.
+
+template <int W, int G = 1> struct TallLayout {
+    static constexpr int STAGES = Cfg<W>::STAGES;
+    static constexpr int RAW = W == 1 ? 3 : 2;               // raw L tiles in flight
+    static constexpr uint32_t A_PLANE = a_plane_bytes<BM>();          // 4 KB
+    static constexpr uint32_t A_STAGE = Cfg<W>::NDIG * A_PLANE;
+    static constexpr uint32_t RAW_BOX = BM * 128;                     // 128 rows x 128 bytes
+    static constexpr uint32_t RAW_TILE = RAW_BOX * W;                 // 16 K values: W boxes
+    static constexpr int NBARS = 2 * MAX_STAGES + 2 * RAW + 2 + 2 + 1 + NINFO;
+    static constexpr uint32_t OFF_B = STAGES * A_STAGE;
+    static constexpr uint32_t OFF_RAW = OFF_B + STAGES * B_STAGE_BYTES;
+    static constexpr uint32_t OFF_BAR = OFF_RAW + RAW * RAW_TILE;
+    static constexpr uint32_t OFF_INFO = (OFF_BAR + NBARS * 8 + 16 + 15) / 16 * 16;
+    static constexpr uint32_t SMEM = OFF_INFO + NINFO * 16;
+};
+static_assert(TallLayout<1>::OFF_RAW % 1024 == 0 && TallLayout<2>::OFF_RAW % 1024 == 0,
+              "the 128-byte swizzle needs 1024-byte aligned raw tiles");
+static_assert(TallLayout<1>::OFF_BAR % 16 == 0 && TallLayout<2>::OFF_BAR % 16 == 0, "barrier alignment");
+
+// Prologue of the tall tile: digit planes of R' = [B + cF ; F] in the stacked
+// layout, and Z = C on the tiles computed in pieces.  2 ND threads per
+// (column tile, stage): thread (column nl, K half kh) converts 8 K values of
+// one column (lanes read consecutive columns of a row of R').
+struct PrologueRParams {
+    const u64 *B, *F, *alpha;
+    int coef;
+    int64_t M, K, N;
+    int64_t Kp;
+    int S_tot;
+    uint8_t* Rp;
+    const u64* C;
+    u64* Z;
+    int I;
+    int64_t m_tiles, n_tiles;
+    int gm;
+};
+
+template <int G> struct PrologueRGroup {
+    int count;
+    int64_t b_off[G + 1];
+    PrologueRParams p[G];
+    int grid;
+};
+
+template <int W>
+__device__ __forceinline__ void prologue_r_body(const PrologueRParams& p, int grid, int64_t id, int64_t nthreads) {
+    constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND;
+    {
+        // Z = C on split tiles (as the row-tile prologue does)
+        constexpr int VPR = ND * W / 2;
+        const int64_t blk = id >> 8, nblk = nthreads >> 8;
+        const int tid = (int)(id & 255);
+        const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C);
+        ulonglong2* z2 = reinterpret_cast<ulonglong2*>(p.Z);
+        const int64_t T = p.m_tiles * p.n_tiles;
+        const Sched sc = sched_of(T * p.I, p.I, grid);
+        for (int64_t t = blk; t < T; t += nblk) {
+            const int64_t u = t * p.I;
+            if (u + p.I <= range_end_of(sc, u)) continue;
+            int64_t mt, nt;
+            tile_mn(t, p.m_tiles, p.n_tiles, p.gm, &mt, &nt);
+            for (int q = tid; q < BM * VPR; q += 256) {
+                const int r = q / VPR, j = q - r * VPR;
+                const int64_t m = mt * BM + r;
+                const int64_t n = nt * ND + (int64_t)j * 2 / W;
+                if (m >= p.M || n >= p.N) continue;
+                const int64_t i = (m * p.N + n) * W / 2;
+                z2[i] = c2 ? __ldg(c2 + i) : make_ulonglong2(0, 0);
+            }
+        }
+    }
+    const int64_t per_tile = (int64_t)p.S_tot * 2 * ND;
+    if (id >= p.n_tiles * per_tile) return;
+    const int nl = (int)(id % ND), kh = (int)((id / ND) & 1);
+    const int64_t kstage = (id / (2 * ND)) % p.S_tot;
+    const int64_t nt = id / per_tile;
+    const int64_t n = nt * ND + nl;
+    const int64_t kp0 = kstage * KS + kh * 8;     // index in [0, 2 Kp)
+    const bool first = kp0 < p.Kp;
+    const int64_t kk = first ? kp0 : kp0 - p.Kp;
+    using T = typename Elem<W>::T;
+    T cv = 0;
+    if (first && p.coef != COEF_ZERO) cv = p.coef == COEF_ONE ? (T)1 : ld_elem<W>(p.alpha, 0);
+    u64 x[8 * W];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        T v = 0;
+        if (n < p.N && kk + e < p.K) {
+            const int64_t i = (kk + e) * p.N + n;
+            v = ldg_elem<W>(first ? p.B : p.F, i);
+            if (first && p.coef != COEF_ZERO) v += cv * ldg_elem<W>(p.F, i);
+        }
+        x[W * e] = (u64)v;
+        if constexpr (W == 2) x[W * e + 1] = (u64)(v >> 64);
+    }
+    Biased<W> b[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) b[e] = biased<W>(x + W * e);
+    uint8_t* dst = p.Rp + ((size_t)nt * p.S_tot + kstage) * B_STAGE_BYTES + (nl >> 3) * CORE_SBO + kh * CORE_LBO +
+                   (nl & 7) * 16;
+#pragma unroll
+    for (int t = 0; t < NDIG; ++t) {
+        const int wi = t >> 2;
+        const uint32_t byte = t & 3;
+        uint4 o;
+        o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
+        o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
+        o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
+        o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
+        *reinterpret_cast<uint4*>(dst + t * (ND * KS * 2)) = o;
+    }
+}
+
+template <int W, int G>
+__global__ void __launch_bounds__(256) prologue_r_kernel(const __grid_constant__ PrologueRGroup<G> g) {
+    ptx::grid_dep_launch();
+    ptx::grid_dep_wait();
+    int gi = 0;
+    if constexpr (G > 1) {
+        int lo = 0, hi = g.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.b_off[mid] <= (int64_t)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        gi = lo;
+    }
+    const int64_t lb = (int64_t)blockIdx.x - g.b_off[gi];
+    const int64_t nb = g.b_off[gi + 1] - g.b_off[gi];
+    prologue_r_body<W>(g.p[gi], g.grid, lb * 256 + threadIdx.x, nb * 256);
+}
+
+// byte offset of K value k (0..15) of row m in a raw tile of the tall kernel:
+// W boxes of 128 rows x 128 bytes (8 W K values), 16-byte chunks swizzled by
+// the row (TMA's 128-byte swizzle: chunk c of row m sits at chunk c ^ (m % 8))
+template <int W>
+__device__ __forceinline__ uint32_t raw_l_offset(int m, int k) {
+    constexpr int PER_BOX = 8 * (W == 1 ? 2 : 1);          // K values per 128-byte box row
+    const int box = k / PER_BOX, kb = k % PER_BOX;
+    const int chunk = (kb * 8 * W) / 16, within = (kb * 8 * W) % 16;
+    return (uint32_t)box * TallLayout<W>::RAW_BOX + (uint32_t)m * 128 + (uint32_t)((chunk ^ (m & 7)) * 16 + within);
+}
+
+template <int W, int G>
+__global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __grid_constant__ TcGroup<G> g) {
+    using Lay = TallLayout<W, G>;
+    constexpr int NDIG = Cfg<W>::NDIG, ND = Cfg<W>::ND, STAGES = Lay::STAGES, RAW = Lay::RAW;
+    constexpr uint32_t A_STAGE = Lay::A_STAGE, A_PLANE = Lay::A_PLANE, RAW_TILE = Lay::RAW_TILE;
+    using Sum = typename Elem<W>::T;
+
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;                       // L digit planes (converter warps)
+    uint8_t* sB = smem + Lay::OFF_B;          // R' stack (copies of the prologue's planes)
+    uint8_t* sRaw = smem + Lay::OFF_RAW;      // raw 128 x 16 tiles of E or X (TMA, swizzled)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Lay::OFF_BAR);
+    uint64_t* full = bars;
+    uint64_t* empty = full + MAX_STAGES;
+    uint64_t* rawFull = empty + MAX_STAGES;
+    uint64_t* rawEmpty = rawFull + RAW;
+    uint64_t* accFull = rawEmpty + RAW;
+    uint64_t* accEmpty = accFull + 2;
+    uint64_t* mmaDone = accEmpty + 2;
+    uint64_t* infoFull = mmaDone + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(infoFull + NINFO);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int4* info = reinterpret_cast<int4*>(smem + Lay::OFF_INFO);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t cta = blockIdx.x;
+    __shared__ TcParams sp[G > 1 ? G : 1];
+    if constexpr (G > 1) {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(&g.p[0]);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(sp);
+        const int nw = g.count * (int)(sizeof(TcParams) / 8);
+        for (int i = threadIdx.x; i < nw; i += NTHREADS) dst[i] = src[i];
+    }
+    const int count = g.count, grid = g.grid;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1 + NCONV / 32);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int r = 0; r < RAW; ++r) {
+            ptx::mbar_init(&rawFull[r], 1);
+            ptx::mbar_init(&rawEmpty[r], NCONV / 32);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&accFull[b], 1);
+            ptx::mbar_init(&accEmpty[b], NDRAIN / 32);
+        }
+        ptx::mbar_init(mmaDone, 1);
+        for (int i = 0; i < NINFO; ++i) ptx::mbar_init(&infoFull[i], 1);
+        *abort_flag = 0;
+        ptx::fence_barrier_init();
+    }
+    if (warp == W_APROD) {
+        ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    ptx::grid_dep_wait();
+    const int64_t nv = G == 1 ? cta_units(sched_of(g.p[0].U, g.p[0].I, grid), cta)
+                              : cta_total(sp, count, grid, cta);
+
+    if (warp == W_APROD) {
+        // the R' stack: one 8 KB stage per 16-deep K step
+        int it = 0;
+        bool ok = true;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
+            const uint8_t* src = p.Ap + ((size_t)x.nt * p.S_tot + (size_t)x.ii * p.KD) * B_STAGE_BYTES;
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int s = it % STAGES;
+                const bool free_ = ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, free_)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                const uint32_t leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &full[s], B_STAGE_BYTES);
+                ptx::bulk_g2s_if(leader, sB + s * B_STAGE_BYTES, src + (size_t)j * B_STAGE_BYTES, B_STAGE_BYTES,
+                                 &full[s]);
+            }
+        }
+        for (int j = max(0, it - STAGES); j < it; ++j)
+            ptx::mbar_wait(&full[j % STAGES], (j / STAGES) & 1, abort_flag, WAIT_LIMIT);
+    } else if (warp == W_BPROD) {
+        // raw tiles of L = [E | X]: map tmB over E, tmF over X
+        int it = 0;
+        bool ok = true;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        int prefetched = -1;
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const TcParams& p = G == 1 ? g.p[0] : sp[wk.gi];
+            const CUtensorMap* tmE = &g.tmB[wk.gi];
+            const CUtensorMap* tmX = &g.tmF[wk.gi];
+            if (prefetched != wk.gi) {
+                if (lane == 0) {
+                    ptx::prefetch_tmap(tmE);
+                    ptx::prefetch_tmap(tmX);
+                }
+                prefetched = wk.gi;
+            }
+            const int y = (int)x.mt * BM;               // first row of the row tile
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int r = it % RAW;
+                const bool free_ = ptx::mbar_wait(&rawEmpty[r], ((it / RAW) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, free_)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                const uint32_t leader = ptx::elect_one();
+                ptx::mbar_arrive_expect_tx_if(leader, &rawFull[r], RAW_TILE);
+                const int64_t kp0 = (int64_t)(x.ii * p.KD + j) * KS;
+                const bool second = kp0 >= p.Kp;
+                const CUtensorMap* tm = second ? tmX : tmE;
+                const int x0 = (int)((second ? kp0 - p.Kp : kp0) * W);   // first word of the 16 K values
+#pragma unroll
+                for (int h = 0; h < W; ++h)
+                    ptx::tma_load_2d_if(leader, sRaw + r * RAW_TILE + h * Lay::RAW_BOX, tm, x0 + 16 * h, y, &rawFull[r]);
+            }
+        }
+        for (int j = max(0, it - RAW); j < it; ++j)
+            ptx::mbar_wait(&rawFull[j % RAW], (j / RAW) & 1, abort_flag, WAIT_LIMIT);
+    } else if (warp >= W_CONV0 && warp < W_CONV0 + 4) {
+        // converter thread m (0..127) forms row m of every L plane
+        const int m = threadIdx.x - W_CONV0 * 32;
+        int total = 0;
+        {
+            Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+            for (int64_t v = 0; v < nv; ++v) total += wk.next().nst;
+        }
+        const uint32_t boff = (uint32_t)(m >> 3) * CORE_SBO + (uint32_t)(m & 7) * 16;
+        for (int it = 0; it < total; ++it) {
+            const int r = it % RAW;
+            if (!__all_sync(0xffffffffu, ptx::mbar_wait(&rawFull[r], (it / RAW) & 1, abort_flag, WAIT_LIMIT))) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            const uint8_t* raw = sRaw + r * RAW_TILE;
+            u64 e[16 * W];
+#pragma unroll
+            for (int k = 0; k < 16; k += (W == 1 ? 2 : 1)) {
+                // one 16-byte chunk: two values (W = 1) or one (W = 2)
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(raw + raw_l_offset<W>(m, k));
+                e[k * W] = v.x;
+                e[k * W + 1] = v.y;
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&rawEmpty[r]);
+            const int s = it % STAGES;
+            if (!__all_sync(0xffffffffu,
+                            ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT))) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            uint8_t* dst = sA + s * A_STAGE + boff;
+#pragma unroll
+            for (int kh = 0; kh < 2; ++kh) {
+                Biased<W> b[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
+#pragma unroll
+                for (int t = 0; t < NDIG; ++t) {
+                    const int wi = t >> 2;
+                    const uint32_t byte = t & 3;
+                    uint4 o;
+                    o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
+                    o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
+                    o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
+                    o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
+                    *reinterpret_cast<uint4*>(dst + t * A_PLANE + kh * CORE_LBO) = o;
+                }
+            }
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&full[s]);
+        }
+    } else if (warp == W_MMA) {
+        const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
+        bool ok = true;
+        int it = 0;
+        Walker<G> wk(G == 1 ? &g.p[0] : sp, count, grid, (int)cta);
+        for (int64_t v = 0; v < nv && ok; ++v) {
+            const Unit x = wk.next();
+            const int set = (int)(v & 1);
+            const bool got = ptx::mbar_wait(&accEmpty[set], (int)((v >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            ptx::tc_fence_after();
+            if (lane == 0) {
+                info[v % NINFO] = make_int4((int)x.mt, (int)x.nt, x.ii, (int)x.flush | (wk.gi << 1));
+                ptx::mbar_arrive(&infoFull[v % NINFO]);
+            }
+            for (int j = 0; j < x.nst; ++j, ++it) {
+                const int s = it % STAGES;
+                const bool ready = ptx::mbar_wait(&full[s], (it / STAGES) & 1, abort_flag, WAIT_LIMIT);
+                if (!__all_sync(0xffffffffu, ready)) {
+                    if (lane == 0) record_timeout(abort_flag);
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t leader = ptx::elect_one();
+                const uint64_t bdesc = ptx::smem_desc_kmajor(bBase + s * B_STAGE_BYTES, CORE_LBO, CORE_SBO);
+#pragma unroll
+                for (int i = 0; i < NDIG; ++i) {
+                    const uint64_t adesc =
+                        ptx::smem_desc_kmajor(aBase + s * A_STAGE + i * A_PLANE, CORE_LBO, CORE_SBO);
+                    const uint32_t idesc = ptx::idesc_f16_f32(BM, (NDIG - i) * ND);
+                    ptx::mma_f16_if(leader, tmem + set * NSTACK + i * ND, adesc, bdesc, idesc,
+                                    (j == 0 && i == 0) ? 0u : 1u);
+                }
+                ptx::mma_commit_if(leader, &empty[s]);
+            }
+            if (ok) ptx::mma_commit_if(ptx::elect_one(), &accFull[set]);
+        }
+        ptx::mma_commit_if(ptx::elect_one(), mmaDone);
+        ptx::mbar_wait(mmaDone, 0, abort_flag, WAIT_LIMIT);
+    } else {
+        // drain: lane l of quadrant q holds row 32 q + l of the tile and its ND sums
+        const int quad = warp & 3;
+        constexpr int DPL = 32 / ND;
+        Sum sum[ND];
+#pragma unroll
+        for (int c = 0; c < ND; ++c) sum[c] = 0;
+        int seg_ii = -1;
+        for (int64_t v = 0; v < nv; ++v) {
+            const bool have = ptx::mbar_wait(&infoFull[v % NINFO], (int)((v / NINFO) & 1), abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, have)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            const int4 u = info[v % NINFO];
+            const int x_ii = u.z;
+            const bool x_flush = (u.w & 1) != 0;
+            const TcParams& p = G == 1 ? g.p[0] : sp[u.w >> 1];
+            const int set = (int)(v & 1);
+            const bool got = ptx::mbar_wait(&accFull[set], (int)((v >> 1) & 1), abort_flag, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) record_timeout(abort_flag);
+                break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * NSTACK;
+#pragma unroll
+            for (int t0 = 0; t0 < NDIG; t0 += DPL) {
+                uint32_t f[32];
+                ptx::tmem_ld32(base + t0 * ND, f);
+                ptx::tmem_wait_ld();
+                if (t0 + DPL >= NDIG) {
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int t = t0 + q / ND, c = q % ND;
+                    const long long d = __float2int_rn(__uint_as_float(f[q]));
+                    const Sum dv = (Sum)(W == 1 ? (Sum)(u64)d : (Sum)(__int128)d);
+                    sum[c] += dv << (8 * t);
+                }
+            }
+            if (seg_ii < 0) seg_ii = x_ii;
+            if (x_flush) {
+                const bool whole = seg_ii == 0 && x_ii == p.I - 1;
+                seg_ii = -1;
+                const int64_t m = (int64_t)u.x * BM + quad * 32 + lane;
+                const int64_t n0 = (int64_t)u.y * ND;
+                if (m < p.M) {
+                    const int64_t e0 = m * p.N + n0;
+                    if (whole && n0 + ND <= p.N) {
+                        // the row's ND sums as 16-byte vectors (N is even for W = 1)
+                        ulonglong2* z2 = reinterpret_cast<ulonglong2*>(p.Z + e0 * W);
+                        const ulonglong2* c2 = reinterpret_cast<const ulonglong2*>(p.C + e0 * W);
+                        constexpr int V = ND * W / 2;
+#pragma unroll
+                        for (int q = 0; q < V; ++q) {
+                            const ulonglong2 cq = p.C ? __ldg(c2 + q) : make_ulonglong2(0, 0);
+                            ulonglong2 o;
+                            if constexpr (W == 1) {
+                                o.x = cq.x + sum[2 * q];
+                                o.y = cq.y + sum[2 * q + 1];
+                            } else {
+                                const Sum r = ((Sum)cq.x | ((Sum)cq.y << 64)) + sum[q];
+                                o.x = (u64)r;
+                                o.y = (u64)(r >> 64);
+                            }
+                            z2[q] = o;
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < ND; ++c) {
+                            if (n0 + c >= p.N) break;
+                            const int64_t e = e0 + c;
+                            if (whole) {
+                                st_elem<W>(p.Z, e, (p.C ? ldg_elem<W>(p.C, e) : (Sum)0) + sum[c]);
+                            } else {
+                                if constexpr (W == 1) red_add_u64(p.Z + e, sum[c]);
+                                else atomic_add_u128(p.Z + 2 * e, sum[c]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < ND; ++c) sum[c] = 0;
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == W_APROD) ptx::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 
 struct Plan {
@@ -1419,6 +1902,10 @@ struct Plan {
 // rows is the ring's ND (32 for Z_2^64, 16 for Z_2^128), else row tiles of
 // 64 rows (rows == 64) or 128 (anything else).
 bool wide_rows(int rows, int words) { return rows == (words == 1 ? Cfg<1>::ND : Cfg<2>::ND); }
+// The tall tile: 128-row tiles whose left operand the GEMM converts itself.
+constexpr int TALL_ROWS = TALL_TILE_ROWS;
+static_assert(TALL_TILE_ROWS == -BM, "the tall tile has 128 rows");
+bool tall_rows(int rows) { return rows == TALL_ROWS; }
 int tile_rows(int rows) { return rows == 64 ? 64 : BM; }
 
 // Row tiles: m_tiles x n_tiles output tiles of R x ND, digit planes of L in
@@ -1426,6 +1913,20 @@ int tile_rows(int rows) { return rows == 64 ? 64 : BM; }
 // n_tiles = row tiles (of ND rows), digit planes of L in ND-row tiles.
 Plan make_plan(int64_t M, int64_t K, int64_t N, int words, int one_half = 0, int rows = BM) {
     Plan pl{};
+    if (tall_rows(rows)) {
+        // row tiles of 128 x ND; the workspace holds the digit planes of
+        // R' = [B + cF ; F] in ND-column tiles (8 KB per tile and stage)
+        pl.KD = words == 1 ? Cfg<1>::KD : Cfg<2>::KD;
+        pl.ND = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
+        pl.m_tiles = (M + BM - 1) / BM;
+        pl.n_tiles = (N + pl.ND - 1) / pl.ND;
+        pl.Kp = ((K + KS - 1) / KS) * KS;
+        pl.S_tot = (int)(2 * pl.Kp / KS);
+        pl.I = (pl.S_tot + pl.KD - 1) / pl.KD;
+        pl.U = pl.m_tiles * pl.n_tiles * pl.I;
+        pl.ap_bytes = (size_t)pl.n_tiles * pl.S_tot * B_STAGE_BYTES;
+        return pl;
+    }
     const bool wide = wide_rows(rows, words);
     pl.KD = words == 1 ? Cfg<1>::KD : Cfg<2>::KD;
     pl.ND = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
@@ -1477,6 +1978,22 @@ bool make_map(CUtensorMap* map, const u64* base, int64_t rows, int64_t cols, int
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<u64*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// 2-D map over an M x K row-major matrix of `words`-word elements for the tall
+// tile's raw L tiles: box of 128 rows x 16 words (128 bytes), 128-byte swizzle
+// (the K row stride, K words x 8 bytes, must be a multiple of 16 bytes)
+bool make_map_l(CUtensorMap* map, const u64* base, int64_t rows, int64_t cols, int words) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)(cols * words), (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(cols * words) * 8};
+    cuuint32_t box[2] = {16u, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<u64*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -1602,6 +2119,84 @@ cudaError_t launch_chunk(const GemmArgs* a, uint8_t* const* Ap, const int* order
     return e;
 }
 
+// The tall tile: entry j of a group (R' planes at Rp).
+template <int W, int G>
+bool fill_tall(TcGroup<G>& tg, PrologueRGroup<G>& pg, int j, const GemmArgs& a, uint8_t* Rp, const Plan& pl) {
+    if (!make_map_l(&tg.tmB[j], a.E, a.M, a.K, W)) return false;
+    if (!make_map_l(&tg.tmF[j], a.X, a.M, a.K, W)) return false;
+    const int gm = a.gm > 0 ? a.gm : GM_DEFAULT;
+    tg.p[j] = TcParams{Rp, a.Z, a.C, 0, a.M, a.K, a.N, pl.Kp, pl.S_tot, pl.I, pl.KD, pl.ND,
+                       pl.m_tiles, pl.n_tiles, pl.U, gm, 0};
+    pg.p[j] = PrologueRParams{a.B, a.F, a.alpha, a.coef, a.M, a.K, a.N, pl.Kp, pl.S_tot, Rp, a.C, a.Z,
+                              pl.I, pl.m_tiles, pl.n_tiles, gm};
+    pg.b_off[j + 1] = pg.b_off[j] + (pl.n_tiles * pl.S_tot * 2 * pl.ND + 255) / 256;
+    return true;
+}
+
+template <int W, int G>
+cudaError_t ensure_smem_attr_tall() {
+    static bool smem_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+    if (dev >= 0 && dev < 64 && smem_set[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(ring_gemm_tc_tall_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TallLayout<W, G>::SMEM);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) smem_set[dev] = true;
+    return cudaSuccess;
+}
+
+template <int W, int G>
+cudaError_t launch_group_tall(TcGroup<G>& tg, PrologueRGroup<G>& pg, cudaStream_t st) {
+    int64_t total = 0;
+    for (int j = 0; j < tg.count; ++j) total += tg.p[j].U;
+    const int sms = sm_count();
+    const int grid = (int)(total < sms ? (total > 0 ? total : 1) : sms);
+    int64_t acc = 0;
+    for (int j = 0; j < tg.count; ++j) {
+        tg.p[j].rot = acc % grid;
+        acc += tg.p[j].U;
+    }
+    tg.grid = pg.grid = grid;
+    cudaError_t e = launch_dependent(prologue_r_kernel<W, G>, dim3((unsigned)pg.b_off[pg.count]), dim3(256), 0, st, pg);
+    if (e != cudaSuccess) return e;
+    e = ensure_smem_attr_tall<W, G>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = TallLayout<W, G>::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, ring_gemm_tc_tall_kernel<W, G>, tg);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <int W, int G>
+cudaError_t launch_chunk_tall(const GemmArgs* a, uint8_t* const* Ap, const int* order, int cnt, cudaStream_t st) {
+    auto* tg = new (std::nothrow) TcGroup<G>;
+    auto* pg = new (std::nothrow) PrologueRGroup<G>;
+    cudaError_t e = (tg && pg) ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) {
+        tg->count = pg->count = cnt;
+        pg->b_off[0] = 0;
+        for (int j = 0; j < cnt && e == cudaSuccess; ++j) {
+            const GemmArgs& x = a[order[j]];
+            if (!fill_tall<W, G>(*tg, *pg, j, x, Ap[order[j]], make_plan(x.M, x.K, x.N, W, 0, TALL_ROWS)))
+                e = cudaErrorInvalidValue;
+        }
+        if (e == cudaSuccess) e = launch_group_tall<W, G>(*tg, *pg, st);
+    }
+    delete tg;
+    delete pg;
+    return e;
+}
+
 constexpr int GSMALL = 16;   // small groups use a kernel with a smaller parameter block
 
 // dynamic shared memory plus the grouped kernels' static layer table stay
@@ -1616,6 +2211,9 @@ static_assert(fits_smem<1, 1>() && fits_smem<2, 1>() && fits_smem<1, GSMALL>() &
                   fits_smem<1, GSMALL, BM, true>() && fits_smem<2, GSMALL, BM, true>() &&
                   fits_smem<1, GMAX, BM, true>() && fits_smem<2, GMAX, BM, true>(),
               "shared memory of a TC GEMM instantiation");
+static_assert(TallLayout<1, GMAX>::SMEM + GMAX * sizeof(TcParams) <= 227 * 1024 &&
+                  TallLayout<2, GMAX>::SMEM + GMAX * sizeof(TcParams) <= 227 * 1024,
+              "shared memory of the tall GEMM");
 
 // A layer with units for at least LONG_WAVES waves of the grid gains little
 // from sharing a launch (its last, partial wave is under 2 % of it), and the
@@ -1630,9 +2228,9 @@ bool long_layer(int64_t M, int64_t K, int64_t N, int words, int one_half, int sm
 // The layers idx[0 .. n) (all with R-row tiles) in launches of up to GMAX
 // layers; layer i's digit planes at Ap[i].  Every layer is eligible and has
 // the ring width W.
-template <int W, int R, bool WIDE = false>
+template <int W, int R, bool WIDE = false, bool TALL = false>
 cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t* const* Ap, cudaStream_t st) {
-    constexpr int rows = WIDE ? Cfg<W>::ND : R;
+    constexpr int rows = TALL ? TALL_ROWS : WIDE ? Cfg<W>::ND : R;
     // layers with more K intervals first, so that whole tiles of the long
     // layers line up with the CTAs' ranges (the order changes no result)
     std::vector<std::pair<int, int>> by_iv;   // (intervals per tile, layer)
@@ -1645,7 +2243,8 @@ cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t*
     std::vector<int> rest;
     for (int i : order) {
         if (long_layer(a[i].M, a[i].K, a[i].N, W, a[i].one_half, sms, rows)) {
-            if (e == cudaSuccess) e = launch_chunk<W, 1, R, WIDE>(a, Ap, &i, 1, st);
+            if (e == cudaSuccess)
+                e = TALL ? launch_chunk_tall<W, 1>(a, Ap, &i, 1, st) : launch_chunk<W, 1, R, WIDE>(a, Ap, &i, 1, st);
         } else {
             rest.push_back(i);
         }
@@ -1654,9 +2253,14 @@ cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t*
     for (int i0 = 0; i0 < n && e == cudaSuccess; i0 += GMAX) {
         const int cnt = n - i0 < GMAX ? n - i0 : GMAX;
         // a lone layer takes the one-layer kernel (parameters at constant offsets)
-        e = cnt == 1        ? launch_chunk<W, 1, R, WIDE>(a, Ap, rest.data() + i0, cnt, st)
-            : cnt <= GSMALL ? launch_chunk<W, GSMALL, R, WIDE>(a, Ap, rest.data() + i0, cnt, st)
-                            : launch_chunk<W, GMAX, R, WIDE>(a, Ap, rest.data() + i0, cnt, st);
+        if constexpr (TALL)
+            e = cnt == 1        ? launch_chunk_tall<W, 1>(a, Ap, rest.data() + i0, cnt, st)
+                : cnt <= GSMALL ? launch_chunk_tall<W, GSMALL>(a, Ap, rest.data() + i0, cnt, st)
+                                : launch_chunk_tall<W, GMAX>(a, Ap, rest.data() + i0, cnt, st);
+        else
+            e = cnt == 1        ? launch_chunk<W, 1, R, WIDE>(a, Ap, rest.data() + i0, cnt, st)
+                : cnt <= GSMALL ? launch_chunk<W, GSMALL, R, WIDE>(a, Ap, rest.data() + i0, cnt, st)
+                                : launch_chunk<W, GMAX, R, WIDE>(a, Ap, rest.data() + i0, cnt, st);
     }
     return e;
 }
@@ -1666,13 +2270,18 @@ cudaError_t launch_many_rows(const GemmArgs* a, std::vector<int> order, uint8_t*
 // tile).
 template <int W>
 cudaError_t launch_many(const GemmArgs* a, int n, uint8_t* const* Ap, cudaStream_t st) {
-    std::vector<int> big, small, wide;
+    std::vector<int> big, small, wide, tall;
     for (int i = 0; i < n; ++i)
-        (wide_rows(a[i].rows, W) ? wide : tile_rows(a[i].rows) == 64 ? small : big).push_back(i);
+        (tall_rows(a[i].rows) && !a[i].one_half ? tall
+         : wide_rows(a[i].rows, W)               ? wide
+         : tile_rows(a[i].rows) == 64            ? small
+                                                 : big)
+            .push_back(i);
     cudaError_t e = cudaSuccess;
     if (!big.empty()) e = launch_many_rows<W, BM>(a, big, Ap, st);
     if (e == cudaSuccess && !small.empty()) e = launch_many_rows<W, 64>(a, small, Ap, st);
     if (e == cudaSuccess && !wide.empty()) e = launch_many_rows<W, BM, true>(a, wide, Ap, st);
+    if (e == cudaSuccess && !tall.empty()) e = launch_many_rows<W, BM, false, true>(a, tall, Ap, st);
     return e;
 }
 
@@ -1683,6 +2292,8 @@ bool gemm_tc_feasible(int64_t M, int64_t K, int64_t N, int words, int rows) {
     if (M <= 8 || N < 1 || K < 1) return false;        // skinny layers stream better on the SIMT GEMV
     if (words == 1 && N % 2 != 0) return false;       // TMA row stride: 16-byte multiple
     if (K > (int64_t(1) << 30) || N > (int64_t(1) << 28)) return false;
+    // the tall tile loads rows of L by 2-D TMA: their stride (K words) must be a multiple of 16 bytes
+    if (tall_rows(rows) && (K * words) % 2 != 0) return false;
     const int R = wide_rows(rows, words) ? (words == 1 ? Cfg<1>::ND : Cfg<2>::ND) : tile_rows(rows);
     if ((M + R - 1) / R > 65535) return false;
     return true;
@@ -1700,12 +2311,20 @@ size_t gemm_tc_workspace(int64_t M, int64_t K, int64_t N, int words, int one_hal
     if (!gemm_tc_feasible(M, K, N, words)) return 0;
     const int wide = words == 1 ? Cfg<1>::ND : Cfg<2>::ND;
     size_t b = make_plan(M, K, N, words, one_half, BM).ap_bytes;
-    for (int rows : {64, wide})
+    for (int rows : {64, wide, TALL_ROWS})
         if (gemm_tc_feasible(M, K, N, words, rows)) b = std::max(b, make_plan(M, K, N, words, one_half, rows).ap_bytes);
     return align256(b);
 }
 
 cudaError_t launch_gemm_tc(const GemmArgs& a, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (tall_rows(a.rows) && !a.one_half && gemm_tc_feasible(a.M, a.K, a.N, a.words, TALL_ROWS)) {
+        Plan pl = make_plan(a.M, a.K, a.N, a.words, 0, TALL_ROWS);
+        if (ws_bytes < align256(pl.ap_bytes) || ws == nullptr) return cudaErrorInvalidValue;
+        uint8_t* Rp = static_cast<uint8_t*>(ws);
+        const int order = 0;
+        return a.words == 1 ? launch_chunk_tall<1, 1>(&a, &Rp, &order, 1, st)
+                            : launch_chunk_tall<2, 1>(&a, &Rp, &order, 1, st);
+    }
     const bool wide = wide_rows(a.rows, a.words);
     const int rows = wide ? a.rows : tile_rows(a.rows);
     if (!gemm_tc_feasible(a.M, a.K, a.N, a.words, rows)) return cudaErrorNotSupported;
@@ -1733,15 +2352,15 @@ cudaError_t launch_gemm_tc_grouped(const GemmArgs* a, int n, uint8_t* const* Ap,
 
 int gemm_tc_grouped_launches(const int64_t* M, const int64_t* K, const int64_t* N, int n, int words) {
     const int sms = sm_count();
-    int alone = 0, rest[3] = {0, 0, 0};
+    int alone = 0, rest[4] = {0, 0, 0, 0};
     for (int i = 0; i < n; ++i) {
         const int rows = gemm_choice(M[i], K[i], N[i], words).rows;
-        const int kind = wide_rows(rows, words) ? 2 : tile_rows(rows) == 64 ? 1 : 0;
-        if (long_layer(M[i], K[i], N[i], words, 0, sms, kind == 2 ? rows : tile_rows(rows))) ++alone;
+        const int kind = tall_rows(rows) ? 3 : wide_rows(rows, words) ? 2 : tile_rows(rows) == 64 ? 1 : 0;
+        if (long_layer(M[i], K[i], N[i], words, 0, sms, kind >= 2 ? rows : tile_rows(rows))) ++alone;
         else ++rest[kind];
     }
     int pairs = alone;
-    for (int k = 0; k < 3; ++k) pairs += (rest[k] + GMAX - 1) / GMAX;
+    for (int k = 0; k < 4; ++k) pairs += (rest[k] + GMAX - 1) / GMAX;
     return 2 * pairs;
 }
 

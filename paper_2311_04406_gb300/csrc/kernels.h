@@ -30,8 +30,9 @@ struct GemmArgs {
     int one_half;      // 1: Z = C + (X + cE) . F over K only (the public product E.F)
     int gm;            // tensor cores: row tiles per swizzle group (0: default)
     int simt_waves;    // integer pipes: K-split target in waves of 152 blocks (0: default)
-    int rows;          // tensor cores: tile rows, 128 or 64 (0: 128), or the wide tile
-                       // (32 for W = 1, 16 for W = 2); integer pipes: 64 or 16 (0: by grid size)
+    int rows;          // tensor cores: tile rows, 128 or 64 (0: 128), the wide tile (32 for
+                       // W = 1, 16 for W = 2) or the tall tile (-128); integer pipes: 64 or
+                       // 16 (0: by grid size)
 };
 
 // The launch choice of one GEMM shape: path 1 = tensor cores (rows = tile
@@ -47,6 +48,9 @@ struct Choice {
 };
 Choice gemm_choice(int64_t M, int64_t K, int64_t N, int words);
 int wide_tile_rows(int words);   // the launch-table value of the wide tensor-core tile
+// the launch-table value of the tall tensor-core tile (128-row tiles whose
+// left operand the GEMM converts itself)
+constexpr int TALL_TILE_ROWS = -128;
 
 cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t st);
 

@@ -40,7 +40,7 @@ std::map<Key, Choice>& table() {
 
 bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
     if (c.path == 1)
-        return (c.rows == 64 || c.rows == 128 || c.rows == wide_tile_rows(words)) &&
+        return (c.rows == 64 || c.rows == 128 || c.rows == wide_tile_rows(words) || c.rows == TALL_TILE_ROWS) &&
                gemm_tc_feasible(M, K, N, words, c.rows) && c.gm >= 1 && c.gm <= 64;
     return c.path == 0 && c.waves >= 0 && c.waves <= 64 && (c.rows == 0 || c.rows == 16 || c.rows == 64);
 }
@@ -49,9 +49,16 @@ bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
 // in the stacked operand) for layers of at most two of its row tiles, 64-row
 // tiles up to 64 rows, 128-row tiles above (an M = 64 MMA costs as much as an
 // M = 128 one).
-int default_rows(int64_t M, int words) {
+int default_rows(int64_t M, int64_t K, int64_t N, int words) {
     if (M <= 2 * wide_tile_rows(words)) return wide_tile_rows(words);
-    return M <= 64 ? 64 : 128;
+    if (M <= 64) return 64;
+    // tall and narrow Z_2^64 layers: the left operand's digit planes would cost
+    // an HBM round trip comparable to the GEMM itself, so the GEMM converts them
+    // in place (measured: 32768 x 576 x 64 share 285 -> 207 us; equal at
+    // N = 128; in Z_2^128 the raw tiles' extra shared-memory traffic cancels
+    // the saving: 829 -> 842 us)
+    if (words == 1 && N <= 64 && gemm_tc_feasible(M, K, N, words, TALL_TILE_ROWS)) return TALL_TILE_ROWS;
+    return 128;
 }
 
 }  // namespace
@@ -67,7 +74,7 @@ Choice gemm_choice(int64_t M, int64_t K, int64_t N, int words) {
     c.gm = 0;
     c.waves = 0;
     c.tuned = 0;
-    c.rows = c.path == 1 ? default_rows(M, words) : 0;
+    c.rows = c.path == 1 ? default_rows(M, K, N, words) : 0;
     return c;
 }
 
@@ -140,8 +147,9 @@ int mpc_autotune(const mpc_layer* layers, int count, void* stream) {
         // tiles: 64 rows only where the layer has at most 64 rows (it would
         // double the MMA work of taller layers), the wide tile up to 128 rows
         if (tc)
-            for (int rows : {128, 64, mpcl::wide_tile_rows(w)}) {
+            for (int rows : {128, 64, mpcl::wide_tile_rows(w), mpcl::TALL_TILE_ROWS}) {
                 if (rows == 64 && M > 64) continue;
+                if (rows == mpcl::TALL_TILE_ROWS && M < 128) continue;
                 if (rows == mpcl::wide_tile_rows(w) && M > 128) continue;
                 if (!mpcl::gemm_tc_feasible(M, K, N, w, rows)) continue;
                 for (int gm : {1, 4, 8, 16}) cands.push_back(mpcl::Choice{1, gm, 0, 1, rows});

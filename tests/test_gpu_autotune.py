@@ -32,7 +32,9 @@ def operands(ring, M, K, N, seed):
 
 
 CHOICES = [(1, 1, 0), (1, 4, 0), (1, 16, 0), (1, 64, 0), (0, 0, 1), (0, 0, 2), (0, 0, 8)]
-TILE_ROWS = (128, 64, "wide")  # tensor cores ("wide": 128 columns x 32 rows, Z_2^64, or 16, Z_2^128)
+# tensor cores ("wide": 128 columns x 32 rows, Z_2^64, or 16, Z_2^128; -128: the tall tile, whose
+# left operand the GEMM converts itself)
+TILE_ROWS = (128, 64, "wide", -128)
 SIMT_ROWS = (0, 64, 16)        # integer pipes (0: chosen by grid size)
 
 
@@ -48,6 +50,8 @@ def test_every_choice_is_exact(ring, shape):
     for path, gm, waves in CHOICES:
         for rows in (TILE_ROWS if path else SIMT_ROWS):
             rows = rows_of(rows, ring)
+            if rows == -128 and (K * ring.words) % 2:
+                continue                    # the tall tile's 2-D loads need an even row stride
             abi.mpc_autotune_set(L, path, gm if path else 0, waves, tile_rows=rows)
             assert abi.mpc_gemm_path(L) == path
             assert abi.mpc_autotune_choice(L)[4] == rows
@@ -61,7 +65,7 @@ def test_every_choice_is_exact(ring, shape):
 # ragged heights around both tile heights (M <= 8 runs on the integer pipes
 # only), ragged K (one partial 16-deep stage; a K below one stage) and N
 @pytest.mark.parametrize("ring", [synth.Z64, synth.Z128], ids=["w1", "w2"])
-@pytest.mark.parametrize("M", [9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 130])
+@pytest.mark.parametrize("M", [9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 130, 300])
 def test_every_tile_is_exact(ring, M):
     for K, N in ((27, 34), (300, 96), (5, 66), (40, 258)):
         E, F, A, B, C = operands(ring, M, K, N, 1000 * M + K)
@@ -72,6 +76,10 @@ def test_every_tile_is_exact(ring, M):
         L = abi.make_layer(M, K, N, ring.k, ring.s, 0, 2)
         for rows in TILE_ROWS:
             rows = rows_of(rows, ring)
+            if rows == -128 and (K * ring.words) % 2:
+                with pytest.raises(abi.MpcError):
+                    abi.mpc_autotune_set(L, 1, 8, 0, tile_rows=rows)
+                continue
             for gm in (1, 8):
                 abi.mpc_autotune_set(L, 1, gm, 0, tile_rows=rows)
                 Z = empty_like_ring((M, N), ring.words)
@@ -90,6 +98,10 @@ def test_built_in_rule_takes_short_tiles_for_short_layers():
     assert abi.mpc_autotune_choice(abi.make_layer(65, 4608, 512))[::4] == (1, 128)
     assert abi.mpc_autotune_choice(abi.make_layer(16, 2304, 512, 64, 64))[::4] == (1, 16)
     assert abi.mpc_autotune_choice(abi.make_layer(40, 2304, 512, 64, 64))[::4] == (1, 64)
+    assert abi.mpc_autotune_choice(abi.make_layer(32768, 576, 64))[::4] == (1, -128)           # tall
+    assert abi.mpc_autotune_choice(abi.make_layer(32768, 576, 64, 64, 64))[::4] == (1, 128)
+    assert abi.mpc_autotune_choice(abi.make_layer(1024, 27, 64))[::4] == (0, 0)                 # small: SIMT
+    assert abi.mpc_autotune_choice(abi.make_layer(1024, 575, 64))[::4] == (1, 128)   # odd K: not tall
 
 
 @pytest.mark.parametrize("ring", [synth.Z64, synth.Z128], ids=["w1", "w2"])
@@ -98,9 +110,11 @@ def test_grouped_with_mixed_choices(ring):
     integer pipes (the tensor-core layers of each tile height share a
     persistent launch)."""
     shapes = [(300, 200, 96), (1100, 64, 66), (64, 256, 256), (520, 128, 130), (40, 300, 96), (17, 1000, 34),
-              (64, 27, 64), (130, 600, 66), (12, 700, 300), (100, 64, 130), (33, 1500, 258)]
+              (64, 27, 64), (130, 600, 66), (12, 700, 300), (100, 64, 130), (33, 1500, 258), (1300, 576, 64),
+              (257, 40, 34), (200, 130, 300)]
     choices = [(1, 1, 0, 128), (0, 0, 4, 16), (1, 16, 0, 64), (1, 4, 0, 128), (1, 8, 0, 64), (1, 1, 0, 64),
-               (1, 8, 0, 128), (0, 0, 2, 64), (1, 8, 0, "wide"), (1, 1, 0, "wide"), (1, 4, 0, "wide")]
+               (1, 8, 0, 128), (0, 0, 2, 64), (1, 8, 0, "wide"), (1, 1, 0, "wide"), (1, 4, 0, "wide"),
+               (1, 8, 0, -128), (1, 1, 0, -128), (1, 4, 0, -128)]
     choices = [(p_, g_, w_, rows_of(r_, ring)) for p_, g_, w_, r_ in choices]
     layers = [abi.make_layer(M, K, N, ring.k, ring.s) for M, K, N in shapes]
     for L, (path, gm, waves, rows) in zip(layers, choices):
@@ -124,7 +138,7 @@ def test_autotune_fills_the_table(tmp_path):
         path, gm, waves, tuned, rows = abi.mpc_autotune_choice(L)
         assert tuned
         assert path in (0, 1)
-        assert rows in ((0, 16, 64) if path == 0 else (128, 64, 32))
+        assert rows in ((0, 16, 64) if path == 0 else (128, 64, 32, -128))
     assert abi.mpc_autotune_choice(layers[2])[0] == 0      # M <= 8: integer pipes only
     f = tmp_path / "t.txt"
     assert abi.mpc_autotune_save(str(f)) == 4
