@@ -868,6 +868,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         extras["grouped_uneven"] = extra_grouped_uneven(torch, abi, args.warmup)
+        extras["vgg16_grouped"] = extra_vgg16(torch, abi, args.warmup)
         extras["serving"] = extra_serving(torch, abi)
 
     cpu = None
@@ -984,6 +985,39 @@ def extra_grouped_uneven(torch, abi, warmup):
     torch.cuda.empty_cache()
     abi.mpc_autotune_clear()
     return rec
+
+
+def extra_vgg16(torch, abi, warmup, batches=(1, 16)):
+    """VGG16 on 32x32x3 (13 convs as im2col GEMMs + 3 dense layers), Z_2^64, two
+    parties, grouped calls with the launch table filled for the shapes; one
+    captured step replayed per batch size."""
+    out = {}
+    for b in batches:
+        layers = synth.vgg16_layers(b)
+        abi.mpc_autotune([abi.make_layer(L.M, L.K, L.N, RING.k, RING.s) for L in layers])
+        run = GpuWorkload(layers, torch, abi, device_gen=True)
+        run.setup_grouped()
+        for _ in range(warmup):
+            run.step_grouped()
+        g = capture(torch, run.step_grouped)
+        for _ in range(warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        with Clocks(torch.cuda.current_device()) as ck:
+            ms = timed_steps(torch, g.replay, 4 * EXTRA_STEPS)
+        check_device(abi, f"the VGG16 b{b} steps")
+        fu = time_calls(torch, lambda: run.full_group(1), 50, True, budget_s=0.3)
+        co = time_calls(torch, lambda: run.compact_group(1), 50, True, budget_s=0.3)
+        out[f"b{b}"] = {"ms_per_step": ms, "ring_gmacs": step_units(layers) / (ms / 1e3) / 1e9,
+                        "tag_overhead_ratio": pct(co, 50) / pct(fu, 50), "clocks": ck.summary()}
+        del g, run
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    abi.mpc_autotune_clear()
+    out.update(workload="vgg16_32x32x3", ring=f"Z_2^{RING.bits}", parties=PARTIES,
+               step_launch="CUDA graph replay of one captured step (grouped calls, launch table filled)",
+               inputs="device-generated uniform words, resident")
+    return out
 
 
 def extra_serving(torch, abi, n_requests=200, load=0.7):
@@ -1213,7 +1247,7 @@ def main():
     ap.add_argument("--eager", action="store_true", help="time eager API calls instead of graph replay")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="default workload only: skip the grouped uneven-layer and serving records")
+                    help="default workload only: skip the grouped uneven-layer, VGG16 and serving records")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cnn",
                     help="layer set (default: the CNN pair, conv 1024x576x64 + dense 128x4096x4096)")

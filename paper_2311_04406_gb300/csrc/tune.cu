@@ -57,7 +57,9 @@ int default_rows(int64_t M, int64_t K, int64_t N, int words) {
     // in place (measured: 32768 x 576 x 64 share 285 -> 207 us; equal at
     // N = 128; in Z_2^128 the raw tiles' extra shared-memory traffic cancels
     // the saving: 829 -> 842 us)
-    if (words == 1 && N <= 64 && gemm_tc_feasible(M, K, N, words, TALL_TILE_ROWS)) return TALL_TILE_ROWS;
+    // (at M = 1024 it is 2 us slower per call: its small R' prologue runs on few blocks)
+    if (words == 1 && N <= 64 && M >= 2048 && gemm_tc_feasible(M, K, N, words, TALL_TILE_ROWS))
+        return TALL_TILE_ROWS;
     return 128;
 }
 

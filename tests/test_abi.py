@@ -108,9 +108,10 @@ def test_grouped_host_logic(lib):
     cws = abi.mpc_workspace_size_grouped(layers, abi.MPC_WS_TAG_COMPACT)
     assert cws == sum(-(-abi.mpc_workspace_size(L, abi.MPC_WS_TAG_COMPACT) // 256) * 256 for L in layers)
     # one prologue + GEMM pair per tile: the 128-row tile (128 x 4096 x 4096), the tall tile
-    # (1024 x 576 x 64: tall and narrow), the wide tile (M = 64: two of its 32-row tiles); one
-    # kernel for the integer-pipe layer
-    assert [abi.mpc_autotune_choice(L)[4] for L in layers] == [128, 0, -128, 32]
+    # (set for 1024 x 576 x 64: tall and narrow; the built-in rule takes it from 2048 rows), the
+    # wide tile (M = 64: two of its 32-row tiles); one kernel for the integer-pipe layer
+    assert [abi.mpc_autotune_choice(L)[4] for L in layers] == [128, 0, 128, 32]
+    abi.mpc_autotune_set(layers[2], 1, 8, 0, tile_rows=-128)
     assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_SHARE) == 2 + 2 + 2 + 1
     # 30 layers of each tile: one launch pair per tile (at most 64 layers each)
     assert abi.mpc_launch_count_grouped(layers * 30, abi.MPC_WS_TAG_FULL) == 3 * 2 + 30
@@ -119,6 +120,7 @@ def test_grouped_host_logic(lib):
     # launch pair of its own
     long_ = abi.make_layer(2048, 4096, 4096)
     assert abi.mpc_launch_count_grouped([long_] + layers, abi.MPC_WS_SHARE) == 2 + 2 + 2 + 2 + 1
+    abi.mpc_autotune_clear()
     # the CompactTag tags of a group: rows, finalize and vec passes, one launch each per 64 layers
     assert abi.mpc_launch_count_grouped(layers, abi.MPC_WS_TAG_COMPACT) == 3
     assert abi.mpc_launch_count_grouped(layers * 20, abi.MPC_WS_TAG_COMPACT) == 6
