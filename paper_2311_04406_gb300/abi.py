@@ -180,6 +180,41 @@ def _ptr(t):
     return t.data_ptr() if t.numel() > 0 else None
 
 
+def _sized(fn, name, t, elems, words):
+    """Address of a tensor argument that the call reads or writes as `elems`
+    elements of `words` 64-bit words, after checking that the tensor is
+    contiguous and holds at least that many bytes: a shorter tensor raises
+    ValueError before anything is launched, instead of letting a kernel run
+    past its end.  None and raw integer addresses pass through unchecked; the
+    caller answers for those, as in C."""
+    if t is None or isinstance(t, int):
+        return t
+    need = int(elems) * words * 8
+    if t.nbytes < need or not t.is_contiguous():
+        raise ValueError(f"{fn}: {name} must be a contiguous buffer of at least {need} bytes "
+                         f"({int(elems)} elements of {words} word(s)); got {tuple(t.shape)} {t.dtype}"
+                         + ("" if t.is_contiguous() else ", not contiguous"))
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _share_elems(M, K, N):
+    return dict(E=M * K, F=K * N, A_i=M * K, B_i=K * N, C_i=M * N, Z_i=M * N)
+
+
+def _tag_elems(M, K, N, mode):
+    e = dict(alpha_i=1, E=M * K, F=K * N, mA_i=M * K, mB_i=K * N, mC_i=M * N, mZ_i=M * N)
+    if mode != MPC_TAG_FULL:
+        e.update(mR_i=M * N, Dtilde=M * N, chi=N, mDc_i=M, Dc=M)
+    return e
+
+
+def _args(fn, layer, elems, given):
+    """Sized addresses of `given` (name -> tensor), in the order of `given`;
+    names without an element count (ignored by the call) pass through."""
+    w = layer.ring.words
+    return [_sized(fn, n, t, elems[n], w) if n in elems else _ptr(t) for n, t in given.items()]
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -248,30 +283,36 @@ def _alloc_ws(need, stream):
 
 
 def mpc_linear_share(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None):
+    a = _args("mpc_linear_share", layer, _share_elems(layer.M, layer.K, layer.N),
+              dict(E=E, F=F, A_i=A_i, B_i=B_i, C_i=C_i, Z_i=Z_i))
     wp, wb = _ws(layer, MPC_WS_SHARE, ws, stream)
-    _check("mpc_linear_share", load().mpc_linear_share(
-        ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(A_i), _ptr(B_i), _ptr(C_i), _ptr(Z_i),
-        wp, wb, _stream(stream)))
+    _check("mpc_linear_share", load().mpc_linear_share(ctypes.byref(layer), *a, wp, wb, _stream(stream)))
     return Z_i
 
 
 def mpc_linear_tag(layer, mode, alpha_i, E, F, mA_i, mB_i, mC_i, mZ_i, mR_i=None, Dtilde=None,
                    chi=None, mDc_i=None, Dc=None, ws=None, stream=None):
     which = MPC_WS_TAG_FULL if mode == MPC_TAG_FULL else MPC_WS_TAG_COMPACT
+    a = _args("mpc_linear_tag", layer, _tag_elems(layer.M, layer.K, layer.N, mode),
+              dict(alpha_i=alpha_i, E=E, F=F, mA_i=mA_i, mB_i=mB_i, mC_i=mC_i, mR_i=mR_i, Dtilde=Dtilde,
+                   chi=chi, mZ_i=mZ_i, mDc_i=mDc_i, Dc=Dc))
     wp, wb = _ws(layer, which, ws, stream)
-    _check("mpc_linear_tag", load().mpc_linear_tag(
-        ctypes.byref(layer), int(mode), _ptr(alpha_i), _ptr(E), _ptr(F), _ptr(mA_i), _ptr(mB_i),
-        _ptr(mC_i), _ptr(mR_i), _ptr(Dtilde), _ptr(chi), _ptr(mZ_i), _ptr(mDc_i), _ptr(Dc),
-        wp, wb, _stream(stream)))
+    _check("mpc_linear_tag", load().mpc_linear_tag(ctypes.byref(layer), int(mode), *a, wp, wb,
+                                                   _stream(stream)))
     return mZ_i
 
 
 def mpc_tag_check(layer, mode, alpha_i, chi_hat, opened, tag_i, cs_i, ws=None, stream=None):
     which = MPC_WS_CHECK_COMPACT if mode == MPC_CHECK_COMPACT else MPC_WS_CHECK_BATCHREC
+    fn, w = "mpc_tag_check", layer.ring.words
+    n = layer.M if mode == MPC_CHECK_COMPACT else layer.M * layer.N
+    # the seeded BATCHREC check reads one 64-bit seed word, not ring elements
+    ch = _sized(fn, "chi_hat", chi_hat, 1, 1) if mode == MPC_CHECK_BATCHREC_SEEDED \
+        else _sized(fn, "chi_hat", chi_hat, n, w)
+    a = [_sized(fn, "alpha_i", alpha_i, 1, w), ch, _sized(fn, "opened", opened, n, w),
+         _sized(fn, "tag_i", tag_i, n, w), _sized(fn, "cs_i", cs_i, 1, w)]
     wp, wb = _ws(layer, which, ws, stream)
-    _check("mpc_tag_check", load().mpc_tag_check(
-        ctypes.byref(layer), int(mode), _ptr(alpha_i), _ptr(chi_hat), _ptr(opened), _ptr(tag_i),
-        _ptr(cs_i), wp, wb, _stream(stream)))
+    _check(fn, load().mpc_tag_check(ctypes.byref(layer), int(mode), *a, wp, wb, _stream(stream)))
     return cs_i
 
 
@@ -279,43 +320,50 @@ def mpc_linear_tag_compact_noalloc(layer, alpha_i, E, F, mA_i, mB_i, mC_i, mR_i,
                                    mZ_i, mDc_i, Dc, stream=None):
     """CompactTag tag without a workspace: scratch comes from the library's
     static device buffer (see include/mpclinear.h for the rules of use)."""
-    _check("mpc_linear_tag_compact_noalloc", load().mpc_linear_tag_compact_noalloc(
-        ctypes.byref(layer), _ptr(alpha_i), _ptr(E), _ptr(F), _ptr(mA_i), _ptr(mB_i), _ptr(mC_i),
-        _ptr(mR_i), _ptr(Dtilde), _ptr(chi), _ptr(mZ_i), _ptr(mDc_i), _ptr(Dc), _stream(stream)))
+    fn = "mpc_linear_tag_compact_noalloc"
+    a = _args(fn, layer, _tag_elems(layer.M, layer.K, layer.N, MPC_TAG_COMPACT),
+              dict(alpha_i=alpha_i, E=E, F=F, mA_i=mA_i, mB_i=mB_i, mC_i=mC_i, mR_i=mR_i, Dtilde=Dtilde,
+                   chi=chi, mZ_i=mZ_i, mDc_i=mDc_i, Dc=Dc))
+    _check(fn, load().mpc_linear_tag_compact_noalloc(ctypes.byref(layer), *a, _stream(stream)))
     return mZ_i
 
 
 def mpc_linear_share_trunc(layer, E, F, A_i, B_i, C_i, Z_i, ws=None, stream=None):
     """Truncated layer, step 2: Z_i = C_i + E.B_i + A_i.F for every party."""
+    a = _args("mpc_linear_share_trunc", layer, _share_elems(layer.M, layer.K, layer.N),
+              dict(E=E, F=F, A_i=A_i, B_i=B_i, C_i=C_i, Z_i=Z_i))
     wp, wb = _ws(layer, MPC_WS_SHARE_TRUNC, ws, stream)
-    _check("mpc_linear_share_trunc", load().mpc_linear_share_trunc(
-        ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(A_i), _ptr(B_i), _ptr(C_i), _ptr(Z_i),
-        wp, wb, _stream(stream)))
+    _check("mpc_linear_share_trunc", load().mpc_linear_share_trunc(ctypes.byref(layer), *a, wp, wb,
+                                                                   _stream(stream)))
     return Z_i
 
 
 def mpc_public_product(layer, E, F, P, ws=None, stream=None):
     """P = E.F (public)."""
+    M, K, N = layer.M, layer.K, layer.N
+    a = _args("mpc_public_product", layer, dict(E=M * K, F=K * N, P=M * N), dict(E=E, F=F, P=P))
     wp, wb = _ws(layer, MPC_WS_PUBLIC_PRODUCT, ws, stream)
-    _check("mpc_public_product", load().mpc_public_product(
-        ctypes.byref(layer), _ptr(E), _ptr(F), _ptr(P), wp, wb, _stream(stream)))
+    _check("mpc_public_product", load().mpc_public_product(ctypes.byref(layer), *a, wp, wb, _stream(stream)))
     return P
 
 
 def mpc_optmac_trunc(layer, f, alpha_i, Rf_i, mRf_i, Dtilde, P, Zf_i, mZf_i, stream=None):
     """Truncated layer, steps 3-4 (OptMAC&Trunc plus the public product term)."""
-    _check("mpc_optmac_trunc", load().mpc_optmac_trunc(
-        ctypes.byref(layer), int(f), _ptr(alpha_i), _ptr(Rf_i), _ptr(mRf_i), _ptr(Dtilde), _ptr(P),
-        _ptr(Zf_i), _ptr(mZf_i), _stream(stream)))
+    MN = layer.M * layer.N
+    a = _args("mpc_optmac_trunc", layer, dict(alpha_i=1, Rf_i=MN, mRf_i=MN, Dtilde=MN, P=MN, Zf_i=MN, mZf_i=MN),
+              dict(alpha_i=alpha_i, Rf_i=Rf_i, mRf_i=mRf_i, Dtilde=Dtilde, P=P, Zf_i=Zf_i, mZf_i=mZf_i))
+    _check("mpc_optmac_trunc", load().mpc_optmac_trunc(ctypes.byref(layer), int(f), *a, _stream(stream)))
     return Zf_i, mZf_i
 
 
 def mpc_batchrec_mask(k, s, rows, cols, X_i, A_i, R_i, mX_i, mA_i, mR_i, W_i, mW_i, stream=None):
     """Pi_BatchRec open phase step 1: W_i = X_i - A_i + R_i and the same for the tags."""
     ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
-    _check("mpc_batchrec_mask", load().mpc_batchrec_mask(
-        ctypes.byref(ring), int(rows), int(cols), _ptr(X_i), _ptr(A_i), _ptr(R_i), _ptr(mX_i),
-        _ptr(mA_i), _ptr(mR_i), _ptr(W_i), _ptr(mW_i), _stream(stream)))
+    fn, n = "mpc_batchrec_mask", int(rows) * int(cols)
+    a = [_sized(fn, name, t, n, ring.words) for name, t in
+         (("X_i", X_i), ("A_i", A_i), ("R_i", R_i), ("mX_i", mX_i), ("mA_i", mA_i), ("mR_i", mR_i),
+          ("W_i", W_i), ("mW_i", mW_i))]
+    _check(fn, load().mpc_batchrec_mask(ctypes.byref(ring), int(rows), int(cols), *a, _stream(stream)))
     return W_i, mW_i
 
 
@@ -324,9 +372,10 @@ def mpc_lincomb(k, s, coefs, ins, out, stream=None):
     ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
     n = out.numel() // ring.words if out is not None and hasattr(out, "numel") else 0
     c = (ctypes.c_int64 * len(coefs))(*[int(x) for x in coefs])
-    p = (ctypes.c_void_p * len(ins))(*[_ptr(t) for t in ins])
-    _check("mpc_lincomb", load().mpc_lincomb(ctypes.byref(ring), int(n), len(coefs), c, p, _ptr(out),
-                                             _stream(stream)))
+    p = (ctypes.c_void_p * len(ins))(*[_sized("mpc_lincomb", f"ins[{j}]", t, n, ring.words)
+                                       for j, t in enumerate(ins)])
+    _check("mpc_lincomb", load().mpc_lincomb(ctypes.byref(ring), int(n), len(coefs), c, p,
+                                             _sized("mpc_lincomb", "out", out, n, ring.words), _stream(stream)))
     return out
 
 
@@ -337,10 +386,13 @@ def mpc_lincomb_grouped(k, s, coefs, ins, outs, stream=None):
     if G == 0:
         return outs
     cnt = len(coefs)
-    n = (ctypes.c_int64 * G)(*[o.numel() // ring.words for o in outs])
+    ns = [o.numel() // ring.words for o in outs]
+    n = (ctypes.c_int64 * G)(*ns)
     c = (ctypes.c_int64 * cnt)(*[int(x) for x in coefs])
-    p = (ctypes.c_void_p * (G * cnt))(*[_ptr(t) for g in ins for t in g])
-    o = (ctypes.c_void_p * G)(*[_ptr(t) for t in outs])
+    fn = "mpc_lincomb_grouped"
+    p = (ctypes.c_void_p * (G * cnt))(*[_sized(fn, f"ins[{g}][{j}]", t, ns[g], ring.words)
+                                        for g in range(G) for j, t in enumerate(ins[g])])
+    o = (ctypes.c_void_p * G)(*[_sized(fn, f"outs[{g}]", t, ns[g], ring.words) for g, t in enumerate(outs)])
     _check("mpc_lincomb_grouped", load().mpc_lincomb_grouped(ctypes.byref(ring), G, n, cnt, c, p, o,
                                                              _stream(stream)))
     return outs
@@ -353,24 +405,35 @@ def mpc_tag_check_grouped(layers, ptrs, stream=None):
     arr = (mpc_layer * len(layers))(*layers)
     pa = (mpc_check_ptrs * len(layers))()
     for i, d in enumerate(ptrs):
+        L = layers[i]
+        elems = dict(alpha_i=1, chi_hat=L.M, Dc=L.M, mDc_i=L.M, cs_i=1)
         for f in CHECK_PTR_FIELDS:
-            setattr(pa[i], f, _ptr(d[f]))
+            setattr(pa[i], f, _sized("mpc_tag_check_grouped", f"layers[{i}].{f}", d[f], elems[f], L.ring.words))
     _check("mpc_tag_check_grouped", load().mpc_tag_check_grouped(arr, len(layers), pa, _stream(stream)))
 
 
 def mpc_im2col(k, s, batch, channels, height, width, f, pad, stride, src, dst, stream=None):
     """dst = the im2col matrix of NCHW images src for an f x f filter (zero padding, stride)."""
     ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
+    src_p, dst_p = _ptr(src), _ptr(dst)
+    if f >= 1 and 0 <= pad < f and stride >= 1 and height + 2 * pad >= f and width + 2 * pad >= f:
+        # sizes of a valid call (the library rejects the others with MPC_E_SHAPE)
+        ho, wo = (height - f + 2 * pad) // stride + 1, (width - f + 2 * pad) // stride + 1
+        src_p = _sized("mpc_im2col", "src", src, batch * channels * height * width, ring.words)
+        dst_p = _sized("mpc_im2col", "dst", dst, batch * ho * wo * channels * f * f, ring.words)
     _check("mpc_im2col", load().mpc_im2col(ctypes.byref(ring), int(batch), int(channels), int(height), int(width),
-                                           int(f), int(pad), int(stride), _ptr(src), _ptr(dst), _stream(stream)))
+                                           int(f), int(pad), int(stride), src_p, dst_p, _stream(stream)))
     return dst
 
 
 def mpc_transpose(k, s, rows, cols, src, dst, stream=None):
     """dst (cols x rows) = src (rows x cols)^T, ring elements of Z_2^(k+s)."""
     ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
-    _check("mpc_transpose", load().mpc_transpose(ctypes.byref(ring), int(rows), int(cols), _ptr(src),
-                                                 _ptr(dst), _stream(stream)))
+    n = int(rows) * int(cols)
+    _check("mpc_transpose", load().mpc_transpose(ctypes.byref(ring), int(rows), int(cols),
+                                                 _sized("mpc_transpose", "src", src, n, ring.words),
+                                                 _sized("mpc_transpose", "dst", dst, n, ring.words),
+                                                 _stream(stream)))
     return dst
 
 
@@ -383,11 +446,17 @@ def _layer_array(layers):
     return arr
 
 
-def _ptr_array(cls, fields, ptrs):
+def _ptr_array(cls, fields, ptrs, fn, layers, elems_of):
+    """ctypes array of pointer structs; elems_of(layer) gives each field's
+    element count (fields it omits are not read by the call)."""
     arr = (cls * len(ptrs))()
     for i, d in enumerate(ptrs):
+        L = layers[i]
+        elems = elems_of(L)
         for f in fields:
-            setattr(arr[i], f, _ptr(d.get(f)))
+            t = d.get(f)
+            setattr(arr[i], f, _sized(fn, f"layers[{i}].{f}", t, elems[f], L.ring.words) if f in elems
+                    else _ptr(t))
     return arr
 
 
@@ -410,19 +479,20 @@ def _ws_grouped(layers, which, ws, stream=None):
 
 def mpc_linear_share_grouped(layers, ptrs, ws=None, stream=None):
     """Shares of many layers in one call (same results as one mpc_linear_share per layer)."""
+    fn = "mpc_linear_share_grouped"
+    pa = _ptr_array(mpc_share_ptrs, SHARE_PTR_FIELDS, ptrs, fn, layers, lambda L: _share_elems(L.M, L.K, L.N))
     wp, wb = _ws_grouped(layers, MPC_WS_SHARE, ws, stream)
-    _check("mpc_linear_share_grouped", load().mpc_linear_share_grouped(
-        _layer_array(layers), len(layers), _ptr_array(mpc_share_ptrs, SHARE_PTR_FIELDS, ptrs), wp, wb,
-        _stream(stream)))
+    _check(fn, load().mpc_linear_share_grouped(_layer_array(layers), len(layers), pa, wp, wb, _stream(stream)))
 
 
 def mpc_linear_tag_grouped(layers, mode, ptrs, ws=None, stream=None):
     """Tags of many layers in one call (same results as one mpc_linear_tag per layer)."""
     which = MPC_WS_TAG_FULL if mode == MPC_TAG_FULL else MPC_WS_TAG_COMPACT
+    fn = "mpc_linear_tag_grouped"
+    pa = _ptr_array(mpc_tag_ptrs, TAG_PTR_FIELDS, ptrs, fn, layers, lambda L: _tag_elems(L.M, L.K, L.N, mode))
     wp, wb = _ws_grouped(layers, which, ws, stream)
-    _check("mpc_linear_tag_grouped", load().mpc_linear_tag_grouped(
-        _layer_array(layers), len(layers), int(mode), _ptr_array(mpc_tag_ptrs, TAG_PTR_FIELDS, ptrs), wp, wb,
-        _stream(stream)))
+    _check(fn, load().mpc_linear_tag_grouped(_layer_array(layers), len(layers), int(mode), pa, wp, wb,
+                                             _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

@@ -281,3 +281,48 @@ def test_grouped_check_and_lincomb_validation(lib):
     assert lib.mpc_lincomb_grouped(R, 2, n, 3, c, bad, outs, None) == abi.MPC_E_ALIGN
     neg = (ctypes.c_int64 * 2)(8, -1)
     assert lib.mpc_lincomb_grouped(R, 2, neg, 3, c, ins, outs, None) == abi.MPC_E_SHAPE
+
+
+def test_binding_rejects_short_tensors_before_the_call():
+    """The binding checks every tensor argument against the element counts the
+    header gives for the call, so a buffer that is too short (here: s-bit
+    values stored one word each for Z_2^128, where the call reads ring
+    elements of two words) raises before any kernel could read past its end."""
+    import torch
+    M, K, N = 5, 3, 7
+    lay = abi.make_layer(M, K, N, 64, 64)
+    full = lambda *shape: torch.zeros(shape + (2,), dtype=torch.int64)
+    x = dict(alpha_i=full(1), E=full(M, K), F=full(K, N), mA_i=full(M, K), mB_i=full(K, N), mC_i=full(M, N),
+             mR_i=full(M, N), Dtilde=full(M, N), chi=full(N), mZ_i=full(M, N), mDc_i=full(M), Dc=full(M))
+    # the right sizes pass the check
+    assert len(abi._args("f", lay, abi._tag_elems(M, K, N, abi.MPC_TAG_COMPACT), x)) == 12
+    short = dict(x, chi=torch.zeros(N, dtype=torch.int64))
+    with pytest.raises(ValueError, match="chi"):
+        abi.mpc_linear_tag(lay, abi.MPC_TAG_COMPACT, **short)
+    with pytest.raises(ValueError, match="alpha_i"):
+        abi.mpc_linear_tag_compact_noalloc(lay, **dict(x, alpha_i=torch.zeros(1, dtype=torch.int64)))
+    with pytest.raises(ValueError, match="not contiguous"):
+        abi.mpc_linear_share(lay, x["E"], full(N, K).transpose(0, 1), x["mA_i"], x["mB_i"], x["mC_i"], x["mZ_i"])
+    with pytest.raises(ValueError, match="Z_i"):
+        abi.mpc_linear_share(lay, x["E"], x["F"], x["mA_i"], x["mB_i"], x["mC_i"], full(M, N - 1))
+    # inputs the mode ignores are not checked; the ones it reads are
+    assert abi._args("f", lay, abi._tag_elems(M, K, N, abi.MPC_TAG_FULL), dict(x, chi=full(1)))
+    with pytest.raises(ValueError, match="tag_i"):
+        abi.mpc_tag_check(lay, abi.MPC_CHECK_COMPACT, x["alpha_i"], x["Dc"], x["Dc"], full(M - 1), full(1))
+    # the seeded check's chi_hat is one 64-bit seed word
+    seed = torch.zeros(1, dtype=torch.int64)
+    with pytest.raises(ValueError, match="opened"):
+        abi.mpc_tag_check(lay, abi.MPC_CHECK_BATCHREC_SEEDED, x["alpha_i"], seed, full(M), x["mC_i"], full(1))
+    # grouped calls name the layer
+    lays = [abi.make_layer(M, K, N, 64, 64), abi.make_layer(M + 1, K, N, 64, 64)]
+    with pytest.raises(ValueError, match=r"layers\[1\]\.E"):
+        abi.mpc_linear_tag_grouped(lays, abi.MPC_TAG_COMPACT, [x, x])
+    with pytest.raises(ValueError, match=r"layers\[1\]\.chi_hat"):
+        abi.mpc_tag_check_grouped(lays, [dict(alpha_i=x["alpha_i"], chi_hat=x["Dc"], Dc=x["Dc"], mDc_i=x["Dc"],
+                                              cs_i=x["alpha_i"])] * 2)
+    with pytest.raises(ValueError, match=r"ins\[1\]\[0\]"):
+        abi.mpc_lincomb_grouped(64, 64, [1], [[full(4)], [full(3)]], [full(4), full(4)])
+    with pytest.raises(ValueError, match="dst"):
+        abi.mpc_transpose(64, 64, 3, 4, full(3, 4), full(11))
+    with pytest.raises(ValueError, match="dst"):
+        abi.mpc_im2col(64, 64, 1, 2, 5, 5, 3, 1, 1, full(2, 5, 5), full(25, 17))

@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import synth
 from paper_2311_04406_gb300 import abi, build
 
@@ -25,11 +26,17 @@ pytestmark = pytest.mark.gpu
 
 
 def _inputs(ring, M, K, N, seed):
-    b = ring.bits
-    g = lambda name, shape, bits=b: synth.uniform(seed, synth.TID[name], 0, shape, bits)
-    return dict(alpha=g("alpha", (1,), ring.s), E=g("E", (M, K)), F=g("F", (K, N)),
+    g = lambda name, shape: synth.uniform(seed, synth.TID[name], 0, shape, ring.bits)
+
+    def key(name, shape):
+        # s-bit values (the MAC key share, the compression vector) stored as
+        # ring elements: in Z_2^128 each takes two words, the high one zero
+        v = synth.uniform(seed, synth.TID[name], 0, shape, ring.s)
+        return v if ring.words == 1 else np.stack([v, np.zeros_like(v)], axis=-1)
+
+    return dict(alpha=key("alpha", (1,)), E=g("E", (M, K)), F=g("F", (K, N)),
                 mA=g("mA", (M, K)), mB=g("mB", (K, N)), mC=g("mC", (M, N)), mR=g("mR", (M, N)),
-                Dt=g("Dt", (M, N)), chi=g("chi", (N,), ring.s))
+                Dt=g("Dt", (M, N)), chi=key("chi", (N,)))
 
 
 def _dev(a):
@@ -41,7 +48,12 @@ def _pad(words, ring):
 
 
 def _both(ring, M, K, N, seed):
-    x = {k: _dev(v) for k, v in _inputs(ring, M, K, N, seed).items()}
+    host = _inputs(ring, M, K, N, seed)
+    # every buffer holds exactly the ring elements the call reads
+    elems = dict(alpha=1, E=M * K, F=K * N, mA=M * K, mB=K * N, mC=M * N, mR=M * N, Dt=M * N, chi=N)
+    for name, n in elems.items():
+        assert host[name].size == n * ring.words, name
+    x = {k: _dev(v) for k, v in host.items()}
     lay = abi.make_layer(M, K, N, ring.k, ring.s, party=1, nparties=2)
     outs = []
     for noalloc in (False, True):
@@ -57,7 +69,11 @@ def _both(ring, M, K, N, seed):
                                mDc_i=mDc, Dc=Dc)
         torch.cuda.synchronize()
         outs.append((mZ.cpu(), mDc.cpu(), Dc.cpu()))
-    return outs
+    return host, outs
+
+
+def _as_ring(t, ring):
+    return t.numpy().view(np.uint64)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -76,9 +92,16 @@ def test_noalloc_equals_workspace_entry_point_on_consecutive_calls():
     for ring, M, K, N, seed in cases:
         lay = abi.make_layer(M, K, N, ring.k, ring.s)
         assert abi.mpc_workspace_size(lay, abi.MPC_WS_TAG_COMPACT) <= abi.MPC_NOALLOC_SCRATCH_BYTES
-        (ref, got) = _both(ring, M, K, N, seed)
+        host, (ref, got) = _both(ring, M, K, N, seed)
         for a, b, name in zip(ref, got, ("mZ", "mDc", "Dc")):
             assert torch.equal(a, b), f"{name} differs for {(M, K, N)} w={ring.words}"
+        # and both equal the oracle
+        h = host
+        mDc, Dc, _ = O.compact_tag(ring.bits, h["alpha"], h["E"], h["F"], h["mA"], h["mB"], h["mC"],
+                                   h["mR"], h["Dt"], h["chi"])
+        assert np.array_equal(_as_ring(got[0], ring), O.optmac(ring.bits, h["alpha"], h["mR"], h["Dt"]))
+        assert np.array_equal(_as_ring(got[1], ring), mDc), f"mDc vs oracle for {(M, K, N)}"
+        assert np.array_equal(_as_ring(got[2], ring), Dc), f"Dc vs oracle for {(M, K, N)}"
 
 
 @pytest.mark.hidden_gpu
