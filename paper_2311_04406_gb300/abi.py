@@ -379,21 +379,23 @@ def mpc_lincomb(k, s, coefs, ins, out, stream=None):
     return out
 
 
-def mpc_lincomb_grouped(k, s, coefs, ins, outs, stream=None):
-    """outs[g] = sum_j coefs[j] * ins[g][j] for every group g (one launch per 64 groups)."""
+def mpc_lincomb_grouped(k, s, coefs, ins, outs, stream=None, n=None):
+    """outs[g] = sum_j coefs[j] * ins[g][j] for every group g (one launch per 64 groups).
+    n[g]: ring elements of group g; taken from outs[g] when omitted (tensors),
+    required when the buffers are raw addresses."""
     ring = mpc_ring(int(k), int(s), (int(k) + int(s) + 63) // 64)
     G = len(outs)
     if G == 0:
         return outs
     cnt = len(coefs)
-    ns = [o.numel() // ring.words for o in outs]
-    n = (ctypes.c_int64 * G)(*ns)
+    ns = [int(x) for x in n] if n is not None else [o.numel() // ring.words for o in outs]
+    nv = (ctypes.c_int64 * G)(*ns)
     c = (ctypes.c_int64 * cnt)(*[int(x) for x in coefs])
     fn = "mpc_lincomb_grouped"
     p = (ctypes.c_void_p * (G * cnt))(*[_sized(fn, f"ins[{g}][{j}]", t, ns[g], ring.words)
                                         for g in range(G) for j, t in enumerate(ins[g])])
     o = (ctypes.c_void_p * G)(*[_sized(fn, f"outs[{g}]", t, ns[g], ring.words) for g, t in enumerate(outs)])
-    _check("mpc_lincomb_grouped", load().mpc_lincomb_grouped(ctypes.byref(ring), G, n, cnt, c, p, o,
+    _check("mpc_lincomb_grouped", load().mpc_lincomb_grouped(ctypes.byref(ring), G, nv, cnt, c, p, o,
                                                              _stream(stream)))
     return outs
 

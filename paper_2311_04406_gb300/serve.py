@@ -61,13 +61,14 @@ class Request:
     arrival: float                 # seconds after the run starts
     seed: int
     layers: list = field(default_factory=list)
-    bufs: list = None              # per layer: dict of device tensors
+    bufs: list = None              # per layer: device addresses (tensors once kept)
     region: tuple = None           # (offset, bytes) in the server's arena
-    plan: list = None              # per layer: key -> (shape, byte offset in the region)
+    plan: list = None              # per layer: key -> (shape, byte offset in the region, words)
     nxt: int = 0                   # next layer to run
     ready: object = None           # event: shares materialised
     done_ms: float = None          # device time of completion
     admit_s: float = None
+    carve: tuple = None            # (words, _carve(layers, words)), made once per ring width
 
     @property
     def units(self) -> int:
@@ -84,13 +85,14 @@ def _carve(layers, words: int):
     the pool-filled inputs (256-byte aligned tensors), the keys and combiners
     (alpha, chi, chi^: 16-byte aligned, filled by one generator call) and the
     outputs.  Returns (plan, inputs_end, keys_end, total), plan[layer][key] =
-    (shape, byte offset)."""
+    (shape, byte offset, words)."""
     shp = (lambda *d: d + ((2,) if words == 2 else ()))
     plan = [dict() for _ in layers]
 
     def put(li, k, shape, off, align):
-        plan[li][k] = (shape, off)
-        return off + (8 * int(np.prod(shape)) + align - 1) // align * align
+        n = math.prod(shape)            # words (plain ints: this runs per admitted request)
+        plan[li][k] = (shape, off, n)
+        return off + (8 * n + align - 1) // align * align
 
     off = 0
     for li, L in enumerate(layers):
@@ -164,11 +166,13 @@ class Arena(RangeAllocator):
     def __init__(self, torch, nbytes: int):
         super().__init__(nbytes)
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.words = self.buf.view(torch.int64)
+        self.base = self.buf.data_ptr()     # device address of byte 0
 
-    def view(self, off: int, shape):
-        import torch
-        n = int(np.prod(shape))
-        return self.buf[off:off + 8 * n].view(torch.int64).view(shape)
+    def view(self, off: int, shape, n: int = None):
+        """int64 tensor of `shape` at byte offset `off` (a multiple of 8)."""
+        n = math.prod(shape) if n is None else n
+        return self.words[off // 8:off // 8 + n].view(shape)
 
 
 def make_requests(n: int, rate: float, seed: int, max_batch: int = 32, models=("resnet18", "vgg16"),
@@ -207,6 +211,7 @@ class Server:
         self._seen = collections.OrderedDict()      # tick keys issued eagerly once
         self._cap_stream = None
         self.tick_counts = {"eager": 0, "captured": 0, "replayed": 0}
+        self._ws_cache = {}
         abi.load()
         # every admitted request's shares live in this arena: its size is the
         # memory budget that gates admission
@@ -229,7 +234,7 @@ class Server:
         torch = self.torch
         w = self.ring.words
         base = req.region[0]
-        plan, inputs_end, keys_end, _ = _carve(req.layers, w)
+        plan, inputs_end, keys_end, _ = req.carve[1]
         rng = np.random.default_rng(req.seed)
         gen = torch.Generator(device="cuda")
         gen.manual_seed(req.seed)
@@ -256,28 +261,42 @@ class Server:
         req.bufs = [None] * len(req.layers)
         req.ready = ev
 
-    def _bufs(self, req: Request, li: int) -> dict:
-        """The tensors of layer li of a request (views into its arena range)."""
+    def _layer_args(self, req: Request, li: int) -> dict:
+        """The call arguments of layer li of a request: the device address of
+        each of its tensors in the arena (plain ints: the library reads the
+        layouts the plan gives them, and a tick builds no tensor objects), the
+        mpc_layer and the workspace it needs."""
         d = req.bufs[li]
         if d is None:
-            base = req.region[0]
-            d = {k: self.arena.view(base + off, shape) for k, (shape, off) in req.plan[li].items()}
+            base = self.arena.base + req.region[0]
+            d = {k: base + off for k, (_, off, _) in req.plan[li].items()}
             L = req.layers[li]
             d["layer"] = abi.make_layer(L.M, L.K, L.N, self.ring.k, self.ring.s, self.party, self.nparties)
-            d["ws_need"] = (self._layer_ws(d["layer"]) + 255) // 256 * 256
+            d["ws_need"] = self._layer_ws(L.M, L.K, L.N)
             req.bufs[li] = d
         return d
 
-    def _layer_ws(self, L) -> int:
-        which = (abi.MPC_WS_SHARE, abi.MPC_WS_TAG_COMPACT if self.tag == "compact" else abi.MPC_WS_TAG_FULL)
-        return max(abi.mpc_workspace_size_grouped([L], w) for w in which)
+    def _views(self, req: Request, li: int) -> dict:
+        """Tensor views of layer li of a request (for reading its outputs)."""
+        base = req.region[0]
+        return {k: self.arena.view(base + off, shape, n) for k, (shape, off, n) in req.plan[li].items()}
+
+    def _layer_ws(self, M, K, N) -> int:
+        key = (M, K, N, self.tag)
+        need = self._ws_cache.get(key)
+        if need is None:
+            L = abi.make_layer(M, K, N, self.ring.k, self.ring.s, self.party, self.nparties)
+            which = (abi.MPC_WS_SHARE, abi.MPC_WS_TAG_COMPACT if self.tag == "compact" else abi.MPC_WS_TAG_FULL)
+            need = self._ws_cache[key] = (max(abi.mpc_workspace_size_grouped([L], w) for w in which)
+                                          + 255) // 256 * 256
+        return need
 
     def _parts(self, group):
         """`group` split into parts whose grouped calls fit the workspace; the
         last part may need a workspace of its own (returned size > 0)."""
         parts, part, used = [], [], 0
         for r in group:
-            need = self._bufs(r, r.nxt)["ws_need"]
+            need = self._layer_args(r, r.nxt)["ws_need"]
             if part and used + need > self.ws.numel():
                 parts.append(part)
                 part, used = [], 0
@@ -344,7 +363,7 @@ class Server:
 
     def _tick_part(self, group, ws):
         a = abi
-        bufs = [self._bufs(r, r.nxt) for r in group]
+        bufs = [self._layer_args(r, r.nxt) for r in group]
         layers = [d["layer"] for d in bufs]
         a.mpc_linear_share_grouped(layers, [dict(E=d["E"], F=d["F"], A_i=d["A"], B_i=d["B"], C_i=d["C"],
                                                  Z_i=d["Z"]) for d in bufs], ws=ws)
@@ -354,7 +373,7 @@ class Server:
             # every layer of the tick in one call
             k, s = self.ring.k, self.ring.s
             a.mpc_lincomb_grouped(k, s, [1, -1, 1], [[d["R"], d["Z"], d["Drest"]] for d in bufs],
-                                  [d["Dt"] for d in bufs])
+                                  [d["Dt"] for d in bufs], n=[d["layer"].M * d["layer"].N for d in bufs])
         tp = [dict(alpha_i=d["alpha"], E=d["E"], F=d["F"], mA_i=d["mA"], mB_i=d["mB"], mC_i=d["mC"],
                    mR_i=d["mR"], Dtilde=d["Dt"], chi=d["chi"], mZ_i=d["mZ"], mDc_i=d["mDc"], Dc=d["Dc"])
               for d in bufs]
@@ -416,8 +435,8 @@ class Server:
                         # outputs stay readable: copy them out of the arena before
                         # the range is handed to the next request (whose shares
                         # are written on the side stream)
-                        r.bufs = [{k: (v.clone() if hasattr(v, "clone") else v)
-                                   for k, v in self._bufs(r, li).items()} for li in range(len(r.layers))]
+                        r.bufs = [{k: v.clone() for k, v in self._views(r, li).items()}
+                                  for li in range(len(r.layers))]
                         st.synchronize()
                     else:
                         r.bufs = None
@@ -435,7 +454,9 @@ class Server:
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
             while waiting:
-                need = request_bytes(waiting[0].layers, words)
+                if waiting[0].carve is None or waiting[0].carve[0] != words:
+                    waiting[0].carve = (words, _carve(waiting[0].layers, words))
+                need = waiting[0].carve[1][3]
                 off = self.arena.alloc(need)
                 if off is None:
                     if not (active or inflight):

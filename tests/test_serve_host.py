@@ -50,8 +50,9 @@ def test_request_layout():
             for li, L in enumerate(r.layers):
                 assert set(plan[li]) == {"E", "A", "mA", "F", "B", "mB", "C", "mC", "R", "mR", "Drest", "alpha",
                                          "chi", "chi_hat", "Z", "mZ", "Dt", "mDc", "Dc", "cs"}
-                for k, (shape, off) in plan[li].items():
-                    n = 8 * int(np.prod(shape))
+                for k, (shape, off, words_k) in plan[li].items():
+                    assert words_k == int(np.prod(shape))
+                    n = 8 * words_k
                     assert off % 16 == 0 and off + n <= total
                     assert shape[-1] == 2 if words == 2 else True
                     spans.append((off, n))
