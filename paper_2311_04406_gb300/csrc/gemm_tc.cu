@@ -151,6 +151,77 @@ __device__ __forceinline__ uint32_t digit_pair(uint32_t a, uint32_t c, uint32_t 
     return o;
 }
 
+// ---------------------------------------------------------------------------
+// drain arithmetic
+//
+// The value d of diagonal t (an integer, |d| <= 2^24, converted exactly from
+// its fp32 accumulator) adds d 2^(8t) to its output's wrapping sum mod
+// 2^(64 W).  Z_2^64 adds the sign-extended, shifted term.  Z_2^128 touches
+// only the words of the sum a term can change: the two diagonals t, t + 1 of
+// one TMEM load (t even) first form g = d_t 2^(8 (t mod 4)) +
+// d_(t+1) 2^(8 ((t+1) mod 4)), |g| < 2^41, which is added to the sum's four
+// 32-bit words as g 2^0 (t < 4), g 2^32 (t < 8), g mod 2^64 at 2^64 (t < 12)
+// or g mod 2^32 at 2^96, with explicit carry chains.
+
+__device__ __forceinline__ long long mad_wide_s32(int a, int b, long long c) {
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// sum + g 2^(32 q) mod 2^128 for a signed 64-bit g (q = 0, 1, 2) or, q = 3,
+// the low 32 bits of g at 2^96
+template <int Q>
+__device__ __forceinline__ u128 add_at(u128 sum, long long g) {
+    u64 lo = (u64)sum, hi = (u64)(sum >> 64);
+    const uint32_t gl = (uint32_t)(u64)g, gh = (uint32_t)((u64)g >> 32);
+    const uint32_t sg = (uint32_t)(g >> 63);   // sign word (0 or ~0)
+    uint32_t w0, w1, w2, w3;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(w0), "=r"(w1) : "l"(lo));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(w2), "=r"(w3) : "l"(hi));
+    if constexpr (Q == 0) {
+        asm("add.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, %5;\n\taddc.cc.u32 %2, %2, %6;\n\taddc.u32 %3, %3, %6;"
+            : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3) : "r"(gl), "r"(gh), "r"(sg));
+    } else if constexpr (Q == 1) {
+        asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
+            : "+r"(w1), "+r"(w2), "+r"(w3) : "r"(gl), "r"(gh), "r"(sg));
+    } else if constexpr (Q == 2) {
+        asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(w2), "+r"(w3) : "r"(gl), "r"(gh));
+    } else {
+        w3 += gl;
+    }
+    asm("mov.b64 %0, {%1, %2};" : "=l"(lo) : "r"(w0), "r"(w1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(hi) : "r"(w2), "r"(w3));
+    return (u128)lo | ((u128)hi << 64);
+}
+
+// One 32-column TMEM load of diagonals t0 .. t0 + 32 / NC - 1 (NC columns
+// each) into the NC sums.
+template <int W, int NC>
+__device__ __forceinline__ void drain_fold(const uint32_t (&f)[32], int t0, typename Elem<W>::T (&sum)[NC]) {
+    if constexpr (W == 1) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int t = t0 + q / NC, c = q % NC;
+            const long long d = __float2int_rn(__uint_as_float(f[q]));
+            sum[c] += (u64)d << (8 * t);
+        }
+    } else {
+        static_assert(NC == 16, "two diagonals per load");
+        const int s0 = 8 * (t0 & 3), s1 = 8 * ((t0 + 1) & 3);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int d0 = __float2int_rn(__uint_as_float(f[c]));
+            const int d1 = __float2int_rn(__uint_as_float(f[NC + c]));
+            const long long g = mad_wide_s32(d1, 1 << s1, (long long)d0 << s0);
+            if (t0 < 4) sum[c] = add_at<0>(sum[c], g);
+            else if (t0 < 8) sum[c] = add_at<1>(sum[c], g);
+            else if (t0 < 12) sum[c] = add_at<2>(sum[c], g);
+            else sum[c] = add_at<3>(sum[c], g);
+        }
+    }
+}
+
 // A ring element with the digit bias added, as 2 W 32-bit words (little
 // endian): word t / 4, byte t % 4 holds the biased digit t.
 template <int W> struct Biased { uint32_t w[2 * W]; };
@@ -975,14 +1046,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
                 }
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int t = t0 + q / ND, c = q % ND;
-                    const long long d = __float2int_rn(__uint_as_float(f[q]));
-                    // sign-extend to the ring width, then weight by 2^(8t)
-                    const Sum dv = (Sum)(W == 1 ? (Sum)(u64)d : (Sum)(__int128)d);
-                    sum[c] += dv << (8 * t);
-                }
+                drain_fold<W, ND>(f, t0, sum);
             }
             if (seg_ii < 0) seg_ii = x_ii;
             if (x_flush) {
@@ -1354,13 +1418,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
                 }
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int t = t0 + q / ND, c = q % ND;
-                    const long long d = __float2int_rn(__uint_as_float(f[q]));
-                    const Sum dv = (Sum)(W == 1 ? (Sum)(u64)d : (Sum)(__int128)d);
-                    sum[c] += dv << (8 * t);
-                }
+                drain_fold<W, ND>(f, t0, sum);
             }
             if (seg_ii < 0) seg_ii = x_ii;
             if (x_flush) {
@@ -1828,13 +1886,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
                 }
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int t = t0 + q / ND, c = q % ND;
-                    const long long d = __float2int_rn(__uint_as_float(f[q]));
-                    const Sum dv = (Sum)(W == 1 ? (Sum)(u64)d : (Sum)(__int128)d);
-                    sum[c] += dv << (8 * t);
-                }
+                drain_fold<W, ND>(f, t0, sum);
             }
             if (seg_ii < 0) seg_ii = x_ii;
             if (x_flush) {

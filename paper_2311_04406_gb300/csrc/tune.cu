@@ -52,13 +52,13 @@ bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
 int default_rows(int64_t M, int64_t K, int64_t N, int words) {
     if (M <= 2 * wide_tile_rows(words)) return wide_tile_rows(words);
     if (M <= 64) return 64;
-    // tall and narrow Z_2^64 layers: the left operand's digit planes would cost
-    // an HBM round trip comparable to the GEMM itself, so the GEMM converts them
-    // in place (measured: 32768 x 576 x 64 share 285 -> 207 us; equal at
-    // N = 128; in Z_2^128 the raw tiles' extra shared-memory traffic cancels
-    // the saving: 829 -> 842 us)
-    // (at M = 1024 it is 2 us slower per call: its small R' prologue runs on few blocks)
-    if (words == 1 && N <= 64 && M >= 2048 && gemm_tc_feasible(M, K, N, words, TALL_TILE_ROWS))
+    // tall and narrow layers: the left operand's digit planes would cost an HBM
+    // round trip comparable to the GEMM itself, so the GEMM converts them in
+    // place (measured, N = 64: Z_2^64 32768 x 576 x 64 share 285 -> 207 us, but
+    // 2 us slower at M = 1024, where its small R' prologue runs on few blocks;
+    // Z_2^128 3-17 % faster from M = 1024 to 32768, e.g. 821 -> 686 us at
+    // 32768 rows; at N >= 128 the 128-row tile is as fast or faster)
+    if (N <= 64 && M >= (words == 1 ? 2048 : 1024) && gemm_tc_feasible(M, K, N, words, TALL_TILE_ROWS))
         return TALL_TILE_ROWS;
     return 128;
 }
