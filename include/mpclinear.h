@@ -243,7 +243,7 @@ int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
  * shapes use a built-in rule (tensor cores from 2^22 ring MACs, 2^20 for
  * Z_2^128; the wide tile up to two of its row tiles, 64-row tiles up to
  * M = 64, the tall tile for layers with N <= 64 and M >= 2048 (Z_2^64) or
- * M >= 1024 (Z_2^128)).  The table is process-wide and thread-safe; workspace
+ * M >= 1024 (Z_2^128), and for N <= 128 from M = 4096).  The table is process-wide and thread-safe; workspace
  * sizes do not depend on it.
  *
  * mpc_autotune: for each distinct shape of layers[count], times the

@@ -222,6 +222,17 @@ __device__ __forceinline__ void drain_fold(const uint32_t (&f)[32], int t0, type
     }
 }
 
+// fp16x2 digits of bytes 0-3 of a and c: h[b] = {digit of byte b of a, digit
+// of byte b of c}.  One permute gathers bytes 0-1 (2-3) of both words, one
+// more per pair places them under 0x64: 6 ALU operations per 8 digits.
+__device__ __forceinline__ void digit_quad(uint32_t a, uint32_t c, uint32_t (&h)[4]) {
+    const uint32_t lo = __byte_perm(a, c, 0x5140), hi = __byte_perm(a, c, 0x7362);
+    const uint32_t r[4] = {__byte_perm(lo, 0x64646464u, 0x5140), __byte_perm(lo, 0x64646464u, 0x5342),
+                           __byte_perm(hi, 0x64646464u, 0x5140), __byte_perm(hi, 0x64646464u, 0x5342)};
+#pragma unroll
+    for (int b = 0; b < 4; ++b) asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(h[b]) : "r"(r[b]), "r"(F16_1152X2));
+}
+
 // A ring element with the digit bias added, as 2 W 32-bit words (little
 // endian): word t / 4, byte t % 4 holds the biased digit t.
 template <int W> struct Biased { uint32_t w[2 * W]; };
@@ -234,12 +245,11 @@ __device__ __forceinline__ Biased<W> biased(const u64* e) {
         b.w[0] = (uint32_t)y;
         b.w[1] = (uint32_t)(y >> 32);
     } else {
-        const u64 lo = e[0] + DIGIT_BIAS;
-        const u64 hi = e[1] + DIGIT_BIAS + (lo < e[0] ? 1ull : 0ull);
-        b.w[0] = (uint32_t)lo;
-        b.w[1] = (uint32_t)(lo >> 32);
-        b.w[2] = (uint32_t)hi;
-        b.w[3] = (uint32_t)(hi >> 32);
+        // one carry chain over the four 32-bit words
+        asm("add.cc.u32 %0, %4, 0x80808080;\n\taddc.cc.u32 %1, %5, 0x80808080;\n\t"
+            "addc.cc.u32 %2, %6, 0x80808080;\n\taddc.u32 %3, %7, 0x80808080;"
+            : "=r"(b.w[0]), "=r"(b.w[1]), "=r"(b.w[2]), "=r"(b.w[3])
+            : "r"((uint32_t)e[0]), "r"((uint32_t)(e[0] >> 32)), "r"((uint32_t)e[1]), "r"((uint32_t)(e[1] >> 32)));
     }
     return b;
 }
@@ -1320,16 +1330,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
                 Biased<W> b[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
+                // word wi of the 8 values gives planes 4 wi .. 4 wi + 3
 #pragma unroll
-                for (int t = 0; t < NDIG; ++t) {
-                    const int wi = t >> 2;
-                    const uint32_t byte = t & 3;
-                    uint4 o;
-                    o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
-                    o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
-                    o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
-                    o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
-                    *reinterpret_cast<uint4*>(dst + t * A_PLANE + kh * CORE_LBO) = o;
+                for (int wi = 0; wi < 2 * W; ++wi) {
+                    uint32_t h[4][4];   // [value pair][byte]
+#pragma unroll
+                    for (int pr = 0; pr < 4; ++pr) digit_quad(b[2 * pr].w[wi], b[2 * pr + 1].w[wi], h[pr]);
+#pragma unroll
+                    for (int byte = 0; byte < 4; ++byte)
+                        *reinterpret_cast<uint4*>(dst + (4 * wi + byte) * A_PLANE + kh * CORE_LBO) =
+                            make_uint4(h[0][byte], h[1][byte], h[2][byte], h[3][byte]);
                 }
             }
             // each thread orders its plane writes before the MMAs (async proxy);
@@ -1791,16 +1801,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __
                 Biased<W> b[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
+                // word wi of the 8 values gives planes 4 wi .. 4 wi + 3
 #pragma unroll
-                for (int t = 0; t < NDIG; ++t) {
-                    const int wi = t >> 2;
-                    const uint32_t byte = t & 3;
-                    uint4 o;
-                    o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
-                    o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
-                    o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
-                    o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
-                    *reinterpret_cast<uint4*>(dst + t * A_PLANE + kh * CORE_LBO) = o;
+                for (int wi = 0; wi < 2 * W; ++wi) {
+                    uint32_t h[4][4];   // [value pair][byte]
+#pragma unroll
+                    for (int pr = 0; pr < 4; ++pr) digit_quad(b[2 * pr].w[wi], b[2 * pr + 1].w[wi], h[pr]);
+#pragma unroll
+                    for (int byte = 0; byte < 4; ++byte)
+                        *reinterpret_cast<uint4*>(dst + (4 * wi + byte) * A_PLANE + kh * CORE_LBO) =
+                            make_uint4(h[0][byte], h[1][byte], h[2][byte], h[3][byte]);
                 }
             }
             ptx::fence_proxy_async_smem();

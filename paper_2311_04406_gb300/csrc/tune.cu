@@ -54,11 +54,14 @@ int default_rows(int64_t M, int64_t K, int64_t N, int words) {
     if (M <= 64) return 64;
     // tall and narrow layers: the left operand's digit planes would cost an HBM
     // round trip comparable to the GEMM itself, so the GEMM converts them in
-    // place (measured, N = 64: Z_2^64 32768 x 576 x 64 share 285 -> 207 us, but
-    // 2 us slower at M = 1024, where its small R' prologue runs on few blocks;
-    // Z_2^128 3-17 % faster from M = 1024 to 32768, e.g. 821 -> 686 us at
-    // 32768 rows; at N >= 128 the 128-row tile is as fast or faster)
-    if (N <= 64 && M >= (words == 1 ? 2048 : 1024) && gemm_tc_feasible(M, K, N, words, TALL_TILE_ROWS))
+    // place.  Measured share calls, 128-row tile -> tall tile: Z_2^64
+    // 32768 x 576 x 64 284 -> 184 us and 4096 x 1152 x 128 115 -> 100 us, equal
+    // at 1024 x 576 x 64 (its small R' prologue runs on few blocks); Z_2^128
+    // 32768 x 576 x 64 821 -> 616 us, 1024 x 576 x 64 51 -> 47 us,
+    // 8192 x 1152 x 128 632 -> 585 us, but 2048 x 1152 x 128 196 -> 201 us and
+    // wider layers mostly slower
+    const int64_t tall_from = N <= 64 ? (words == 1 ? 2048 : 1024) : 4096;
+    if (N <= 128 && M >= tall_from && gemm_tc_feasible(M, K, N, words, TALL_TILE_ROWS))
         return TALL_TILE_ROWS;
     return 128;
 }

@@ -104,7 +104,9 @@ def test_built_in_rule_takes_short_tiles_for_short_layers():
     assert abi.mpc_autotune_choice(abi.make_layer(32768, 576, 64, 64, 64))[::4] == (1, -128)   # Z_2^128 tall
     assert abi.mpc_autotune_choice(abi.make_layer(1024, 576, 64, 64, 64))[::4] == (1, -128)
     assert abi.mpc_autotune_choice(abi.make_layer(512, 576, 64, 64, 64))[::4] == (1, 128)
-    assert abi.mpc_autotune_choice(abi.make_layer(32768, 1152, 128, 64, 64))[::4] == (1, 128)  # N > 64
+    assert abi.mpc_autotune_choice(abi.make_layer(32768, 1152, 128, 64, 64))[::4] == (1, -128)  # N <= 128
+    assert abi.mpc_autotune_choice(abi.make_layer(2048, 1152, 128, 64, 64))[::4] == (1, 128)    # from 4096 rows
+    assert abi.mpc_autotune_choice(abi.make_layer(8192, 2304, 256, 64, 64))[::4] == (1, 128)    # N > 128
     assert abi.mpc_autotune_choice(abi.make_layer(1024, 27, 64))[::4] == (0, 0)                 # small: SIMT
     assert abi.mpc_autotune_choice(abi.make_layer(4096, 575, 64))[::4] == (1, 128)   # odd K: not tall
 
