@@ -140,17 +140,6 @@ static_assert(Layout<1>::OFF_INFO % 16 == 0 && Layout<2>::OFF_INFO % 16 == 0, "i
 constexpr unsigned long long DIGIT_BIAS = 0x8080808080808080ULL;
 constexpr uint32_t F16_1152X2 = 0x64806480u;   // fp16 (1152, 1152)
 
-// fp16x2 {digit of byte `b` of a, digit of byte `b` of c}: the byte placed
-// under 0x64 reads as fp16 1024 + byte; subtracting 1152 gives byte - 128.
-__device__ __forceinline__ uint32_t digit_pair(uint32_t a, uint32_t c, uint32_t b) {
-    const uint32_t sel = b | (b << 4) | ((b + 4) << 8) | ((b + 4) << 12);
-    uint32_t r = __byte_perm(a, c, sel);
-    r = (r & 0x00FF00FFu) | 0x64006400u;
-    uint32_t o;
-    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(o) : "r"(r), "r"(F16_1152X2));
-    return o;
-}
-
 // ---------------------------------------------------------------------------
 // drain arithmetic
 //
@@ -252,6 +241,23 @@ __device__ __forceinline__ Biased<W> biased(const u64* e) {
             : "r"((uint32_t)e[0]), "r"((uint32_t)(e[0] >> 32)), "r"((uint32_t)e[1]), "r"((uint32_t)(e[1] >> 32)));
     }
     return b;
+}
+
+
+// The NDIG fp16 digit planes of 8 consecutive K values (biased words b[0..7]):
+// 16 bytes per plane (8 digits), plane t at dst + t * stride.
+template <int W>
+__device__ __forceinline__ void store_planes8(const Biased<W> (&b)[8], uint8_t* dst, uint32_t stride) {
+#pragma unroll
+    for (int wi = 0; wi < 2 * W; ++wi) {
+        uint32_t h[4][4];   // [value pair][byte]
+#pragma unroll
+        for (int pr = 0; pr < 4; ++pr) digit_quad(b[2 * pr].w[wi], b[2 * pr + 1].w[wi], h[pr]);
+#pragma unroll
+        for (int byte = 0; byte < 4; ++byte)
+            *reinterpret_cast<uint4*>(dst + (4 * wi + byte) * stride) =
+                make_uint4(h[0][byte], h[1][byte], h[2][byte], h[3][byte]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -442,17 +448,7 @@ __device__ __forceinline__ void prologue_body(const PrologueParams& p, int grid,
 #pragma unroll
     for (int e = 0; e < 8; ++e) b[e] = biased<W>(x + W * e);
     uint8_t* dst = p.Ap + ((size_t)mt * p.S_tot + kstage) * A_STAGE + rg * CORE_SBO + kg * CORE_LBO + r * 16;
-#pragma unroll
-    for (int t = 0; t < NDIG; ++t) {
-        const int wi = t >> 2;
-        const uint32_t byte = t & 3;
-        uint4 o;
-        o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
-        o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
-        o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
-        o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
-        *reinterpret_cast<uint4*>(dst + t * A_PLANE) = o;
-    }
+    store_planes8<W>(b, dst, A_PLANE);
 }
 
 template <int W, int G, int R, bool WIDE = false>
@@ -937,16 +933,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                 break;
             }
             uint8_t* dst = sB + s * B_STAGE_BYTES + boff;
+            // word wi of the 4 values gives planes 4 wi .. 4 wi + 3
 #pragma unroll
-            for (int tt = 0; tt < TPT; ++tt) {
-                const int t = tlo + tt;
-                const int wi = t >> 2;
-                const uint32_t byte = t & 3;
-                uint2 o;
-                o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
-                o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
-                // stacked row t * ND + ncol: 8-row group (t * ND) / 8 + ncol / 8
-                *reinterpret_cast<uint2*>(dst + t * (ND / 8) * CORE_SBO) = o;
+            for (int wq = 0; wq < TPT / 4; ++wq) {
+                const int wi = tlo / 4 + wq;
+                uint32_t h01[4], h23[4];
+                digit_quad(b[0].w[wi], b[1].w[wi], h01);
+                digit_quad(b[2].w[wi], b[3].w[wi], h23);
+#pragma unroll
+                for (int byte = 0; byte < 4; ++byte) {
+                    const int t = 4 * wi + byte;
+                    // stacked row t * ND + ncol: 8-row group (t * ND) / 8 + ncol / 8
+                    *reinterpret_cast<uint2*>(dst + t * (ND / 8) * CORE_SBO) = make_uint2(h01[byte], h23[byte]);
+                }
             }
             // each thread orders its plane writes before the MMAs (async
             // proxy); the warp then arrives once
@@ -1330,17 +1329,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
                 Biased<W> b[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
-                // word wi of the 8 values gives planes 4 wi .. 4 wi + 3
-#pragma unroll
-                for (int wi = 0; wi < 2 * W; ++wi) {
-                    uint32_t h[4][4];   // [value pair][byte]
-#pragma unroll
-                    for (int pr = 0; pr < 4; ++pr) digit_quad(b[2 * pr].w[wi], b[2 * pr + 1].w[wi], h[pr]);
-#pragma unroll
-                    for (int byte = 0; byte < 4; ++byte)
-                        *reinterpret_cast<uint4*>(dst + (4 * wi + byte) * A_PLANE + kh * CORE_LBO) =
-                            make_uint4(h[0][byte], h[1][byte], h[2][byte], h[3][byte]);
-                }
+                store_planes8<W>(b, dst + kh * CORE_LBO, A_PLANE);
             }
             // each thread orders its plane writes before the MMAs (async proxy);
             // the warp then arrives once
@@ -1589,17 +1578,7 @@ __device__ __forceinline__ void prologue_r_body(const PrologueRParams& p, int gr
     for (int e = 0; e < 8; ++e) b[e] = biased<W>(x + W * e);
     uint8_t* dst = p.Rp + ((size_t)nt * p.S_tot + kstage) * B_STAGE_BYTES + (nl >> 3) * CORE_SBO + kh * CORE_LBO +
                    (nl & 7) * 16;
-#pragma unroll
-    for (int t = 0; t < NDIG; ++t) {
-        const int wi = t >> 2;
-        const uint32_t byte = t & 3;
-        uint4 o;
-        o.x = digit_pair(b[0].w[wi], b[1].w[wi], byte);
-        o.y = digit_pair(b[2].w[wi], b[3].w[wi], byte);
-        o.z = digit_pair(b[4].w[wi], b[5].w[wi], byte);
-        o.w = digit_pair(b[6].w[wi], b[7].w[wi], byte);
-        *reinterpret_cast<uint4*>(dst + t * (ND * KS * 2)) = o;
-    }
+    store_planes8<W>(b, dst, ND * KS * 2);
 }
 
 template <int W, int G>
@@ -1801,17 +1780,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __
                 Biased<W> b[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
-                // word wi of the 8 values gives planes 4 wi .. 4 wi + 3
-#pragma unroll
-                for (int wi = 0; wi < 2 * W; ++wi) {
-                    uint32_t h[4][4];   // [value pair][byte]
-#pragma unroll
-                    for (int pr = 0; pr < 4; ++pr) digit_quad(b[2 * pr].w[wi], b[2 * pr + 1].w[wi], h[pr]);
-#pragma unroll
-                    for (int byte = 0; byte < 4; ++byte)
-                        *reinterpret_cast<uint4*>(dst + (4 * wi + byte) * A_PLANE + kh * CORE_LBO) =
-                            make_uint4(h[0][byte], h[1][byte], h[2][byte], h[3][byte]);
-                }
+                store_planes8<W>(b, dst + kh * CORE_LBO, A_PLANE);
             }
             ptx::fence_proxy_async_smem();
             __syncwarp();
