@@ -2160,7 +2160,12 @@ bool fill_tall(TcGroup<G>& tg, PrologueRGroup<G>& pg, int j, const GemmArgs& a, 
                        pl.m_tiles, pl.n_tiles, pl.U, gm, 0};
     pg.p[j] = PrologueRParams{a.B, a.F, a.alpha, a.coef, a.M, a.K, a.N, pl.Kp, pl.S_tot, Rp, a.C, a.Z,
                               pl.I, pl.m_tiles, pl.n_tiles, gm};
-    pg.b_off[j + 1] = pg.b_off[j] + (pl.n_tiles * pl.S_tot * 2 * pl.ND + 255) / 256;
+    // blocks of 256 threads, 2 ND threads per (column tile, stage) of R'; the
+    // same blocks also preset Z = C on the split tiles (32 KB each), so a layer
+    // with few column tiles still gets about four blocks per SM for that copy
+    const int64_t conv = (pl.n_tiles * pl.S_tot * 2 * pl.ND + 255) / 256;
+    const int64_t copy = std::min<int64_t>(pl.m_tiles * pl.n_tiles, 4 * (int64_t)sm_count());
+    pg.b_off[j + 1] = pg.b_off[j] + std::max(conv, copy);
     return true;
 }
 
