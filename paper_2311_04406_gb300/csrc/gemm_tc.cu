@@ -917,12 +917,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                     e[2 * q + 1] = v.y;
                 }
             }
-            // the next TMA write into this slot is an async-proxy access: order
-            // these generic-proxy reads before it (without this fence the TMA
-            // overwrote tiles still being read, measured on GB300)
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&rawEmpty[r]);
             Biased<W> b[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) b[q] = biased<W>(e + q * W);
@@ -947,11 +941,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
                     *reinterpret_cast<uint2*>(dst + t * (ND / 8) * CORE_SBO) = make_uint2(h01[byte], h23[byte]);
                 }
             }
-            // each thread orders its plane writes before the MMAs (async
-            // proxy); the warp then arrives once
+            // each thread orders its plane writes before the MMAs and its raw
+            // reads before the next TMA write into the raw slot (both async
+            // proxy; without ordering the reads the TMA overwrote tiles still
+            // being read, measured on GB300); the warp then arrives once on each
             ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&full[s]);
+            if (lane == 0) {
+                ptx::mbar_arrive(&full[s]);
+                ptx::mbar_arrive(&rawEmpty[r]);
+            }
         }
     } else if (warp == W_MMA) {
         // The whole warp runs the loop (waits included) and one elected lane
@@ -1313,10 +1312,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
                     e[2 * k + 1] = v.y;
                 }
             }
-            // order these generic-proxy reads before the next TMA write into the slot
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&rawEmpty[r]);
             const int s = it % STAGES;
             if (!__all_sync(0xffffffffu,
                             ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT))) {
@@ -1331,11 +1326,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
                 for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
                 store_planes8<W>(b, dst + kh * CORE_LBO, A_PLANE);
             }
-            // each thread orders its plane writes before the MMAs (async proxy);
-            // the warp then arrives once
+            // each thread orders its plane writes before the MMAs and its raw
+            // reads before the next TMA write into the raw slot (async proxy);
+            // the warp then arrives once on each
             ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&full[s]);
+            if (lane == 0) {
+                ptx::mbar_arrive(&full[s]);
+                ptx::mbar_arrive(&rawEmpty[r]);
+            }
         }
     } else if (warp == W_MMA) {
         const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
@@ -1765,9 +1764,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __
                 e[k * W] = v.x;
                 e[k * W + 1] = v.y;
             }
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&rawEmpty[r]);
             const int s = it % STAGES;
             if (!__all_sync(0xffffffffu,
                             ptx::mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort_flag, WAIT_LIMIT))) {
@@ -1782,9 +1778,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __
                 for (int q = 0; q < 8; ++q) b[q] = biased<W>(e + (kh * 8 + q) * W);
                 store_planes8<W>(b, dst + kh * CORE_LBO, A_PLANE);
             }
+            // one fence orders the plane writes before the MMAs and the raw
+            // reads before the next TMA write into the raw slot
             ptx::fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&full[s]);
+            if (lane == 0) {
+                ptx::mbar_arrive(&full[s]);
+                ptx::mbar_arrive(&rawEmpty[r]);
+            }
         }
     } else if (warp == W_MMA) {
         const uint32_t aBase = ptx::smem_u32(sA), bBase = ptx::smem_u32(sB);
