@@ -5,13 +5,22 @@
 //   a5  mZc  = mC.chi + E.(mB.chi) + mA.(F.chi) + alpha * E.(F.chi)
 //       mDc  = mR.chi - mZc,  Dc = D~.chi            (Eq. (compute-zcomptag))
 //
+// In Z_2^64 the two terms in E are one product: E.(mB.chi) + alpha * E.(F.chi)
+// = E.(mB.chi + alpha * F.chi) mod 2^64 (the ring is commutative and the sums
+// distribute).  The rows pass stores w = mB.chi + alpha * F.chi in place of
+// mB.chi (chunk by chunk: the sum over chunks is linear), so the vec pass
+// multiplies each element of E and mA once: mZc = mC.chi + E.w + mA.(F.chi).
+// In Z_2^128 the vec pass keeps the three products (w = mB.chi): measured on
+// GB300, 160 us against 188 us for the 32768 x 576 x 64 layer's call, where the
+// Z_2^64 layers gain 2-5 % from the fold.
+//
 // Up to three launches on the caller's stream:
 //   1. rows_kernel   one pass over the five N-wide matrices.  A warp owns a
 //                    (row, column-chunk) task: it streams mR, D~, mC (writing
 //                    mZ on the fly) or mB, F, and leaves per-chunk partial
 //                    dot products with chi in the workspace.  Each input word
 //                    is read from HBM exactly once.
-//   2. finalize_kernel  sums the K-side partials into the vectors mB.chi, F.chi
+//   2. finalize_kernel  sums the K-side partials into the vectors w (or mB.chi), F.chi
 //                    (only when a row is split into several chunks; with one
 //                    chunk the partials are those vectors and vec reads them).
 //   3. vec_kernel    one warp per output row: the two M x K GEMVs over E and
@@ -98,6 +107,7 @@ struct RowsParams {
     const u64 *alpha, *mR, *Dt, *mC, *mB, *F, *chi;
     u64* mZ;   // NULL: the OptMAC tag is not written
     u64 *pmr, *pd, *pmc, *qmb, *qf;
+    int with_eu;   // the E.(F.chi) term is present (Z_2^64: folded into the K-side partial of mB.chi)
 };
 
 // VEC = 2: two Z_2^64 elements per 16-byte access (needs even N).  Warp
@@ -172,6 +182,7 @@ __device__ __forceinline__ void rows_body(const RowsParams& p, int64_t g, int la
         }
         s1 = warp_sum<W>(s1);
         s2 = warp_sum<W>(s2);
+        if (W == 1 && p.with_eu) s1 += alpha * s2;   // the chunk's part of w = mB.chi + alpha * F.chi
         if (lane == 0) {
             st_elem<W>(p.qmb, t, s1);
             st_elem<W>(p.qf, t, s2);
@@ -213,7 +224,7 @@ __global__ void finalize_kernel(int64_t K, int64_t S, const u64* qmb, const u64*
 struct VecParams {
     int64_t M, K, S;
     int with_eu;
-    const u64 *alpha, *E, *mA, *vmb, *vf, *pmr, *pd, *pmc;
+    const u64 *alpha, *E, *mA, *vmb, *vf, *pmr, *pd, *pmc;   // vmb: w (Z_2^64) or mB.chi (Z_2^128)
     u64 *mDc, *Dc;
 };
 
@@ -222,12 +233,13 @@ struct VecParams {
 template <int W, int VEC>
 __device__ __forceinline__ void vec_body(const VecParams& p, int wpr, int64_t blk) {
     using T = typename Elem<W>::T;
-    __shared__ T part[3][WARPS];
+    constexpr int NP = W == 1 ? 2 : 3;   // partial sums per row
+    __shared__ T part[NP][WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rows_per_block = WARPS / wpr;
     const int64_t r = blk * rows_per_block + warp / wpr;
     const int sub = warp % wpr;
-    T e_mb = 0, ma_u = 0, e_u = 0;
+    T e_w = 0, ma_u = 0, e_u = 0;   // E.w, mA.(F.chi) and (Z_2^128) E.(F.chi) of row r
     if (r < p.M) {
         const int64_t base = r * p.K;
         if constexpr (VEC == 2) {
@@ -235,39 +247,38 @@ __device__ __forceinline__ void vec_body(const VecParams& p, int wpr, int64_t bl
             for (int64_t k = 2 * (sub * 32 + lane); k < p.K; k += 64 * wpr) {
                 ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(p.E + base + k));
                 ulonglong2 ma = __ldg(reinterpret_cast<const ulonglong2*>(p.mA + base + k));
-                ulonglong2 mb = *reinterpret_cast<const ulonglong2*>(p.vmb + k);
+                ulonglong2 w = *reinterpret_cast<const ulonglong2*>(p.vmb + k);
                 ulonglong2 u = *reinterpret_cast<const ulonglong2*>(p.vf + k);
-                e_mb += e.x * mb.x + e.y * mb.y;
+                e_w += e.x * w.x + e.y * w.y;
                 ma_u += ma.x * u.x + ma.y * u.y;
-                e_u += e.x * u.x + e.y * u.y;
             }
         } else {
 #pragma unroll 4
             for (int64_t k = sub * 32 + lane; k < p.K; k += 32 * wpr) {
                 T e = ldg_elem<W>(p.E, base + k);
                 T ma = ldg_elem<W>(p.mA, base + k);
-                T mb = ld_elem<W>(p.vmb, k);
+                T w = ld_elem<W>(p.vmb, k);
                 T u = ld_elem<W>(p.vf, k);
-                e_mb += e * mb;
+                e_w += e * w;
                 ma_u += ma * u;
-                e_u += e * u;
+                if constexpr (W == 2) e_u += e * u;
             }
         }
-        e_mb = warp_sum<W>(e_mb);
+        e_w = warp_sum<W>(e_w);
         ma_u = warp_sum<W>(ma_u);
-        e_u = warp_sum<W>(e_u);
+        if constexpr (W == 2) e_u = warp_sum<W>(e_u);
     }
     if (lane == 0) {
-        part[0][warp] = e_mb;
+        part[0][warp] = e_w;
         part[1][warp] = ma_u;
-        part[2][warp] = e_u;
+        if constexpr (W == 2) part[2][warp] = e_u;
     }
     __syncthreads();
     if (r < p.M && sub == 0 && lane == 0) {
         for (int j = 1; j < wpr; ++j) {
-            e_mb += part[0][warp + j];
+            e_w += part[0][warp + j];
             ma_u += part[1][warp + j];
-            e_u += part[2][warp + j];
+            if constexpr (W == 2) e_u += part[2][warp + j];
         }
         T mrc = 0, dc = 0, mcc = 0;
         for (int64_t s = 0; s < p.S; ++s) {
@@ -275,8 +286,8 @@ __device__ __forceinline__ void vec_body(const VecParams& p, int wpr, int64_t bl
             dc += ld_elem<W>(p.pd, r * p.S + s);
             mcc += ld_elem<W>(p.pmc, r * p.S + s);
         }
-        const T alpha = ld_elem<W>(p.alpha, 0);
-        T mzc = mcc + e_mb + ma_u + (p.with_eu ? alpha * e_u : (T)0);
+        T mzc = mcc + e_w + ma_u;
+        if (W == 2 && p.with_eu) mzc += ld_elem<W>(p.alpha, 0) * e_u;
         st_elem<W>(p.mDc, r, mrc - mzc);
         st_elem<W>(p.Dc, r, dc);
     }
@@ -303,14 +314,14 @@ __device__ __forceinline__ void vec_small_body(const VecParams& p, int64_t blk) 
     __syncthreads();
     const int64_t r = blk * NT + threadIdx.x;
     if (r >= p.M) return;
-    T e_mb = 0, ma_u = 0, e_u = 0;
+    T e_w = 0, ma_u = 0, e_u = 0;
     const int64_t base = r * p.K;
     for (int k = 0; k < (int)p.K; ++k) {
         const T e = ldg_elem<W>(p.E, base + k);
         const T ma = ldg_elem<W>(p.mA, base + k);
-        e_mb += e * smb[k];
+        e_w += e * smb[k];
         ma_u += ma * sf[k];
-        e_u += e * sf[k];
+        if constexpr (W == 2) e_u += e * sf[k];
     }
     T mrc = 0, dc = 0, mcc = 0;
     for (int64_t s = 0; s < p.S; ++s) {
@@ -318,8 +329,8 @@ __device__ __forceinline__ void vec_small_body(const VecParams& p, int64_t blk) 
         dc += ld_elem<W>(p.pd, r * p.S + s);
         mcc += ld_elem<W>(p.pmc, r * p.S + s);
     }
-    const T alpha = ld_elem<W>(p.alpha, 0);
-    const T mzc = mcc + e_mb + ma_u + (p.with_eu ? alpha * e_u : (T)0);
+    T mzc = mcc + e_w + ma_u;
+    if (W == 2 && p.with_eu) mzc += ld_elem<W>(p.alpha, 0) * e_u;
     st_elem<W>(p.mDc, r, mrc - mzc);
     st_elem<W>(p.Dc, r, dc);
 }
@@ -340,7 +351,7 @@ cudaError_t run(const CompactArgs& a, char* ws, cudaStream_t st) {
     WsLayout L = ws_layout(a.M, a.K, a.N, W);
     RowsParams rp{a.M, a.K, a.N, sp.S, sp.cw, a.alpha, a.mR, a.Dt, a.mC, a.mB, a.F, a.chi, a.mZ,
                   (u64*)(ws + L.pmr), (u64*)(ws + L.pd), (u64*)(ws + L.pmc),
-                  (u64*)(ws + L.qmb), (u64*)(ws + L.qf)};
+                  (u64*)(ws + L.qmb), (u64*)(ws + L.qf), a.with_eu};
     const int64_t tasks = (a.M + a.K) * sp.S;
     if (tasks > 0) {
         const unsigned blocks = (unsigned)((tasks + WARPS - 1) / WARPS);
@@ -488,7 +499,7 @@ cudaError_t run_group(const CompactArgs* a, int n, char* const* ws, cudaStream_t
             CompactLayer& L = g->L[cnt];
             L.rp = RowsParams{x.M, x.K, x.N, sp.S, sp.cw, x.alpha, x.mR, x.Dt, x.mC, x.mB, x.F, x.chi, x.mZ,
                               (u64*)(w + wl.pmr), (u64*)(w + wl.pd), (u64*)(w + wl.pmc),
-                              (u64*)(w + wl.qmb), (u64*)(w + wl.qf)};
+                              (u64*)(w + wl.qmb), (u64*)(w + wl.qf), x.with_eu};
             L.vmb = (u64*)(w + wl.vmb);
             L.vf = (u64*)(w + wl.vf);
             // one chunk per row: the vec pass reads the partials in place (no finalize blocks)
