@@ -29,8 +29,10 @@ CASES = [
     (synth.Z64, (2048, 4096, 1024)),     # Transformer ffn_down
     (synth.Z64, (4096, 128, 4096)),      # training grad W of the dense layer
     (synth.Z64, (65536, 576, 64)),       # VGG16 conv2 at batch 64
-    (synth.Z128, (32768, 576, 64)),      # ResNet-18 stage-0 conv at batch 32, Z_2^128
+    (synth.Z128, (32768, 576, 64)),      # ResNet-18 stage-0 conv at batch 32, Z_2^128 (tall tile)
+    (synth.Z128, (8192, 1152, 128)),     # ResNet-18 stage-1 conv at batch 32, Z_2^128 (tall tile, N = 128)
     (synth.Z128, (2048, 2304, 256)),     # ResNet-18 stage-2 conv at batch 32, Z_2^128
+    (synth.Z64, (4096, 1152, 128)),      # VGG16 conv at 16x16 and batch 16, Z_2^64 (tall tile, N = 128)
 ]
 
 
