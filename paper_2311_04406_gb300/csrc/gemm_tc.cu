@@ -145,12 +145,12 @@ constexpr uint32_t F16_1152X2 = 0x64806480u;   // fp16 (1152, 1152)
 //
 // The value d of diagonal t (an integer, |d| <= 2^24, converted exactly from
 // its fp32 accumulator) adds d 2^(8t) to its output's wrapping sum mod
-// 2^(64 W).  Z_2^64 adds the sign-extended, shifted term.  Z_2^128 touches
-// only the words of the sum a term can change: the two diagonals t, t + 1 of
-// one TMEM load (t even) first form g = d_t 2^(8 (t mod 4)) +
-// d_(t+1) 2^(8 ((t+1) mod 4)), |g| < 2^41, which is added to the sum's four
-// 32-bit words as g 2^0 (t < 4), g 2^32 (t < 8), g mod 2^64 at 2^64 (t < 12)
-// or g mod 2^32 at 2^96, with explicit carry chains.
+// 2^(64 W).  Z_2^64 adds the sign-extended, shifted term.  Z_2^128 takes four
+// consecutive diagonals t .. t + 3 (t = 0, 4, 8, 12) of one column together:
+// g = d_t + 2^8 d_(t+1) + 2^16 d_(t+2) + 2^24 d_(t+3), |g| < 2^49, by a
+// mad.wide.s32 chain, which then enters the sum's four 32-bit words through one
+// explicit carry chain: at 2^0 (t = 0), 2^32 (t = 4), 2^64 (t = 8, low 64 bits
+// of g) or 2^96 (t = 12, low 32 bits).
 
 __device__ __forceinline__ long long mad_wide_s32(int a, int b, long long c) {
     long long d;
@@ -184,29 +184,59 @@ __device__ __forceinline__ u128 add_at(u128 sum, long long g) {
     return (u128)lo | ((u128)hi << 64);
 }
 
-// One 32-column TMEM load of diagonals t0 .. t0 + 32 / NC - 1 (NC columns
-// each) into the NC sums.
-template <int W, int NC>
-__device__ __forceinline__ void drain_fold(const uint32_t (&f)[32], int t0, typename Elem<W>::T (&sum)[NC]) {
+// The drain of one accumulator set (TMEM column block t of ND columns holds
+// diagonal t) into the ND sums of the warp's lanes; `release` runs once every
+// load of the set has completed, after which the MMAs may reuse it.
+template <int W, int ND, typename Release>
+__device__ __forceinline__ void drain_set(uint32_t base, typename Elem<W>::T (&sum)[ND], Release release) {
+    constexpr int NDIG = 8 * W;
     if constexpr (W == 1) {
+        static_assert(ND == 32, "one diagonal per 32-column load");
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int t = t0 + q / NC, c = q % NC;
-            const long long d = __float2int_rn(__uint_as_float(f[q]));
-            sum[c] += (u64)d << (8 * t);
+        for (int t0 = 0; t0 < NDIG; ++t0) {
+            uint32_t f[32];
+            ptx::tmem_ld32(base + t0 * ND, f);
+            ptx::tmem_wait_ld();
+            if (t0 + 1 == NDIG) release();
+#pragma unroll
+            for (int c = 0; c < ND; ++c) {
+                const long long d = __float2int_rn(__uint_as_float(f[c]));
+                sum[c] += (u64)d << (8 * t0);
+            }
         }
     } else {
-        static_assert(NC == 16, "two diagonals per load");
-        const int s0 = 8 * (t0 & 3), s1 = 8 * ((t0 + 1) & 3);
+        // diagonals t0 .. t0 + 3 of 8 columns at a time (four 8-column loads,
+        // one wait): g = d_t0 + 2^8 d_(t0+1) + 2^16 d_(t0+2) + 2^24 d_(t0+3)
+        static_assert(ND == 16, "two halves of 8 columns");
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int d0 = __float2int_rn(__uint_as_float(f[c]));
-            const int d1 = __float2int_rn(__uint_as_float(f[NC + c]));
-            const long long g = mad_wide_s32(d1, 1 << s1, (long long)d0 << s0);
-            if (t0 < 4) sum[c] = add_at<0>(sum[c], g);
-            else if (t0 < 8) sum[c] = add_at<1>(sum[c], g);
-            else if (t0 < 12) sum[c] = add_at<2>(sum[c], g);
-            else sum[c] = add_at<3>(sum[c], g);
+        for (int t0 = 0; t0 < NDIG; t0 += 4) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t f[32];   // f[8 j + c]: diagonal t0 + j, column 8 h + c
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ptx::tmem_ld8(base + (t0 + j) * ND + 8 * h, f + 8 * j);
+                ptx::tmem_wait_ld();
+                if (t0 + 4 == NDIG && h == 1) release();
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    int d[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) d[j] = __float2int_rn(__uint_as_float(f[8 * j + c]));
+                    typename Elem<W>::T& sc = sum[8 * h + c];
+                    if (t0 < 12) {
+                        long long g = mad_wide_s32(d[1], 1 << 8, (long long)d[0]);
+                        g = mad_wide_s32(d[2], 1 << 16, g);
+                        g = mad_wide_s32(d[3], 1 << 24, g);
+                        if (t0 == 0) sc = add_at<0>(sc, g);
+                        else if (t0 == 4) sc = add_at<1>(sc, g);
+                        else sc = add_at<2>(sc, g);
+                    } else {
+                        const uint32_t g = (uint32_t)d[0] + ((uint32_t)d[1] << 8) + ((uint32_t)d[2] << 16) +
+                                           ((uint32_t)d[3] << 24);
+                        sc = add_at<3>(sc, (long long)g);
+                    }
+                }
+            }
         }
     }
 }
@@ -1019,7 +1049,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
     } else {
         // drain warps: TMEM lane quadrant = warp % 4
         const int quad = warp & 3;
-        constexpr int DPL = 32 / ND;   // diagonals per 32-column TMEM load
         Sum sum[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
@@ -1042,20 +1071,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_kernel(const __grid_
             }
             ptx::tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * NSTACK;
-#pragma unroll
-            for (int t0 = 0; t0 < NDIG; t0 += DPL) {
-                uint32_t f[32];
-                ptx::tmem_ld32(base + t0 * ND, f);
-                ptx::tmem_wait_ld();
-                if (t0 + DPL >= NDIG) {
-                    // every lane's loads are complete (wait::ld above); the
-                    // warp releases the accumulator set as one arrival
-                    ptx::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
-                }
-                drain_fold<W, ND>(f, t0, sum);
-            }
+            drain_set<W, ND>(base, sum, [&] {
+                // every lane's loads are complete (wait::ld); the warp
+                // releases the accumulator set as one arrival
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
+            });
             if (seg_ii < 0) seg_ii = x_ii;
             if (x_flush) {
                 // a tile computed whole by this segment is written as C + sum;
@@ -1383,7 +1405,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
         // drain: lane l of quadrant q holds output column 32 q + l of the tile
         // and the sums of its ND rows
         const int quad = warp & 3;
-        constexpr int DPL = 32 / ND;
         Sum sum[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
@@ -1406,18 +1427,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_wide_kernel(const __
             }
             ptx::tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * NSTACK;
-#pragma unroll
-            for (int t0 = 0; t0 < NDIG; t0 += DPL) {
-                uint32_t f[32];
-                ptx::tmem_ld32(base + t0 * ND, f);
-                ptx::tmem_wait_ld();
-                if (t0 + DPL >= NDIG) {
-                    ptx::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
-                }
-                drain_fold<W, ND>(f, t0, sum);
-            }
+            drain_set<W, ND>(base, sum, [&] {
+                // every lane's loads are complete (wait::ld); the warp
+                // releases the accumulator set as one arrival
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
+            });
             if (seg_ii < 0) seg_ii = x_ii;
             if (x_flush) {
                 // whole tiles store C + sum, pieces of split tiles are added
@@ -1833,7 +1849,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __
     } else {
         // drain: lane l of quadrant q holds row 32 q + l of the tile and its ND sums
         const int quad = warp & 3;
-        constexpr int DPL = 32 / ND;
         Sum sum[ND];
 #pragma unroll
         for (int c = 0; c < ND; ++c) sum[c] = 0;
@@ -1856,18 +1871,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) ring_gemm_tc_tall_kernel(const __
             }
             ptx::tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(quad * 32) << 16) + set * NSTACK;
-#pragma unroll
-            for (int t0 = 0; t0 < NDIG; t0 += DPL) {
-                uint32_t f[32];
-                ptx::tmem_ld32(base + t0 * ND, f);
-                ptx::tmem_wait_ld();
-                if (t0 + DPL >= NDIG) {
-                    ptx::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
-                }
-                drain_fold<W, ND>(f, t0, sum);
-            }
+            drain_set<W, ND>(base, sum, [&] {
+                // every lane's loads are complete (wait::ld); the warp
+                // releases the accumulator set as one arrival
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&accEmpty[set]);
+            });
             if (seg_ii < 0) seg_ii = x_ii;
             if (x_flush) {
                 const bool whole = seg_ii == 0 && x_ii == p.I - 1;
