@@ -167,9 +167,12 @@ int mpc_tag_check(const mpc_layer *layer, int mode, const uint64_t *alpha_i,
  * GPU: every tensor-core layer of the group (up to 64 per launch) is scheduled
  * by ONE persistent prologue + GEMM launch pair whose CTAs work through the
  * layers' (tile, K interval) units in turn; the remaining layers run the
- * integer-pipe kernels one by one.  A tensor-core layer long enough to keep
- * every SM busy for 64 waves of units gets a launch pair of its own (it gains
- * nothing from sharing one and runs faster alone).
+ * integer-pipe kernels on side streams of the library, concurrently with one
+ * another and with that launch pair (forked from and joined back to `stream`
+ * with events, so the call stays ordered on `stream` and can be captured).
+ * A tensor-core layer long enough to keep every SM busy for 64 waves of units
+ * gets a launch pair of its own (it gains nothing from sharing one and runs
+ * faster alone).
  *
  * layers[count], ptrs[count]: HOST arrays, read during the call only.  All
  * layers share one ring (MPC_E_RING otherwise); the party may differ per

@@ -4,8 +4,10 @@
 // pointers, alignment, workspace) and returns a negative status without
 // launching anything when they are invalid, so no kernel ever runs on bad
 // input.  Valid calls enqueue kernels on the caller's stream and return.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "mpclinear.h"
@@ -428,6 +430,45 @@ size_t group_compact_ws(const mpc_layer* layers, int count) {
 }
 
 // the tensor-core layers as one grouped launch, the others one by one
+// Side streams for the integer-pipe layers of a grouped call.  Those layers are
+// independent of one another and of the tensor-core layers, and each uses a
+// fraction of the GPU (a split-K GEMV of a batch-1 layer streams its weights
+// with a few hundred blocks), so they run concurrently: a fork event recorded
+// on the caller's stream before any of the call's launches, which every side
+// stream waits for (nothing starts before the call's inputs are ready), the
+// layers dealt round-robin to the side streams, and one join event per side
+// stream that the caller's stream waits for.  Under stream capture the same
+// calls make parallel branches of the graph.  Per device, created on first use
+// and kept until the process exits; the mutex keeps two host threads from
+// interleaving their fork and join records.  If the streams cannot be created
+// the layers run one after another on the caller's stream.
+constexpr int SIDE_STREAMS = 4;
+constexpr int SIDE_DEVICES = 64;
+
+struct SidePool {
+    std::mutex mu;
+    bool tried = false, ok = false;
+    cudaStream_t s[SIDE_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[SIDE_STREAMS] = {};
+};
+
+SidePool* side_pool() {
+    static SidePool pools[SIDE_DEVICES];
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SIDE_DEVICES) return nullptr;
+    SidePool* p = &pools[dev];
+    std::lock_guard<std::mutex> lk(p->mu);
+    if (!p->tried) {
+        p->tried = true;
+        bool ok = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; ok && i < SIDE_STREAMS; ++i)
+            ok = cudaStreamCreateWithFlags(&p->s[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&p->join[i], cudaEventDisableTiming) == cudaSuccess;
+        p->ok = ok;
+    }
+    return p->ok ? p : nullptr;
+}
+
 int run_gemm_group(const mpc_layer* layers, int count, const mpcl::GemmArgs* g, void* ws, size_t ws_bytes,
                    cudaStream_t st) {
     const size_t need = group_gemm_ws(layers, count);
@@ -454,9 +495,30 @@ int run_gemm_group(const mpc_layer* layers, int count, const mpcl::GemmArgs* g, 
         }
         cur += (mpcl::gemm_tc_workspace(g[i].M, g[i].K, g[i].N, g[i].words) + 255) & ~size_t(255);
     }
-    if (!tc.empty()) CHK(cuda_status(mpcl::launch_gemm_tc_grouped(tc.data(), (int)tc.size(), ap.data(), st)));
-    for (const auto& x : simt) CHK(cuda_status(mpcl::launch_gemm_simt(x, st)));
-    return MPC_OK;
+    SidePool* side = (!simt.empty() && simt.size() + (tc.empty() ? 0 : 1) >= 2) ? side_pool() : nullptr;
+    if (!side) {
+        if (!tc.empty()) CHK(cuda_status(mpcl::launch_gemm_tc_grouped(tc.data(), (int)tc.size(), ap.data(), st)));
+        for (const auto& x : simt) CHK(cuda_status(mpcl::launch_gemm_simt(x, st)));
+        return MPC_OK;
+    }
+    std::lock_guard<std::mutex> lk(side->mu);
+    const int ns = (int)std::min<size_t>(simt.size(), SIDE_STREAMS);
+    CHK(cuda_status(cudaEventRecord(side->fork, st)));
+    for (int i = 0; i < ns; ++i) CHK(cuda_status(cudaStreamWaitEvent(side->s[i], side->fork, 0)));
+    // from here on every side stream is joined back whatever a launch returns,
+    // so that the caller's stream never runs ahead of work queued on a side
+    // stream; the first error is reported
+    int status = MPC_OK;
+    for (size_t j = 0; j < simt.size() && status == MPC_OK; ++j)
+        status = cuda_status(mpcl::launch_gemm_simt(simt[j], side->s[j % ns]));
+    if (status == MPC_OK && !tc.empty())
+        status = cuda_status(mpcl::launch_gemm_tc_grouped(tc.data(), (int)tc.size(), ap.data(), st));
+    for (int i = 0; i < ns; ++i) {
+        const int a = cuda_status(cudaEventRecord(side->join[i], side->s[i]));
+        const int b = a == MPC_OK ? cuda_status(cudaStreamWaitEvent(st, side->join[i], 0)) : a;
+        if (status == MPC_OK) status = b;
+    }
+    return status;
 }
 
 }  // namespace
