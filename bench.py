@@ -407,11 +407,13 @@ class GpuWorkload:
     def setup_grouped(self):
         a, torch = self.abi, self.torch
         self.glayers, self.gshare, self.gtag_full, self.gtag_comp, self.gws = [], [], [], [], []
+        self.gcheck = []
         for p in range(PARTIES):
             lays = [par[p]["layer"] for _, _, par in self.items]
-            sh, tf, tc = [], [], []
+            sh, tf, tc, ck = [], [], [], []
             for _, pub, par in self.items:
                 d = par[p]
+                ck.append(dict(alpha_i=d["alpha"], chi_hat=pub["chi_hat"], Dc=d["Dc"], mDc_i=d["mDc"], cs_i=d["cs"]))
                 sh.append(dict(E=pub["E"], F=pub["F"], A_i=d["A"], B_i=d["B"], C_i=d["C"], Z_i=d["Z"]))
                 base = dict(alpha_i=d["alpha"], E=pub["E"], F=pub["F"], mA_i=d["mA"], mB_i=d["mB"], mC_i=d["mC"],
                             mR_i=d["mR"], Dtilde=pub["Dt"], chi=pub["chi"], mDc_i=d["mDc"], Dc=d["Dc"])
@@ -423,6 +425,7 @@ class GpuWorkload:
             self.gshare.append(sh)
             self.gtag_full.append(tf)
             self.gtag_comp.append(tc)
+            self.gcheck.append(ck)
             self.gws.append(torch.empty(max(need, 256), dtype=torch.uint8, device="cuda"))
 
     def share_group(self, p):
@@ -440,10 +443,8 @@ class GpuWorkload:
             self._pre(i, p, tag=True)
         self.abi.mpc_linear_tag_grouped(self.glayers[p], self.abi.MPC_TAG_COMPACT, self.gtag_comp[p],
                                         ws=self.gws[p])
-        for i, (L, pub, par) in enumerate(self.items):
-            d = par[p]
-            self.abi.mpc_tag_check(d["layer"], self.abi.MPC_CHECK_COMPACT, d["alpha"], pub["chi_hat"],
-                                   d["Dc"], d["mDc"], d["cs"], ws=d["ws"])
+        # every layer's check share in one launch per 64 layers
+        self.abi.mpc_tag_check_grouped(self.glayers[p], self.gcheck[p])
 
     def step_grouped(self):
         for p in range(PARTIES):
@@ -458,7 +459,7 @@ class GpuWorkload:
             lays = self.glayers[p]
             n += sum(a.mpc_launch_count_grouped(lays, w)
                      for w in (a.MPC_WS_SHARE, a.MPC_WS_TAG_FULL, a.MPC_WS_TAG_COMPACT))
-            n += len(lays) + 3 * len(self.links)
+            n += (len(lays) + 63) // 64 + 3 * len(self.links)   # grouped checks; transposes
         return n
 
     def launches_per_step(self):
