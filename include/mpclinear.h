@@ -244,8 +244,8 @@ int mpc_launch_count_grouped(const mpc_layer *layers, int count, int which);
  * blocks than SMs, else 64; skinny layers with M <= 8 use a GEMV whatever the
  * value) and a K-split target of `waves` x 152 blocks (0 = default).  Untuned
  * shapes use a built-in rule (tensor cores from 2^22 ring MACs, 2^20 for
- * Z_2^128; the wide tile up to two of its row tiles, 64-row tiles up to
- * M = 64, the tall tile for layers with N <= 64 and M >= 2048 (Z_2^64) or
+ * Z_2^128; the wide tile up to two of its row tiles, and for Z_2^128 up to
+ * M = 64 when it has a work unit per SM; 64-row tiles up to M = 64, the tall tile for layers with N <= 64 and M >= 2048 (Z_2^64) or
  * M >= 1024 (Z_2^128), and for N <= 128 from M = 4096).  The table is process-wide and thread-safe; workspace
  * sizes do not depend on it.
  *

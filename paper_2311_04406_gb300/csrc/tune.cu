@@ -51,6 +51,14 @@ bool choice_ok(const Choice& c, int64_t M, int64_t K, int64_t N, int words) {
 // M = 128 one).
 int default_rows(int64_t M, int64_t K, int64_t N, int words) {
     if (M <= 2 * wide_tile_rows(words)) return wide_tile_rows(words);
+    // Z_2^128 layers of 33-64 rows: an M = 64 MMA costs as much as an M = 128
+    // one, and the wide tile is faster once it has a work unit per SM (measured:
+    // 64 x 2304 x 256 46 -> 39 us, 64 x 4608 x 512 129 -> 94 us, 48 x 2304 x 256
+    // 45 -> 37 us; but 64 x 576 x 128, 72 wide units, 23 -> 27 us)
+    if (words == 2 && M <= 64) {
+        const int64_t rb = (M + 15) / 16, ct = (N + 127) / 128, iv = (2 * K + 63) / 64;
+        if (rb * ct * iv >= 152) return wide_tile_rows(words);
+    }
     if (M <= 64) return 64;
     // tall and narrow layers: the left operand's digit planes would cost an HBM
     // round trip comparable to the GEMM itself, so the GEMM converts them in

@@ -97,7 +97,9 @@ def test_built_in_rule_takes_short_tiles_for_short_layers():
     assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512))[::4] == (1, 32)        # wide
     assert abi.mpc_autotune_choice(abi.make_layer(65, 4608, 512))[::4] == (1, 128)
     assert abi.mpc_autotune_choice(abi.make_layer(16, 2304, 512, 64, 64))[::4] == (1, 16)
-    assert abi.mpc_autotune_choice(abi.make_layer(40, 2304, 512, 64, 64))[::4] == (1, 64)
+    assert abi.mpc_autotune_choice(abi.make_layer(40, 2304, 512, 64, 64))[::4] == (1, 16)    # wide: 864 units
+    assert abi.mpc_autotune_choice(abi.make_layer(64, 576, 128, 64, 64))[::4] == (1, 64)     # wide: 72 units
+    assert abi.mpc_autotune_choice(abi.make_layer(64, 2304, 256))[::4] == (1, 32)            # Z_2^64: wide to 64
     assert abi.mpc_autotune_choice(abi.make_layer(32768, 576, 64))[::4] == (1, -128)           # tall
     assert abi.mpc_autotune_choice(abi.make_layer(2048, 576, 64))[::4] == (1, -128)
     assert abi.mpc_autotune_choice(abi.make_layer(1024, 576, 64))[::4] == (1, 128)    # Z_2^64 tall from 2048 rows
