@@ -160,6 +160,15 @@ def test_launch_table_host_logic(lib, tmp_path):
     assert abi.mpc_autotune_choice(abi.make_layer(64, 4608, 512)) == (1, 0, 0, False, 32)     # wide tile
     assert abi.mpc_autotune_choice(abi.make_layer(65, 4608, 512)) == (1, 0, 0, False, 128)
     assert abi.mpc_autotune_choice(abi.make_layer(32, 4608, 512, 64, 64)) == (1, 0, 0, False, 16)
+    # the built-in tile rule's thresholds (host logic only)
+    rows = lambda M, K, N, *ring: abi.mpc_autotune_choice(abi.make_layer(M, K, N, *ring))[4]
+    assert rows(64, 2304, 256, 64, 64) == 16      # Z_2^128, 33-64 rows: wide once it has a unit per SM
+    assert rows(64, 576, 128, 64, 64) == 64       # 72 wide units: 64-row tiles
+    assert rows(2048, 576, 64) == -128 and rows(1024, 576, 64) == 128          # Z_2^64 tall from 2048 rows
+    assert rows(1024, 576, 64, 64, 64) == -128 and rows(512, 576, 64, 64, 64) == 128   # Z_2^128 from 1024
+    assert rows(4096, 1152, 128) == -128 and rows(2048, 1152, 128, 64, 64) == 128      # N = 128 from 4096
+    assert rows(8192, 2304, 256, 64, 64) == 128   # N > 128: 128-row tiles
+    assert rows(4096, 575, 64) == 128             # odd K in Z_2^64: no tall tile
     abi.mpc_autotune_set(small, 1, 4, 0, tile_rows=32)                 # the Z_2^64 wide tile
     with pytest.raises(abi.MpcError):
         abi.mpc_autotune_set(abi.make_layer(64, 128, 64, 64, 64), 1, 4, 0, tile_rows=32)   # Z_2^128: 16
